@@ -1,0 +1,142 @@
+"""CPU oracle for the shifted m-Hessenberg solver (TEST INFRASTRUCTURE ONLY).
+
+This package is the slow, plain, obviously correct reference the CUDA path is
+checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline of ``bench.py`` may import it; the product package never does, and the
+two share no code.
+
+All arithmetic is IEEE double (complex128), done in ``csrc/ssv_oracle.c``:
+
+* :func:`dense_solve` -- X = (A - sigma I)^{-1} B by LU with partial pivoting
+  on the full matrix (the plain definition of the shifted solve, Sec. 1).
+* :func:`reduce` -- controller-Hessenberg form (H, R, Ct[, Q]) of (A, B, C) by
+  unblocked Householder reflectors in the order of Algorithm 1 (Sec. 2).
+* :func:`reduced_solve` -- Xhat = (H - sigma I)^{-1} R (or G = Ct Xhat) by
+  band-limited Gaussian elimination with row pivoting in reduced coordinates,
+  plus an optional Hager/Higham estimate of kappa_1(H - sigma I).
+
+Conventions (Sec. 2, Sec. 3): G(sigma) = C X = Ct Xhat with
+X = (A - sigma I)^{-1} B; the paper's transfer function is
+C (sigma I - A)^{-1} B = -G(sigma).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+STATUS_OK = 0
+STATUS_SINGULAR = 1
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        lib.ora_dense_solve.argtypes = [I, I, P, I, P, I, I, P, P, P]
+        lib.ora_reduce.argtypes = [I, I, I, P, I, P, I, P, I, P, P, P, P]
+        lib.ora_reduced_solve.argtypes = [I, I, I, P, I, P, I, P, I, I, P, I, P, P, P]
+        for f in (lib.ora_dense_solve, lib.ora_reduce, lib.ora_reduced_solve):
+            f.restype = I
+        _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def dense_solve(A, B, sigmas):
+    """Return (X, status): X[j] = (A - sigmas[j] I)^{-1} B, complex128 (s, n, m).
+
+    status[j] = 1 where LU met an exactly zero pivot (X[j] is NaN there).
+    """
+    lib = _load()
+    A = _f64(A)
+    B = _f64(B)
+    if B.ndim == 1:
+        B = B[:, None]
+    n, m = B.shape
+    sig = np.ascontiguousarray(np.asarray(sigmas, dtype=np.complex128).reshape(-1))
+    ns = sig.size
+    X = np.zeros((ns, m, n), dtype=np.complex128)  # per shift column-major n x m
+    st = np.zeros(ns, dtype=np.int32)
+    rc = lib.ora_dense_solve(n, m, _ptr(A), n, _ptr(B), n, ns, _ptr(sig), _ptr(X), _ptr(st))
+    if rc != 0:
+        raise MemoryError("oracle dense_solve failed")
+    return np.transpose(X, (0, 2, 1)).copy(), st
+
+
+def reduce(A, B, C, want_q=False):
+    """Controller-Hessenberg form: returns (H, R, Ct, Q or None), all float64.
+
+    H = Q^T A Q is zero below the m-th subdiagonal, R = Q^T B is zero below the
+    diagonal (n x m), Ct = C Q (p x n).
+    """
+    lib = _load()
+    A = _f64(A)
+    B = _f64(B)
+    C = _f64(C)
+    n = A.shape[0]
+    m = B.shape[1]
+    p = C.shape[0]
+    H = np.zeros((n, n), order="F")
+    R = np.zeros((n, m), order="F")
+    Ct = np.zeros((p, n), order="F")
+    Q = np.zeros((n, n), order="F") if want_q else None
+    rc = lib.ora_reduce(n, m, p, _ptr(A), n, _ptr(B), n, _ptr(C), max(p, 1), _ptr(H), _ptr(R),
+                        _ptr(Ct), _ptr(Q))
+    if rc != 0:
+        raise MemoryError("oracle reduce failed")
+    return H, R, Ct, Q
+
+
+def reduced_solve(H, R, Ct, sigmas, want="xhat", cond=False):
+    """Solve (H - sigma I) Xhat = R for every shift in reduced coordinates.
+
+    want="xhat" returns Xhat (s, n, m); want="g" returns G = Ct Xhat (s, p, m).
+    Returns (out, status, cond1) with cond1 None unless cond=True.
+    """
+    lib = _load()
+    H = _f64(H)
+    R = _f64(R)
+    Ct = _f64(Ct)
+    n = H.shape[0]
+    m = R.shape[1]
+    p = Ct.shape[0]
+    sig = np.ascontiguousarray(np.asarray(sigmas, dtype=np.complex128).reshape(-1))
+    ns = sig.size
+    mode = 0 if want == "xhat" else 1
+    rows = n if mode == 0 else p
+    out = np.zeros((ns, m, rows), dtype=np.complex128)
+    st = np.zeros(ns, dtype=np.int32)
+    c1 = np.zeros(ns, dtype=np.float64) if cond else None
+    rc = lib.ora_reduced_solve(n, m, p, _ptr(H), n, _ptr(R), n, _ptr(Ct), max(p, 1), ns,
+                               _ptr(sig), mode, _ptr(out), _ptr(st), _ptr(c1))
+    if rc != 0:
+        raise MemoryError("oracle reduced_solve failed")
+    return np.transpose(out, (0, 2, 1)).copy(), st, c1
+
+
+def transfer(C, X):
+    """G = C X for a stack of solutions X (s, n, m) -> (s, p, m)."""
+    return np.einsum("pn,snm->spm", np.asarray(C, dtype=np.float64), X)
+
+
+def backward_error(Mfun_H, sigma, X, R):
+    """Normwise backward error ||(H - sigma I)X - R||_F / (||H - sigma I||_F ||X||_F + ||R||_F)."""
+    H = np.asarray(Mfun_H)
+    n = H.shape[0]
+    M = H.astype(np.complex128) - sigma * np.eye(n)
+    res = M @ X - R
+    return np.linalg.norm(res) / (np.linalg.norm(M) * np.linalg.norm(X) + np.linalg.norm(R))

@@ -1,0 +1,235 @@
+"""Pins of the CPU oracle against facts fixed by the mathematics (no GPU).
+
+Each test ties an oracle function to something other than itself:
+exact rational brute force, closed forms (diagonal and 2x2-block-diagonal A),
+textbook routines for special cases (sigma = 0, m = 1 Hessenberg), block-Krylov
+uniqueness of the controller-Hessenberg form, and invariants of Algorithm 1.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import workloads as W
+from tests import exact
+
+EPS = np.finfo(np.float64).eps
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+# --------------------------------------------------------------------------
+# dense_solve: the plain definition X = (A - sigma I)^{-1} B
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,m,seed", [(1, 1, 1), (3, 2, 2), (5, 1, 3), (6, 3, 4), (8, 2, 5)])
+def test_dense_solve_matches_exact_rational(ora, n, m, seed):
+    An, Bn, sig, den = W.small_rational_system(n, m, seed)
+    A = An / den
+    B = Bn / den
+    sigma = complex(sig[0], sig[1]) / den
+    X, st = ora.dense_solve(A, B, [sigma])
+    Xe = exact.solve(exact.shifted(An, den, sig), exact.real_matrix(Bn, den))
+    assert Xe is not None and st[0] == 0
+    Xe = np.array([[exact.to_complex(z) for z in row] for row in Xe])
+    assert relerr(X[0], Xe) < 1e-12
+
+
+@pytest.mark.parametrize("n,m", [(7, 2), (40, 3)])
+def test_dense_solve_diagonal_closed_form(ora, n, m):
+    a, sysd = W.diagonal_system(n, m, 2, seed=11)
+    sig = W.imag_axis_logspace(-2, 2, 9)
+    X, st = ora.dense_solve(sysd.A, sysd.B, sig)
+    assert (st == 0).all()
+    for j, s in enumerate(sig):
+        assert relerr(X[j], sysd.B / (a - s)[:, None]) < 1e-14
+
+
+def test_dense_solve_sigma_zero_is_linalg_solve(ora):
+    sysr = W.random_system(50, 4, 3, seed=12)
+    X, st = ora.dense_solve(sysr.A, sysr.B, [0.0])
+    assert relerr(X[0], np.linalg.solve(sysr.A, sysr.B)) < 1e-13
+
+
+def test_dense_solve_conjugate_symmetry(ora):
+    sysr = W.random_system(30, 3, 2, seed=13)
+    s = -0.7 + 1.3j
+    X, _ = ora.dense_solve(sysr.A, sysr.B, [s, np.conj(s)])
+    assert relerr(X[1], np.conj(X[0])) < 1e-13
+
+
+def test_dense_solve_exact_singular_shift(ora):
+    a, sysd = W.diagonal_system(6, 2, 2, seed=14)
+    X, st = ora.dense_solve(sysd.A, sysd.B, [a[3] + 0j, 1j])
+    assert st[0] == ora.STATUS_SINGULAR and np.isnan(X[0]).all()
+    assert st[1] == ora.STATUS_OK
+
+
+# --------------------------------------------------------------------------
+# reduce: Algorithm 1 invariants and uniqueness
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,m,p", [(2, 1, 1), (10, 1, 2), (12, 3, 2), (40, 5, 4), (33, 8, 3),
+                                   (7, 7, 2), (9, 8, 1), (65, 16, 16)])
+def test_reduce_invariants(ora, n, m, p):
+    sysr = W.random_system(n, m, p, seed=100 + n + m)
+    H, R, Ct, Q = ora.reduce(sysr.A, sysr.B, sysr.C, want_q=True)
+    tol = 50 * n * EPS
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) < tol
+    i, j = np.indices((n, n))
+    assert (H[i > j + m] == 0).all()                       # stored zeros below m-th subdiagonal
+    ib, jb = np.indices((n, m))
+    assert (R[ib > jb] == 0).all()                         # R upper triangular
+    assert np.linalg.norm(Q.T @ sysr.A @ Q - H) <= tol * np.linalg.norm(sysr.A)
+    assert np.linalg.norm(Q.T @ sysr.B - R) <= tol * np.linalg.norm(sysr.B)
+    assert np.linalg.norm(sysr.C @ Q - Ct) <= tol * np.linalg.norm(sysr.C)
+
+
+def _sign_normalize_hess(H, sub):
+    """D H D with D = diag(+-1) making the sub-th subdiagonal nonnegative, D[0] = +1."""
+    n = H.shape[0]
+    d = np.ones(n)
+    for i in range(sub, n):
+        if H[i, i - sub] * d[i - sub] < 0:
+            d[i] = -1.0
+    return d[:, None] * H * d[None, :]
+
+
+def test_reduce_m1_is_textbook_hessenberg(ora):
+    """For m = 1 the form is the classic Hessenberg reduction with Q e1 ~ b: by the
+    implicit-Q theorem it equals LAPACK's (scipy.linalg.hessenberg) after fixing
+    signs, starting from any orthogonal Q0 with first column b / ||b||."""
+    n = 24
+    sysr = W.random_system(n, 1, 2, seed=21)
+    H, R, Ct, Q = ora.reduce(sysr.A, sysr.B, sysr.C, want_q=True)
+    Q0, _ = np.linalg.qr(np.hstack([sysr.B, np.eye(n)[:, : n - 1]]))
+    H2 = scipy.linalg.hessenberg(Q0.T @ sysr.A @ Q0)
+    assert abs(abs(R[0, 0]) - np.linalg.norm(sysr.B)) < 1e-13 * np.linalg.norm(sysr.B)
+    Hn = _sign_normalize_hess(H, 1)
+    H2n = _sign_normalize_hess(H2, 1)
+    # fix the sign of the first basis vector, then everything follows
+    assert relerr(Hn, H2n) < 1e-12
+
+
+@pytest.mark.parametrize("n,m", [(12, 3), (10, 2), (8, 4)])
+def test_reduce_spans_block_krylov(ora, n, m):
+    """Q(:, 1:k m) is the orthonormal basis of [B, AB, ..., A^{k-1} B] (block-Krylov
+    uniqueness of the controller-Hessenberg form), up to column signs."""
+    sysr = W.random_system(n, m, 1, seed=31 + n)
+    H, R, Ct, Q = ora.reduce(sysr.A, sysr.B, sysr.C, want_q=True)
+    blocks = [sysr.B]
+    while sum(b.shape[1] for b in blocks) < n:
+        blocks.append(sysr.A @ blocks[-1])
+    K = np.hstack(blocks)[:, :n]
+    QK, RK = np.linalg.qr(K)
+    d = np.sign(np.sum(QK * Q, axis=0))
+    assert relerr(Q * d[None, :], QK) < 1e-8
+
+
+# --------------------------------------------------------------------------
+# reduced_solve (tier 2) and coordinate invariance
+# --------------------------------------------------------------------------
+
+def _random_mhess(n, m, seed, den=8):
+    rng = np.random.default_rng(seed)
+    Hn = rng.integers(-9, 10, (n, n))
+    i, j = np.indices((n, n))
+    Hn[i > j + m] = 0
+    Rn = rng.integers(-9, 10, (n, m))
+    ib, jb = np.indices((n, m))
+    Rn[ib > jb] = 0
+    return Hn, Rn
+
+
+@pytest.mark.parametrize("n,m,seed", [(4, 1, 1), (6, 2, 2), (8, 3, 3), (8, 8, 4), (7, 5, 5)])
+def test_reduced_solve_matches_exact_rational(ora, n, m, seed):
+    den = 8
+    Hn, Rn = _random_mhess(n, m, seed, den)
+    sig = (3, -5)
+    Xh, st, _ = ora.reduced_solve(Hn / den, Rn / den, np.zeros((1, n)), [complex(*sig) / den])
+    Xe = exact.solve(exact.shifted(Hn, den, sig), exact.real_matrix(Rn, den))
+    Xe = np.array([[exact.to_complex(z) for z in row] for row in Xe])
+    assert st[0] == 0
+    assert relerr(Xh[0], Xe) < 1e-12
+
+
+def test_reduced_solve_exact_singular_shift(ora):
+    n, m = 6, 2
+    rng = np.random.default_rng(5)
+    H = np.triu(rng.standard_normal((n, n)))
+    R = np.triu(rng.standard_normal((n, m)))
+    Xh, st, _ = ora.reduced_solve(H, R, np.ones((1, n)), [H[2, 2] + 0j, 0.5j])
+    assert st[0] == ora.STATUS_SINGULAR and st[1] == ora.STATUS_OK
+
+
+@pytest.mark.parametrize("n,m,p", [(60, 1, 1), (60, 4, 3), (45, 9, 2), (16, 16, 4)])
+def test_reduced_solve_equals_dense_in_original_coordinates(ora, n, m, p):
+    sysr = W.random_system(n, m, p, seed=200 + n + m)
+    sig = np.concatenate([W.imag_axis_logspace(-2, 2, 5), [-2.1 + 0.3j, -1.0 - 0.5j]])
+    X, st = ora.dense_solve(sysr.A, sysr.B, sig)
+    H, R, Ct, Q = ora.reduce(sysr.A, sysr.B, sysr.C, want_q=True)
+    Xh, st2, _ = ora.reduced_solve(H, R, Ct, sig, want="xhat")
+    G2, st3, _ = ora.reduced_solve(H, R, Ct, sig, want="g")
+    G = ora.transfer(sysr.C, X)
+    for j in range(len(sig)):
+        assert relerr(Q @ Xh[j], X[j]) < 1e-11
+        assert relerr(G2[j], G[j]) < 1e-11
+
+
+def test_transfer_function_diagonal_residues(ora):
+    """G(s) = C (sI - A)^{-1} B = sum_i C(:, i) B(i, :) / (s - a_i) for diagonal A;
+    the reduced path's -Ct Xhat must reproduce it."""
+    n, m, p = 30, 3, 2
+    a, sysd = W.diagonal_system(n, m, p, seed=41)
+    H, R, Ct, _ = ora.reduce(sysd.A, sysd.B, sysd.C)
+    sig = W.imag_axis_logspace(-2, 2, 11)
+    G, st, _ = ora.reduced_solve(H, R, Ct, sig, want="g")
+    for j, s in enumerate(sig):
+        tf = sum(np.outer(sysd.C[:, i], sysd.B[i, :]) / (s - a[i]) for i in range(n))
+        assert relerr(-G[j], tf) < 1e-12
+
+
+def test_transfer_function_block_diagonal_poles(ora):
+    """2x2 blocks [[alpha, beta], [-beta, alpha]] have poles alpha +- i beta with
+    eigenvectors [1, +-i]; G(s) = sum over poles of residue / (s - lambda)."""
+    nblk, m, p = 12, 2, 3
+    alpha, beta, sysb = W.block_diagonal_system(nblk, m, p, seed=42)
+    H, R, Ct, _ = ora.reduce(sysb.A, sysb.B, sysb.C)
+    sig = np.concatenate([W.imag_axis_logspace(-1, 1, 7), [0.3 - 0.2j]])
+    G, st, _ = ora.reduced_solve(H, R, Ct, sig, want="g")
+    Gd, _ = ora.dense_solve(sysb.A, sysb.B, sig)
+    for j, s in enumerate(sig):
+        tf = np.zeros((p, m), dtype=complex)
+        for k in range(nblk):
+            Ck = sysb.C[:, 2 * k:2 * k + 2]
+            Bk = sysb.B[2 * k:2 * k + 2, :]
+            for sgn in (+1, -1):
+                lam = alpha[k] + sgn * 1j * beta[k]
+                v = np.array([1.0, sgn * 1j])            # right eigenvector
+                w = np.array([0.5, -sgn * 0.5j])         # left eigenvector, w v = 1
+                tf += np.outer(Ck @ v, w @ Bk) / (s - lam)
+        assert relerr(-G[j], tf) < 1e-12
+        assert relerr(-sysb.C @ Gd[j], tf) < 1e-12
+
+
+def test_reduced_solve_conjugate_symmetry_and_sigma_zero(ora):
+    sysr = W.random_system(40, 3, 2, seed=51)
+    H, R, Ct, Q = ora.reduce(sysr.A, sysr.B, sysr.C, want_q=True)
+    s = 0.4 + 0.9j
+    Xh, _, _ = ora.reduced_solve(H, R, Ct, [s, np.conj(s), 0.0])
+    assert relerr(Xh[1], np.conj(Xh[0])) < 1e-13
+    assert relerr(Q @ Xh[2], np.linalg.solve(sysr.A, sysr.B)) < 1e-12
+
+
+def test_hager_condition_estimate_is_tight_lower_bound(ora):
+    n, m = 40, 2
+    sysr = W.random_system(n, m, 1, seed=61)
+    H, R, Ct, _ = ora.reduce(sysr.A, sysr.B, sysr.C)
+    sig = np.array([-2.0 + 0.1j, 1j, -1.5 - 0.4j])
+    _, _, c1 = ora.reduced_solve(H, R, Ct, sig, cond=True)
+    for j, s in enumerate(sig):
+        M = H - s * np.eye(n)
+        k1 = np.linalg.norm(M, 1) * np.linalg.norm(np.linalg.inv(M), 1)
+        assert c1[j] <= k1 * (1 + 1e-10)
+        assert c1[j] >= k1 / 10
