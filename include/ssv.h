@@ -1,0 +1,155 @@
+/*
+ * ssv.h -- C ABI of the GB300 shifted-system solver.
+ *
+ * Solves (A - sigma_j I) X_j = B for many complex shifts sigma_j and m
+ * right-hand sides, the problem of Bosner, Bujanovic and Drmac, "Parallel
+ * solver for shifted systems in a hybrid CPU-GPU framework" (Sec. 1), by
+ *   (1) one reduction of (A, B, C) to controller-Hessenberg form
+ *       (Algorithm 1, Sec. 2): H = Q^T A Q upper m-Hessenberg
+ *       (H(i,j) = 0 for i > j + m), R = Q^T B upper triangular, Ct = C Q;
+ *   (2) for every shift, the blocked elimination of the m subdiagonals of
+ *       H - sigma I from the bottom up with a sliding window of n_b + m
+ *       columns (Sec. 3.1, Algorithm 8), back substitution against R(1:m,1:m),
+ *       and optionally G = Ct Xhat.
+ *
+ * Conventions
+ *   - All matrices are column-major.  Leading dimensions are in elements.
+ *   - Complex arrays are interleaved (re, im) doubles, the layout of
+ *     complex128 / cuDoubleComplex; their leading dimension counts complex
+ *     elements.
+ *   - Every pointer named "device" must point to memory of the current CUDA
+ *     device; "host" pointers to host memory.  All work is enqueued on the
+ *     given stream (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream) and is stream-ordered: inputs must stay valid until the stream
+ *     passes the call, outputs are valid once it does.
+ *   - Return value 0 = success, negative = failure (SSV_E*); no call throws,
+ *     traps or aborts.  ssv_strerror() names a code.  After SSV_ECUDA the
+ *     CUDA error is also retrievable with ssv_last_cuda_error().
+ *   - Per-shift outcomes are reported in a device int array (SSV_SHIFT_*).
+ */
+#ifndef SSV_H
+#define SSV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define SSV_OK 0
+#define SSV_EINVAL (-1)   /* bad argument (size, pointer, leading dimension, option) */
+#define SSV_ENOMEM (-2)   /* device allocation failed */
+#define SSV_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define SSV_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define SSV_ENOTSUP (-5)  /* option combination not supported */
+
+/* ---- per-shift status (device int array, one entry per shift) --------- */
+#define SSV_SHIFT_OK 0
+#define SSV_SHIFT_SINGULAR 1      /* an exactly zero pivot: H - sigma I is singular */
+#define SSV_SHIFT_NOT_CONVERGED 2 /* refinement stopped above the tolerance */
+#define SSV_SHIFT_NONFINITE 3     /* a NaN / Inf appeared */
+
+/* ---- options ----------------------------------------------------------- */
+#define SSV_FP64 0  /* every step in double / complex128 */
+#define SSV_MIXED 1 /* complex64 elimination + FP64-accurate refinement */
+
+#define SSV_G 0    /* out(p x m) = C X = Ct Xhat                             */
+#define SSV_TF 1   /* out(p x m) = C (sigma I - A)^{-1} B = -Ct Xhat (Sec. 2) */
+#define SSV_XHAT 2 /* out(n x m) = Xhat = (H - sigma I)^{-1} R                */
+#define SSV_X 3    /* out(n x m) = X = Q Xhat = (A - sigma I)^{-1} B          */
+
+typedef struct ssv_opts {
+  int precision;           /* SSV_FP64 or SSV_MIXED */
+  int mode;                /* SSV_G, SSV_TF, SSV_XHAT, SSV_X */
+  int nb;                  /* rows per elimination block n_b; 0 = default */
+  int tile;                /* shifts per thread block; 0 = default */
+  int max_refine;          /* SSV_MIXED: maximum refinement sweeps */
+  double tol;              /* SSV_MIXED: target normwise backward error */
+} ssv_opts;
+
+typedef struct ssv_handle_s* ssv_handle;
+
+/* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 6,
+ * tol = 1e-13. */
+void ssv_default_opts(ssv_opts* o);
+
+/*
+ * ssv_reduce -- controller-Hessenberg reduction (Algorithm 1, Sec. 2).
+ *   n >= 1, 1 <= m <= n, p >= 0.
+ *   A (device) n x n double, lda >= n;  B (device) n x m double, ldb >= n;
+ *   C (device) p x n double, ldc >= max(1, p) (may be NULL when p == 0).
+ * A, B and C are read only.  On success *out receives a handle that owns
+ * device copies of H (n x n), R (n x m), Ct (p x n) and the Householder
+ * vectors of Q, all FP64.  The reduction runs entirely on the GPU in FP64.
+ * Errors: SSV_EINVAL (sizes / pointers), SSV_ENOMEM, SSV_ECUDA; *out is then
+ * left NULL.
+ */
+int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double* B,
+               long long ldb, const double* C, long long ldc, void* stream, ssv_handle* out);
+
+/*
+ * ssv_solve -- the batched shifted m-Hessenberg solve (Sec. 3, Algorithm 8).
+ *   s >= 0 shifts, shifts (device) = s interleaved complex doubles.
+ *   o: options (NULL = defaults).
+ *   out (device, complex): for SSV_G / SSV_TF a p x (s*m) matrix with
+ *     ldo >= max(1, p); block j (columns j*m .. j*m+m-1) is G(sigma_j)
+ *     (the layout of Algorithm 8's output).  For SSV_XHAT / SSV_X an
+ *     n x (s*m) matrix with ldo >= n.
+ *   status (device, may be NULL): s ints, SSV_SHIFT_*.
+ *   resid (device, may be NULL): s doubles, the normwise backward error
+ *     ||(H - sigma I) Xhat - R||_F / (||H - sigma I||_F ||Xhat||_F + ||R||_F)
+ *     of each shift's computed Xhat.
+ * The handle is read only; concurrent calls on one handle from different
+ * streams are safe (each call allocates its own stream-ordered scratch).
+ * Errors: SSV_EINVAL, SSV_ENOTSUP, SSV_ENOMEM, SSV_ECUDA.
+ */
+int ssv_solve(ssv_handle h, int s, const double* shifts, const ssv_opts* o, double* out,
+              long long ldo, int* status, double* resid, void* stream);
+
+/*
+ * ssv_apply_q -- X = Q Xhat (Sec. 2: X = Q Xhat in original coordinates).
+ *   Xhat (device, complex) n x ncols, ldx >= n; X (device, complex) n x ncols,
+ *   ldX >= n.  X may equal Xhat (in place).
+ */
+int ssv_apply_q(ssv_handle h, int ncols, const double* Xhat, long long ldx, double* X,
+                long long ldX, void* stream);
+
+/*
+ * ssv_get_reduced -- copy the reduced triple out of the handle (device
+ * destinations, FP64, column-major; entries of H below the m-th subdiagonal
+ * and of R below the diagonal are written as exact zeros).  Any destination
+ * may be NULL to skip it.  H: n x n (ldh >= n); R: n x m (ldr >= n);
+ * Ct: p x n (ldc >= max(1, p)).
+ */
+int ssv_get_reduced(ssv_handle h, double* H, long long ldh, double* R, long long ldr, double* Ct,
+                    long long ldc, void* stream);
+
+/* Dimensions of a handle.  Any output pointer may be NULL. */
+int ssv_dims(ssv_handle h, int* n, int* m, int* p);
+
+/*
+ * ssv_footprint -- device bytes one ssv_solve call with these sizes and
+ * options allocates for scratch (in addition to the handle), for admission
+ * control.  *bytes receives the count.
+ */
+int ssv_footprint(int n, int m, int p, int s, const ssv_opts* o, size_t* bytes);
+
+/* Bytes the handle of an (n, m, p) system keeps on the device. */
+int ssv_handle_bytes(int n, int m, int p, size_t* bytes);
+
+/* Release a handle (stream-ordered on the stream given to ssv_reduce after a
+ * device synchronisation of that stream).  NULL is ignored. */
+void ssv_destroy(ssv_handle h);
+
+/* Static string naming a return code. */
+const char* ssv_strerror(int code);
+
+/* The last CUDA error code seen by this thread's calls (0 if none). */
+int ssv_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSV_H */

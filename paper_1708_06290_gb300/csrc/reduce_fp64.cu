@@ -1,0 +1,341 @@
+// Controller-Hessenberg reduction in FP64 on the GPU (Algorithm 1, Sec. 2).
+//
+// Step 1  QR of B with Householder reflectors (one per column of B).
+// Step 2  each B-reflector applied to A from both sides and to C from the right.
+// Step 3  for column j, a reflector acting on rows j+m .. n-1 annihilates
+//         A(j+m+1 : n-1, j); applied from the left to the trailing columns,
+//         from the right to all rows of A and to C (Step 4, C <- C Q_A).
+//
+// The reflector H = I - tau v v^T with v(0) = 1 is generated in the
+// annihilated column itself: beta is stored at the top and v(1:) below it,
+// as LAPACK stores reflectors, so Q can be applied later (ssv_apply_q).
+// The solver reads only the structural part of H (rows <= column + m).
+//
+// Every kernel is stream-ordered; tau never leaves the device.
+#include <algorithm>
+
+#include "ssv_internal.cuh"
+
+namespace ssv {
+
+namespace {
+
+constexpr int kHouseThreads = 1024;
+
+// x = [alpha; x2] (len entries, contiguous).  Computes beta = -sign(alpha)||x||,
+// tau = (beta - alpha)/beta, scales x2 by 1/(alpha - beta), stores beta in x[0].
+// tau = 0 (identity) when x2 == 0.
+__global__ void __launch_bounds__(kHouseThreads) house_kernel(double* __restrict__ x, int len,
+                                                              double* __restrict__ tau_out) {
+  __shared__ double red[kHouseThreads / 32];
+  __shared__ double s_scal;
+  double ss = 0.0;
+  for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) ss = fma(x[i], x[i], ss);
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+      double alpha = x[0];
+      double tau = 0.0, scal = 0.0;
+      if (len > 1 && v != 0.0) {
+        double nrm = sqrt(fma(alpha, alpha, v));
+        double beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+        x[0] = beta;
+      }
+      *tau_out = tau;
+      s_scal = scal;
+    }
+  }
+  __syncthreads();
+  double scal = s_scal;
+  if (scal != 0.0)
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] *= scal;
+}
+
+// Left application to columns [c0, c1) of a (ld), rows r0 .. r0+len-1:
+// w = v^T a(:, c), a(:, c) -= tau v w.  v(0) = 1, v(1:) = vsrc[1:].
+// One warp per column.
+__global__ void __launch_bounds__(256) apply_left_kernel(double* __restrict__ a, long long ld,
+                                                         int r0, int len, int c0, int c1,
+                                                         const double* __restrict__ vsrc,
+                                                         const double* __restrict__ tau_p) {
+  double tau = *tau_p;
+  if (tau == 0.0) return;
+  int lane = threadIdx.x & 31;
+  int col = c0 + (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (col >= c1) return;
+  double* x = a + (size_t)col * ld + r0;
+  double dot = 0.0;
+  for (int i = lane; i < len; i += 32) {
+    double v = i == 0 ? 1.0 : vsrc[i];
+    dot = fma(v, x[i], dot);
+  }
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  double w = tau * dot;
+  for (int i = lane; i < len; i += 32) {
+    double v = i == 0 ? 1.0 : vsrc[i];
+    x[i] = fma(-v, w, x[i]);
+  }
+}
+
+constexpr int kRightRows = 128;  // rows per CTA
+constexpr int kRightCols = 128;  // columns per chunk
+
+// Right application, pass 1: partial dot products
+// part[chunk * nr + i] = sum_{j in chunk} a(i, c0 + j) v_j.
+__global__ void __launch_bounds__(kRightRows) apply_right_dot_kernel(
+    const double* __restrict__ a, long long ld, int nr, int c0, int len,
+    const double* __restrict__ vsrc, const double* __restrict__ tau_p, double* __restrict__ part) {
+  if (*tau_p == 0.0) return;
+  int i = blockIdx.x * kRightRows + threadIdx.x;
+  int j0 = blockIdx.y * kRightCols, j1 = min(len, j0 + kRightCols);
+  __shared__ double vs[kRightCols];
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vs[j - j0] = j == 0 ? 1.0 : vsrc[j];
+  __syncthreads();
+  if (i >= nr) return;
+  const double* row = a + i + (size_t)c0 * ld;
+  double acc = 0.0;
+  for (int j = j0; j < j1; ++j) acc = fma(row[(size_t)j * ld], vs[j - j0], acc);
+  part[(size_t)blockIdx.y * nr + i] = acc;
+}
+
+// Right application, pass 2: w_i = tau * sum over chunks (fixed order), then
+// a(i, c0 + j) -= w_i v_j for the CTA's column chunk.
+__global__ void __launch_bounds__(kRightRows) apply_right_update_kernel(
+    double* __restrict__ a, long long ld, int nr, int c0, int len, int nchunk,
+    const double* __restrict__ vsrc, const double* __restrict__ tau_p,
+    const double* __restrict__ part) {
+  double tau = *tau_p;
+  if (tau == 0.0) return;
+  int i = blockIdx.x * kRightRows + threadIdx.x;
+  int j0 = blockIdx.y * kRightCols, j1 = min(len, j0 + kRightCols);
+  __shared__ double vs[kRightCols];
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vs[j - j0] = j == 0 ? 1.0 : vsrc[j];
+  __syncthreads();
+  if (i >= nr) return;
+  double w = 0.0;
+  for (int c = 0; c < nchunk; ++c) w += part[(size_t)c * nr + i];
+  w *= tau;
+  double* row = a + i + (size_t)c0 * ld;
+  for (int j = j0; j < j1; ++j) row[(size_t)j * ld] = fma(-w, vs[j - j0], row[(size_t)j * ld]);
+}
+
+// Frobenius norm^2 and trace of the structural part of H.
+__global__ void hnorm_kernel(const double* __restrict__ H, int n, int m, double* __restrict__ out) {
+  __shared__ double red[2][8];
+  double s2 = 0.0, tr = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    if (i <= j + m) {
+      double v = H[idx];
+      s2 = fma(v, v, s2);
+      if (i == j) tr += v;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    tr += __shfl_down_sync(0xffffffffu, tr, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s2;
+    red[1][threadIdx.x >> 5] = tr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
+    atomicAdd(out, a);
+    atomicAdd(out + 1, b);
+  }
+}
+
+// Left application of one reflector to complex columns (for X = Q Xhat).
+__global__ void __launch_bounds__(256) apply_left_complex_kernel(
+    cd* __restrict__ X, long long ldx, int r0, int len, int ncols, const double* __restrict__ vsrc,
+    const double* __restrict__ tau_p) {
+  double tau = *tau_p;
+  if (tau == 0.0) return;
+  int lane = threadIdx.x & 31;
+  int col = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (col >= ncols) return;
+  cd* x = X + (size_t)col * ldx + r0;
+  double dr = 0.0, di = 0.0;
+  for (int i = lane; i < len; i += 32) {
+    double v = i == 0 ? 1.0 : vsrc[i];
+    dr = fma(v, x[i].x, dr);
+    di = fma(v, x[i].y, di);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dr += __shfl_xor_sync(0xffffffffu, dr, o);
+    di += __shfl_xor_sync(0xffffffffu, di, o);
+  }
+  dr *= tau;
+  di *= tau;
+  for (int i = lane; i < len; i += 32) {
+    double v = i == 0 ? 1.0 : vsrc[i];
+    x[i].x = fma(-v, dr, x[i].x);
+    x[i].y = fma(-v, di, x[i].y);
+  }
+}
+
+__global__ void copy_masked_kernel(const double* __restrict__ src, long long lds, int rows, int cols,
+                                   int band, double* __restrict__ dst, long long ldd) {
+  // dst(i, j) = src(i, j) if i <= j + band else 0
+  long long total = (long long)rows * cols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx % rows), j = (int)(idx / rows);
+    dst[i + (size_t)j * ldd] = (i <= j + band) ? src[i + (size_t)j * lds] : 0.0;
+  }
+}
+
+__global__ void copy_cd_kernel(const cd* __restrict__ src, long long lds, int rows, int cols,
+                               cd* __restrict__ dst, long long ldd) {
+  long long total = (long long)rows * cols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx % rows), j = (int)(idx / rows);
+    dst[i + (size_t)j * ldd] = src[i + (size_t)j * lds];
+  }
+}
+
+struct RightWork {
+  double* part;
+  size_t cap;  // doubles
+};
+
+// One Householder reflector on the left of rows [r0, r0+len) of a's columns
+// [c0, c1), where v lives at vsrc (vsrc[0] ignored, treated as 1).
+inline cudaError_t launch_left(double* a, long long ld, int r0, int len, int c0, int c1,
+                               const double* vsrc, const double* tau, cudaStream_t st) {
+  if (c1 <= c0 || len <= 1) return cudaSuccess;
+  long long warps = c1 - c0;
+  int blocks = (int)((warps * 32 + 255) / 256);
+  apply_left_kernel<<<blocks, 256, 0, st>>>(a, ld, r0, len, c0, c1, vsrc, tau);
+  return cudaGetLastError();
+}
+
+inline cudaError_t launch_right(double* a, long long ld, int nr, int c0, int len,
+                                const double* vsrc, const double* tau, double* part,
+                                cudaStream_t st) {
+  if (nr <= 0 || len <= 1) return cudaSuccess;
+  int nchunk = (len + kRightCols - 1) / kRightCols;
+  dim3 grid((nr + kRightRows - 1) / kRightRows, nchunk);
+  apply_right_dot_kernel<<<grid, kRightRows, 0, st>>>(a, ld, nr, c0, len, vsrc, tau, part);
+  apply_right_update_kernel<<<grid, kRightRows, 0, st>>>(a, ld, nr, c0, len, nchunk, vsrc, tau,
+                                                         part);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long long ldb,
+                const double* C, long long ldc, cudaStream_t st) {
+  const int n = h->n, m = h->m, p = h->p;
+  const int ldct = p > 0 ? p : 1;
+  SSV_CUDA_TRY(cudaMemcpy2DAsync(h->H, sizeof(double) * n, A, sizeof(double) * lda,
+                                 sizeof(double) * n, n, cudaMemcpyDeviceToDevice, st));
+  SSV_CUDA_TRY(cudaMemcpy2DAsync(h->R, sizeof(double) * n, B, sizeof(double) * ldb,
+                                 sizeof(double) * n, m, cudaMemcpyDeviceToDevice, st));
+  if (p > 0)
+    SSV_CUDA_TRY(cudaMemcpy2DAsync(h->Ct, sizeof(double) * ldct, C, sizeof(double) * ldc,
+                                   sizeof(double) * p, n, cudaMemcpyDeviceToDevice, st));
+  int nchunk_max = (n + kRightCols - 1) / kRightCols;
+  double* part = nullptr;
+  SSV_CUDA_TRY(
+      cudaMallocAsync((void**)&part, sizeof(double) * (size_t)nchunk_max * std::max(n, p), st));
+
+  int rc = SSV_OK;
+  auto chk = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == SSV_OK) {
+      set_cuda_error(e);
+      rc = SSV_ECUDA;
+    }
+  };
+  // Steps 1-2: QR of B, similarity with Q_B, C <- C Q_B.
+  h->kb = std::min(m, n - 1);
+  for (int i = 0; i < h->kb && rc == SSV_OK; ++i) {
+    int len = n - i;
+    double* x = h->R + i + (size_t)i * n;
+    house_kernel<<<1, kHouseThreads, 0, st>>>(x, len, h->tauB + i);
+    chk(cudaGetLastError());
+    chk(launch_left(h->R, n, i, len, i + 1, m, x, h->tauB + i, st));
+    chk(launch_left(h->H, n, i, len, 0, n, x, h->tauB + i, st));
+    chk(launch_right(h->H, n, n, i, len, x, h->tauB + i, part, st));
+    chk(launch_right(h->Ct, ldct, p, i, len, x, h->tauB + i, part, st));
+  }
+  // Steps 3-4: m-Hessenberg reduction of A, C <- C Q_A.
+  h->ka = std::max(0, n - m - 1);
+  for (int j = 0; j < h->ka && rc == SSV_OK; ++j) {
+    int r0 = j + m, len = n - r0;
+    double* x = h->H + r0 + (size_t)j * n;
+    house_kernel<<<1, kHouseThreads, 0, st>>>(x, len, h->tauA + j);
+    chk(cudaGetLastError());
+    chk(launch_left(h->H, n, r0, len, j + 1, n, x, h->tauA + j, st));
+    chk(launch_right(h->H, n, n, r0, len, x, h->tauA + j, part, st));
+    chk(launch_right(h->Ct, ldct, p, r0, len, x, h->tauA + j, part, st));
+  }
+  if (rc == SSV_OK) {
+    chk(cudaMemsetAsync(h->hnorm2, 0, 2 * sizeof(double), st));
+    hnorm_kernel<<<std::max(1, std::min(1024, (n * n + 255) / 256)), 256, 0, st>>>(h->H, n, m,
+                                                                                  h->hnorm2);
+    chk(cudaGetLastError());
+  }
+  chk(cudaFreeAsync(part, st));
+  return rc;
+}
+
+int apply_q_fp64(const Handle* h, int ncols, const double* Xhat, long long ldx, double* X,
+                 long long ldX, cudaStream_t st) {
+  const int n = h->n, m = h->m;
+  if (ncols == 0) return SSV_OK;
+  cd* Xc = reinterpret_cast<cd*>(X);
+  if (X != Xhat) {
+    int blocks = (int)std::min<long long>(4096, ((long long)n * ncols + 255) / 256);
+    copy_cd_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const cd*>(Xhat), ldx, n, ncols, Xc,
+                                           ldX);
+    SSV_CUDA_TRY(cudaGetLastError());
+  }
+  int blocks = (int)(((long long)ncols * 32 + 255) / 256);
+  // Q = Q_B Q_A = HB_0 .. HB_{kb-1} HA_0 .. HA_{ka-1}: apply the last reflector first.
+  for (int j = h->ka - 1; j >= 0; --j) {
+    int r0 = j + m, len = n - r0;
+    apply_left_complex_kernel<<<blocks, 256, 0, st>>>(Xc, ldX, r0, len, ncols,
+                                                      h->H + r0 + (size_t)j * n, h->tauA + j);
+  }
+  for (int i = h->kb - 1; i >= 0; --i) {
+    int len = n - i;
+    apply_left_complex_kernel<<<blocks, 256, 0, st>>>(Xc, ldX, i, len, ncols,
+                                                      h->R + i + (size_t)i * n, h->tauB + i);
+  }
+  SSV_CUDA_TRY(cudaGetLastError());
+  return SSV_OK;
+}
+
+int get_reduced(const Handle* h, double* H, long long ldh, double* R, long long ldr, double* Ct,
+                long long ldc, cudaStream_t st) {
+  const int n = h->n, m = h->m, p = h->p;
+  if (H) {
+    int blocks = (int)std::min<long long>(4096, ((long long)n * n + 255) / 256);
+    copy_masked_kernel<<<blocks, 256, 0, st>>>(h->H, n, n, n, m, H, ldh);
+    SSV_CUDA_TRY(cudaGetLastError());
+  }
+  if (R) {
+    int blocks = (int)std::min<long long>(4096, ((long long)n * m + 255) / 256);
+    copy_masked_kernel<<<blocks, 256, 0, st>>>(h->R, n, n, m, 0, R, ldr);
+    SSV_CUDA_TRY(cudaGetLastError());
+  }
+  if (Ct && p > 0) {
+    SSV_CUDA_TRY(cudaMemcpy2DAsync(Ct, sizeof(double) * ldc, h->Ct, sizeof(double) * p,
+                                   sizeof(double) * p, n, cudaMemcpyDeviceToDevice, st));
+  }
+  return SSV_OK;
+}
+
+}  // namespace ssv

@@ -1,0 +1,478 @@
+// Persistent shift-batched solver for (H - sigma I) Xhat = R, FP64.
+//
+// The method is the blocked bottom-up elimination of Sec. 3.1 / Algorithm 8:
+// a sliding window of the columns of [Ct; H - sigma I] moves from the last
+// column to the first.  Its "live" part Z2 (m columns, specific to the shift)
+// is combined with n_b fresh columns Z1 of the original [Ct; H] (shared by all
+// shifts) on each block of n_b rows:
+//   1. the n_b x (n_b + m) window block is triangularised from its bottom row
+//      up; in each row the pivot is the candidate column (m live + 1 fresh)
+//      of largest |re| + |im|, and the other m candidates are reduced by a
+//      multiple of it (Gauss transformations from the right).  Only the
+//      coefficients P (n_b + m) x m expressing the m surviving columns in terms
+//      of [Z1 | Z2] are kept (Sec. 3.1: "only the first m columns of P* are
+//      needed");
+//   2. the rows above the block are updated once:
+//      Z2 <- Z1 P(1:n_b, :) + Z2 P(n_b+1:, :) - sigma E P(1:min(m,n_b), :),
+//      the last term being the shifted diagonal of the fresh columns that
+//      lies above the block (Algorithm 8, diagonal correction);
+//   3. the window slides up by n_b rows.
+// When m rows remain, the live block W = [Wc; Wm] (p + m rows) gives
+// Y = Wm^{-1} R(1:m, 1:m) and G = Wc Y (Algorithm 8, final loop; here on the
+// GPU).  For Xhat the window also carries the rows of the accumulated column
+// transformation T (the "Q*" rows of Sec. 3.4), Xhat = T(:, live) Y.
+//
+// Differences from the paper: Gauss transformations with pivoting instead of
+// Givens rotations; each thread block owns one shift at a time for the whole
+// sweep (no grid-wide phases); the final m x m solve runs on the GPU.
+#include <algorithm>
+
+#include "ssv_internal.cuh"
+
+namespace ssv {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kNB = 64;  // maximum rows per block (runtime nb <= kNB)
+
+// Shared memory per thread block:
+//   cand[slot * kNB + t]       rows t of the window block, slot in [0, m]
+//   coef[c * (MAXM + 1) + slot] coefficient of window column c (fresh c < kNB,
+//                               old live kNB + q) in candidate column `slot`
+//   Wm, lmul, Yb               final m x m solve
+template <int MAXM>
+struct Layout {
+  static constexpr int kSlots = MAXM + 2;
+  static constexpr int kCoefRows = kNB + MAXM;
+  static constexpr size_t cand_elems = (size_t)kSlots * kNB;
+  static constexpr size_t coef_elems = (size_t)kCoefRows * kSlots;
+  static constexpr size_t bytes =
+      (cand_elems + coef_elems + 3 * MAXM * MAXM + 2 * MAXM + 4) * sizeof(cd) + 64;
+};
+
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
+    int n, int m, int p, int nb, const double* __restrict__ H, const double* __restrict__ Ct,
+    int ldct, const double* __restrict__ R, int s, const cd* __restrict__ shifts, int mode,
+    cd* __restrict__ scratch, size_t slot_stride, cd* __restrict__ out, long long ldo,
+    int* __restrict__ status, cd* __restrict__ xhat_copy, long long ldxc,
+    const double* __restrict__ hnorm) {
+  using L = Layout<MAXM>;
+  constexpr int S = L::kSlots;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cd* cand = reinterpret_cast<cd*>(smem_raw);
+  cd* coef = cand + L::cand_elems;
+  cd* Wm = coef + L::coef_elems;             // MAXM x (2 MAXM) augmented [Wm | R1]
+  cd* lmul = Wm + 2 * MAXM * MAXM;           // reflector v (MAXM + 2 slots) and tau
+  cd* Yb = lmul + (MAXM + 4);                // MAXM x MAXM solution
+  __shared__ int s_piv;
+  __shared__ int s_sing;
+
+  const int tid = threadIdx.x;
+  const int ldz = p + n;
+  const bool track_t = (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
+  cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
+  cd* ZT = Z2 + (size_t)ldz * m;  // n x m, valid when track_t
+
+  for (int sh = blockIdx.x; sh < s; sh += gridDim.x) {
+    const cd sigma = shifts[sh];
+    // ||H - sigma I||_F from ||H||_F^2 and trace(H); a finalized diagonal entry
+    // of magnitude <= n eps ||H - sigma I||_F marks the shift singular.
+    const double mnorm2 = fmax(hnorm[0] - 2.0 * sigma.x * hnorm[1] +
+                                   (double)n * (sigma.x * sigma.x + sigma.y * sigma.y), 0.0);
+    const double sing_tol = (double)n * 2.220446049250313e-16 * sqrt(mnorm2);
+    // ---- shift setup: Z2 = last m columns of [Ct; H] - sigma on the diagonal
+    for (long long idx = tid; idx < (long long)ldz * m; idx += kThreads) {
+      int i = (int)(idx % ldz), q = (int)(idx / ldz);
+      int j = n - m + q;
+      double v = i < p ? Ct[i + (size_t)j * ldct] : H[(i - p) + (size_t)j * n];
+      cd z = mkcd(v, 0.0);
+      if (i - p == j) z = csub(z, sigma);
+      Z2[idx] = z;
+    }
+    if (track_t) {
+      for (long long idx = tid; idx < (long long)n * m; idx += kThreads) {
+        int i = (int)(idx % n), q = (int)(idx / n);
+        ZT[idx] = mkcd(i == n - m + q ? 1.0 : 0.0, 0.0);
+      }
+    }
+    if (tid == 0) s_sing = 0;
+    __syncthreads();
+
+    int k = n;
+    while (k > m) {
+      const int nbe = min(nb, k - m);
+      const int r = p + k - nbe;        // rows of [Ct; M] above the block
+      const int j0 = k - m - nbe;       // first fresh column
+      // stage the live rows of the block and reset coefficients
+      for (int idx = tid; idx < m * nbe; idx += kThreads) {
+        int t = idx % nbe, q = idx / nbe;
+        cand[q * kNB + t] = Z2[(r + t) + (size_t)q * ldz];
+      }
+      // coefficients: identity on the old live columns, e_{nbe-1} for the
+      // fresh column F_{nbe-1} that enters slot m (slots m, m+1 alternate)
+      for (int idx = tid; idx < L::kCoefRows * S; idx += kThreads) {
+        int c = idx / S, slot = idx % S;
+        cd v = mkcd(0.0, 0.0);
+        if ((slot < m && c == kNB + slot) || (slot == m && c == nbe - 1)) v = mkcd(1.0, 0.0);
+        coef[idx] = v;
+      }
+      {
+        const int c = nbe - 1, jc = j0 + c;
+        for (int t = tid; t <= c; t += kThreads) {
+          cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
+          if (t == c - m) z = csub(z, sigma);
+          cand[m * kNB + t] = z;
+        }
+      }
+      __syncthreads();
+      for (int c = nbe - 1; c >= 0; --c) {
+        const int fs = m + ((nbe - 1 - c) & 1);  // slot holding F_c
+        const int fn = (fs == m) ? m + 1 : m;    // slot for F_{c-1}
+        // ---- reflector U = I - tau v v^H on the m + 1 candidates of row c
+        //      (survivors 0..m-1, fresh fs): x U = conj(alpha) e_fs, x = row c.
+        if (tid < 32) {
+          double rest2 = 0.0;  // sum of |x_q|^2 over the m survivors
+          for (int q = tid; q < m; q += 32) {
+            const cd x = cand[q * kNB + c];
+            rest2 = fma(x.x, x.x, fma(x.y, x.y, rest2));
+          }
+          for (int o = 16; o > 0; o >>= 1) rest2 += __shfl_xor_sync(0xffffffffu, rest2, o);
+          const cd xf = cand[fs * kNB + c];
+          const double af2 = fma(xf.x, xf.x, xf.y * xf.y);
+          const double af = sqrt(af2);
+          const double nrm2 = rest2 + af2;
+          const double nrm = sqrt(nrm2);
+          // y = conj(x); alpha = -exp(i arg y_fs) ||y||; v = y - alpha e_fs
+          cd ph = af > 0.0 ? mkcd(xf.x / af, -xf.y / af) : mkcd(1.0, 0.0);
+          const cd alpha = mkcd(-ph.x * nrm, -ph.y * nrm);
+          const bool trivial = !(rest2 > 0.0);
+          for (int q = tid; q <= m; q += 32) {
+            const int slot = q < m ? q : fs;
+            const cd x = cand[slot * kNB + c];
+            cd v = mkcd(x.x, -x.y);
+            if (slot == fs) v = csub(v, alpha);
+            lmul[slot] = v;
+          }
+          if (tid == 0) {
+            // ||v||^2 = 2 ||y||^2 + 2 |y_fs| ||y||
+            const double vv = 2.0 * nrm2 + 2.0 * af * nrm;
+            lmul[MAXM + 2].x = trivial ? 0.0 : 2.0 / vv;
+            if (nrm <= sing_tol) s_sing = 1;  // |R(row, row)| = ||x|| at working precision
+          }
+        }
+        __syncthreads();
+        const double tau = lmul[MAXM + 2].x;
+        // ---- apply to window rows 0..c-1 and the nonzero coefficient rows;
+        //      load F_{c-1} into slot fn meanwhile.
+        if (tau != 0.0) {
+          const int nrow = c;
+          const int ncoef = (nbe - c) + m;
+          for (int e = tid; e < nrow + ncoef; e += kThreads) {
+            cd* base;
+            int stride;
+            if (e < nrow) {
+              base = cand + e;
+              stride = kNB;
+            } else {
+              const int ee = e - nrow;
+              const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
+              base = coef + crow * S;
+              stride = 1;
+            }
+            cd w = mkcd(0.0, 0.0);
+            for (int q = 0; q <= m; ++q) {
+              const int slot = q < m ? q : fs;
+              w = cfma(base[slot * stride], lmul[slot], w);
+            }
+            w = mkcd(w.x * tau, w.y * tau);
+            for (int q = 0; q <= m; ++q) {
+              const int slot = q < m ? q : fs;
+              const cd vc = mkcd(lmul[slot].x, -lmul[slot].y);
+              base[slot * stride] = cfms(w, vc, base[slot * stride]);
+            }
+          }
+        }
+        if (c > 0) {
+          const int cn = c - 1, jc = j0 + cn;
+          for (int t = tid; t <= cn; t += kThreads) {
+            cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
+            if (t == cn - m) z = csub(z, sigma);
+            cand[fn * kNB + t] = z;
+          }
+          for (int crow = tid; crow < L::kCoefRows; crow += kThreads)
+            coef[crow * S + fn] = mkcd(crow == cn ? 1.0 : 0.0, 0.0);
+        }
+        __syncthreads();
+      }
+
+      // ---- update the rows above the block (and the T rows)
+      for (int i = tid; i < r; i += kThreads) {
+        cd acc[MAXM];
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
+        for (int c = 0; c < nbe; ++c) {
+          const int jc = j0 + c;
+          const double z = i < p ? Ct[i + (size_t)jc * ldct] : H[(i - p) + (size_t)jc * n];
+          const cd* cr = coef + c * S;
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q) {
+            if (q < m) {
+              cd w = cr[q];
+              acc[q].x = fma(z, w.x, acc[q].x);
+              acc[q].y = fma(z, w.y, acc[q].y);
+            }
+          }
+        }
+        for (int qq = 0; qq < m; ++qq) {
+          const cd zz = Z2[i + (size_t)qq * ldz];
+          const cd* cr = coef + (kNB + qq) * S;
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
+        }
+        const int cd_ = i - (r - m);  // diagonal correction of fresh column cd_
+        if (cd_ >= 0 && cd_ < min(m, nbe)) {
+          const cd* cr = coef + cd_ * S;
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            if (q < m) acc[q] = cfms(sigma, cr[q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q < m) Z2[i + (size_t)q * ldz] = acc[q];
+      }
+      if (track_t) {
+        // rows k-m .. n-1: ZT <- ZT P2 ; rows j0 .. j0+nbe-1: ZT = P1
+        const int lo = k - m;
+        for (int i = j0 + tid; i < n; i += kThreads) {
+          cd acc[MAXM];
+          if (i < lo) {
+            const cd* cr = coef + (i - j0) * S;
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) acc[q] = cr[q];
+          } else {
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
+            for (int qq = 0; qq < m; ++qq) {
+              const cd zz = ZT[i + (size_t)qq * n];
+              const cd* cr = coef + (kNB + qq) * S;
+#pragma unroll
+              for (int q = 0; q < MAXM; ++q)
+                if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            if (q < m) ZT[i + (size_t)q * n] = acc[q];
+        }
+      }
+      __syncthreads();
+      k -= nbe;
+    }
+
+    // ---- final m x m block: solve Wm Y = R(0:m, 0:m) by Gauss-Jordan with
+    // partial pivoting on the augmented [Wm | R1] (2m columns).
+    const int w2 = 2 * m;
+    for (int idx = tid; idx < m * w2; idx += kThreads) {
+      int i = idx % m, j = idx / m;
+      cd v;
+      if (j < m) v = Z2[(p + i) + (size_t)j * ldz];
+      else {
+        int jj = j - m;
+        v = mkcd(i <= jj ? R[i + (size_t)jj * n] : 0.0, 0.0);
+      }
+      Wm[i + j * MAXM] = v;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < m; ++kk) {
+      if (tid < 32) {
+        double best = -1.0;
+        int brow = kk;
+        for (int i = kk + tid; i < m; i += 32) {
+          double v = cabs1(Wm[i + kk * MAXM]);
+          if (v > best) { best = v; brow = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+          if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
+        }
+        if (tid == 0) {
+          s_piv = brow;
+          const cd pv = Wm[brow + kk * MAXM];
+          if (best == 0.0 || sqrt(pv.x * pv.x + pv.y * pv.y) <= sing_tol) s_sing = 1;
+        }
+      }
+      __syncthreads();
+      const int pr = s_piv;
+      if (pr != kk) {
+        for (int j = tid; j < w2; j += kThreads) {
+          cd a = Wm[kk + j * MAXM];
+          Wm[kk + j * MAXM] = Wm[pr + j * MAXM];
+          Wm[pr + j * MAXM] = a;
+        }
+      }
+      __syncthreads();
+      const cd d = Wm[kk + kk * MAXM];
+      const bool dz = (d.x == 0.0 && d.y == 0.0);
+      if (tid < m) lmul[tid] = (tid == kk || dz) ? mkcd(0.0, 0.0) : cdiv(Wm[tid + kk * MAXM], d);
+      __syncthreads();
+      for (int idx = tid; idx < m * w2; idx += kThreads) {
+        int i = idx % m, j = idx / m;
+        if (i != kk && j > kk) Wm[i + j * MAXM] = cfms(lmul[i], Wm[kk + j * MAXM], Wm[i + j * MAXM]);
+      }
+      __syncthreads();
+    }
+    // Y(i, q) = Wm(i, m+q) / Wm(i, i)
+    for (int idx = tid; idx < m * m; idx += kThreads) {
+      int i = idx % m, q = idx / m;
+      cd d = Wm[i + i * MAXM];
+      Yb[i + q * MAXM] = (d.x == 0.0 && d.y == 0.0) ? mkcd(0.0, 0.0) : cdiv(Wm[i + (m + q) * MAXM], d);
+    }
+    __syncthreads();
+    const bool sing = s_sing != 0;
+    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+    // ---- outputs
+    if (mode == SSV_G || mode == SSV_TF) {
+      const double sg = mode == SSV_TF ? -1.0 : 1.0;
+      cd* o = out + (size_t)sh * m * ldo;
+      for (int idx = tid; idx < p * m; idx += kThreads) {
+        int i = idx % p, q = idx / p;
+        cd acc = mkcd(0.0, 0.0);
+        for (int t = 0; t < m; ++t) acc = cfma(Z2[i + (size_t)t * ldz], Yb[t + q * MAXM], acc);
+        if (sing) acc = mkcd(nanv, nanv);
+        o[i + (size_t)q * ldo] = mkcd(sg * acc.x, sg * acc.y);
+      }
+    }
+    if (track_t) {
+      cd* o;
+      long long ld;
+      if (mode == SSV_XHAT || mode == SSV_X) {
+        o = out + (size_t)sh * m * ldo;
+        ld = ldo;
+      } else {
+        o = xhat_copy + (size_t)sh * m * ldxc;
+        ld = ldxc;
+      }
+      for (int idx = tid; idx < n * m; idx += kThreads) {
+        int i = idx % n, q = idx / n;
+        cd acc = mkcd(0.0, 0.0);
+        for (int t = 0; t < m; ++t) acc = cfma(ZT[i + (size_t)t * n], Yb[t + q * MAXM], acc);
+        if (sing) acc = mkcd(nanv, nanv);
+        o[i + (size_t)q * ld] = acc;
+      }
+    }
+    if (status != nullptr && tid == 0) status[sh] = sing ? SSV_SHIFT_SINGULAR : SSV_SHIFT_OK;
+    __syncthreads();
+  }
+}
+
+// Non-finite scan: status[sh] = NONFINITE if an output of an OK shift is not finite.
+__global__ void nonfinite_kernel(const cd* __restrict__ out, long long ldo, int rows, int m, int s,
+                                 int* __restrict__ status) {
+  int sh = blockIdx.x;
+  if (sh >= s) return;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const cd* o = out + (size_t)sh * m * ldo;
+  for (int idx = threadIdx.x; idx < rows * m; idx += blockDim.x) {
+    int i = idx % rows, q = idx / rows;
+    cd v = o[i + (size_t)q * ldo];
+    if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && bad && status[sh] == SSV_SHIFT_OK) status[sh] = SSV_SHIFT_NONFINITE;
+}
+
+template <int MAXM>
+int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode, double* out,
+                 long long ldo, int* status, cd* xhat_copy, long long ldxc, cudaStream_t st) {
+  using L = Layout<MAXM>;
+  const int n = h->n, m = h->m, p = h->p;
+  const bool track_t = (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
+  const size_t slot = (size_t)(p + n) * m + (track_t ? (size_t)n * m : 0);
+  int dev = 0;
+  SSV_CUDA_TRY(cudaGetDevice(&dev));
+  auto kern = solve_fp64_kernel<MAXM>;
+  SSV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+  int per_sm = 0;
+  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L::bytes));
+  per_sm = std::max(1, std::min(per_sm, 2));
+  int grid = std::min(s, num_sms() * per_sm);
+  cd* scratch = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(cd) * slot * grid, st));
+  kern<<<grid, kThreads, L::bytes, st>>>(n, m, p, nb, h->H, h->Ct, p > 0 ? p : 1, h->R, s,
+                                         reinterpret_cast<const cd*>(shifts), mode, scratch, slot,
+                                         reinterpret_cast<cd*>(out), ldo, status, xhat_copy, ldxc,
+                                         h->hnorm2);
+  cudaError_t e = cudaGetLastError();
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return SSV_ECUDA;
+  }
+  if (status != nullptr) {
+    int rows = (mode == SSV_G || mode == SSV_TF) ? p : n;
+    if (rows > 0) {
+      nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows, m, s, status);
+      SSV_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return SSV_OK;
+}
+
+}  // namespace
+
+int default_nb(int n, int m) {
+  (void)n;
+  (void)m;
+  return kNB;
+}
+
+size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) {
+  const bool track_t = (o->mode == SSV_XHAT || o->mode == SSV_X);
+  size_t slot = (size_t)(p + n) * m + (track_t ? (size_t)n * m : 0);
+  size_t grid = (size_t)std::min(s, num_sms() * 2);
+  return sizeof(cd) * slot * grid + 256;
+}
+
+int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
+               long long ldo, int* status, double* resid, cudaStream_t st) {
+  const int m = h->m;
+  int nb = o->nb > 0 ? o->nb : default_nb(h->n, m);
+  if (nb > kNB) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  cd* xcopy = nullptr;
+  long long ldxc = 0;
+  if (resid != nullptr && (o->mode == SSV_G || o->mode == SSV_TF)) {
+    ldxc = h->n;
+    SSV_CUDA_TRY(cudaMallocAsync((void**)&xcopy, sizeof(cd) * (size_t)h->n * m * s, st));
+  }
+  int rc;
+  if (m <= 1) rc = launch_solve<1>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+  else if (m <= 2) rc = launch_solve<2>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+  else if (m <= 4) rc = launch_solve<4>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+  else if (m <= 8) rc = launch_solve<8>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+  else if (m <= 16) rc = launch_solve<16>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+  else if (m <= 32) rc = launch_solve<32>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+  else rc = SSV_ENOTSUP;
+  if (rc == SSV_OK && resid != nullptr) {
+    const double* xh = xcopy ? reinterpret_cast<const double*>(xcopy) : out;
+    long long ldx = xcopy ? ldxc : ldo;
+    rc = backward_error_fp64(h, s, shifts, xh, ldx, resid, st);
+  }
+  if (xcopy) {
+    cudaError_t e = cudaFreeAsync(xcopy, st);
+    if (e != cudaSuccess && rc == SSV_OK) {
+      set_cuda_error(e);
+      rc = SSV_ECUDA;
+    }
+  }
+  return rc;
+}
+
+}  // namespace ssv

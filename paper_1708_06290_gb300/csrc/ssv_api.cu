@@ -1,0 +1,196 @@
+// C ABI entry points (include/ssv.h): argument checks, handle lifetime and
+// dispatch to the FP64 reduction and the solvers.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "ssv_internal.cuh"
+
+namespace ssv {
+
+static thread_local int g_last_cuda = 0;
+
+void set_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 132;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 132;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+static void free_handle_buffers(Handle* h) {
+  if (!h) return;
+  cudaFree(h->H);
+  cudaFree(h->R);
+  cudaFree(h->Ct);
+  cudaFree(h->tauB);
+  cudaFree(h->tauA);
+  cudaFree(h->hnorm2);
+}
+
+static size_t handle_bytes(int n, int m, int p) {
+  size_t b = sizeof(double) * ((size_t)n * n + (size_t)n * m + (size_t)(p > 0 ? p : 1) * n +
+                               (size_t)m + (size_t)n + 2);
+  return b;
+}
+
+static int check_opts(const ssv_opts* o) {
+  if (o->precision != SSV_FP64 && o->precision != SSV_MIXED) return SSV_EINVAL;
+  if (o->mode < SSV_G || o->mode > SSV_X) return SSV_EINVAL;
+  if (o->nb < 0 || o->tile < 0 || o->max_refine < 0 || !(o->tol >= 0.0)) return SSV_EINVAL;
+  return SSV_OK;
+}
+
+}  // namespace ssv
+
+using namespace ssv;
+
+extern "C" {
+
+void ssv_default_opts(ssv_opts* o) {
+  if (!o) return;
+  o->precision = SSV_FP64;
+  o->mode = SSV_G;
+  o->nb = 0;
+  o->tile = 0;
+  o->max_refine = 6;
+  o->tol = 1e-13;
+}
+
+int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double* B,
+               long long ldb, const double* C, long long ldc, void* stream, ssv_handle* out) {
+  if (!out) return SSV_EINVAL;
+  *out = nullptr;
+  if (n < 1 || m < 1 || m > n || p < 0) return SSV_EINVAL;
+  if (!A || !B || (p > 0 && !C)) return SSV_EINVAL;
+  if (lda < n || ldb < n || (p > 0 && ldc < p)) return SSV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Handle* h = new (std::nothrow) Handle();
+  if (!h) return SSV_ENOMEM;
+  std::memset(h, 0, sizeof(Handle));
+  h->n = n;
+  h->m = m;
+  h->p = p;
+  cudaGetDevice(&h->dev);
+  const int ldct = p > 0 ? p : 1;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](double** ptr, size_t count) {
+    if (e == cudaSuccess) e = cudaMalloc((void**)ptr, sizeof(double) * (count ? count : 1));
+  };
+  alloc(&h->H, (size_t)n * n);
+  alloc(&h->R, (size_t)n * m);
+  alloc(&h->Ct, (size_t)ldct * n);
+  alloc(&h->tauB, (size_t)m);
+  alloc(&h->tauA, (size_t)n);
+  alloc(&h->hnorm2, 2);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    free_handle_buffers(h);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? SSV_ENOMEM : SSV_ECUDA;
+  }
+  if (p == 0) cudaMemsetAsync(h->Ct, 0, sizeof(double) * n, st);
+  h->bytes = handle_bytes(n, m, p);
+  int rc = reduce_fp64(h, A, lda, B, ldb, C, ldc, st);
+  if (rc != SSV_OK) {
+    cudaStreamSynchronize(st);
+    free_handle_buffers(h);
+    delete h;
+    return rc;
+  }
+  *out = reinterpret_cast<ssv_handle>(h);
+  return SSV_OK;
+}
+
+int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, double* out,
+              long long ldo, int* status, double* resid, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || s < 0) return SSV_EINVAL;
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc != SSV_OK) return rc;
+  if (s == 0) return SSV_OK;
+  if (!shifts || !out) return SSV_EINVAL;
+  const bool gmode = (o.mode == SSV_G || o.mode == SSV_TF);
+  if (gmode && ldo < (h->p > 0 ? h->p : 1)) return SSV_EINVAL;
+  if (!gmode && ldo < h->n) return SSV_EINVAL;
+  if (o.precision != SSV_FP64) return SSV_ENOTSUP;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = solve_fp64(h, s, shifts, &o, out, ldo, status, resid, st);
+  if (rc == SSV_OK && o.mode == SSV_X) rc = apply_q_fp64(h, s * h->m, out, ldo, out, ldo, st);
+  return rc;
+}
+
+int ssv_apply_q(ssv_handle hh, int ncols, const double* Xhat, long long ldx, double* X,
+                long long ldX, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || ncols < 0) return SSV_EINVAL;
+  if (ncols == 0) return SSV_OK;
+  if (!Xhat || !X || ldx < h->n || ldX < h->n) return SSV_EINVAL;
+  return apply_q_fp64(h, ncols, Xhat, ldx, X, ldX, (cudaStream_t)stream);
+}
+
+int ssv_get_reduced(ssv_handle hh, double* H, long long ldh, double* R, long long ldr, double* Ct,
+                    long long ldc, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return SSV_EINVAL;
+  if ((H && ldh < h->n) || (R && ldr < h->n) || (Ct && h->p > 0 && ldc < h->p)) return SSV_EINVAL;
+  return get_reduced(h, H, ldh, R, ldr, Ct, ldc, (cudaStream_t)stream);
+}
+
+int ssv_dims(ssv_handle hh, int* n, int* m, int* p) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return SSV_EINVAL;
+  if (n) *n = h->n;
+  if (m) *m = h->m;
+  if (p) *p = h->p;
+  return SSV_OK;
+}
+
+int ssv_footprint(int n, int m, int p, int s, const ssv_opts* o_in, size_t* bytes) {
+  if (!bytes || n < 1 || m < 1 || m > n || p < 0 || s < 0) return SSV_EINVAL;
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc != SSV_OK) return rc;
+  *bytes = solve_fp64_scratch_bytes(n, m, p, s, &o);
+  return SSV_OK;
+}
+
+int ssv_handle_bytes(int n, int m, int p, size_t* bytes) {
+  if (!bytes || n < 1 || m < 1 || m > n || p < 0) return SSV_EINVAL;
+  *bytes = handle_bytes(n, m, p);
+  return SSV_OK;
+}
+
+void ssv_destroy(ssv_handle hh) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_handle_buffers(h);
+  delete h;
+}
+
+const char* ssv_strerror(int code) {
+  switch (code) {
+    case SSV_OK: return "success";
+    case SSV_EINVAL: return "invalid argument";
+    case SSV_ENOMEM: return "device memory allocation failed";
+    case SSV_ECUDA: return "CUDA runtime error";
+    case SSV_ETIMEOUT: return "bounded device wait timed out";
+    case SSV_ENOTSUP: return "unsupported option combination";
+    default: return "unknown error code";
+  }
+}
+
+int ssv_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

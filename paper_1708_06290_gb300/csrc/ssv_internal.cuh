@@ -1,0 +1,93 @@
+// Internal declarations of the GB300 shifted-system solver library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ssv.h"
+
+namespace ssv {
+
+// --------------------------------------------------------------------------
+// complex double helpers (interleaved re, im)
+// --------------------------------------------------------------------------
+struct cd {
+  double x, y;
+};
+
+__host__ __device__ __forceinline__ cd mkcd(double a, double b) { return cd{a, b}; }
+__host__ __device__ __forceinline__ cd cadd(cd a, cd b) { return cd{a.x + b.x, a.y + b.y}; }
+__host__ __device__ __forceinline__ cd csub(cd a, cd b) { return cd{a.x - b.x, a.y - b.y}; }
+__host__ __device__ __forceinline__ cd cmul(cd a, cd b) {
+  return cd{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a + b * c
+__host__ __device__ __forceinline__ cd cfma(cd b, cd c, cd a) {
+  return cd{fma(b.x, c.x, fma(-b.y, c.y, a.x)), fma(b.x, c.y, fma(b.y, c.x, a.y))};
+}
+// a - b * c
+__host__ __device__ __forceinline__ cd cfms(cd b, cd c, cd a) {
+  return cd{fma(-b.x, c.x, fma(b.y, c.y, a.x)), fma(-b.x, c.y, fma(-b.y, c.x, a.y))};
+}
+__host__ __device__ __forceinline__ double cabs1(cd a) { return fabs(a.x) + fabs(a.y); }
+// a / b (Smith's algorithm, Smith 1962)
+__host__ __device__ __forceinline__ cd cdiv(cd a, cd b) {
+  if (fabs(b.y) <= fabs(b.x)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    return cd{(a.x + a.y * r) / d, (a.y - a.x * r) / d};
+  } else {
+    double r = b.x / b.y, d = b.y + b.x * r;
+    return cd{(a.x * r + a.y) / d, (a.y * r - a.x) / d};
+  }
+}
+
+// --------------------------------------------------------------------------
+// handle
+// --------------------------------------------------------------------------
+struct Handle {
+  int n, m, p;
+  int dev;
+  double* H;      // n x n, ld n; Householder vectors of Q_A below the m-th subdiagonal
+  double* R;      // n x m, ld n; Householder vectors of Q_B below the diagonal
+  double* Ct;     // max(p,1) x n, ld max(p,1)
+  double* tauB;   // m
+  double* tauA;   // n
+  double* hnorm2; // 1: ||H||_F^2 (for backward errors)
+  int kb;         // number of Q_B reflectors
+  int ka;         // number of Q_A reflectors
+  size_t bytes;
+};
+
+// error plumbing (thread-local last CUDA error)
+void set_cuda_error(cudaError_t e);
+#define SSV_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) {                       \
+      ::ssv::set_cuda_error(_e);                   \
+      return _e == cudaErrorMemoryAllocation ? SSV_ENOMEM : SSV_ECUDA; \
+    }                                              \
+  } while (0)
+
+// reduction (reduce_fp64.cu)
+int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long long ldb,
+                const double* C, long long ldc, cudaStream_t st);
+// back-transform X = Q Xhat (reduce_fp64.cu)
+int apply_q_fp64(const Handle* h, int ncols, const double* Xhat, long long ldx, double* X,
+                 long long ldX, cudaStream_t st);
+// copy-out with explicit zeros (reduce_fp64.cu)
+int get_reduced(const Handle* h, double* H, long long ldh, double* R, long long ldr, double* Ct,
+                long long ldc, cudaStream_t st);
+
+// solver (solve_fp64.cu)
+int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
+               long long ldo, int* status, double* resid, cudaStream_t st);
+size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o);
+// normwise backward error of computed Xhat (residual_fp64.cu)
+int backward_error_fp64(const Handle* h, int s, const double* shifts, const double* Xhat,
+                        long long ldx, double* resid, cudaStream_t st);
+
+int default_nb(int n, int m);
+int num_sms();
+
+}  // namespace ssv

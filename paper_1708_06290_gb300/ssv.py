@@ -1,0 +1,265 @@
+"""Python binding of ``libssv.so`` (the C ABI of ``include/ssv.h``).
+
+Argument marshalling only: every step of the reduction and the solve runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams; the
+tensors passed in must live on the current CUDA device.  Matrices are
+column-major: a (rows, cols) tensor with stride (1, ld), ld >= rows, e.g. made
+by :func:`colmajor`.  There is no CPU path: without the built library and a
+CUDA device every call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+SSV_OK = 0
+SSV_EINVAL = -1
+SSV_ENOMEM = -2
+SSV_ECUDA = -3
+SSV_ETIMEOUT = -4
+SSV_ENOTSUP = -5
+
+SHIFT_OK = 0
+SHIFT_SINGULAR = 1
+SHIFT_NOT_CONVERGED = 2
+SHIFT_NONFINITE = 3
+
+FP64 = 0
+MIXED = 1
+
+G = 0
+TF = 1
+XHAT = 2
+X = 3
+
+_MODES = {"g": G, "tf": TF, "xhat": XHAT, "x": X}
+_PREC = {"fp64": FP64, "mixed": MIXED}
+
+
+class SsvError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = "%s failed: %s (%d)" % (what, strerror(code), code)
+        if code == SSV_ECUDA and _lib is not None:
+            msg += ", cuda error %d" % _lib.ssv_last_cuda_error()
+        super().__init__(msg)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("nb", ctypes.c_int),
+                ("tile", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced",
+           "ssv_dims", "ssv_footprint", "ssv_handle_bytes", "ssv_destroy", "ssv_strerror",
+           "ssv_last_cuda_error")
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load (building first if needed) the shared library and declare its ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libssv.so is not built (%s); run paper_1708_06290_gb300/build.py" % path)
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    LL = ctypes.c_longlong
+    L.ssv_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.ssv_default_opts.restype = None
+    L.ssv_reduce.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
+    L.ssv_solve.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P, P]
+    L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
+    L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
+    L.ssv_dims.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.ssv_footprint.argtypes = [I, I, I, I, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]
+    L.ssv_handle_bytes.argtypes = [I, I, I, ctypes.POINTER(ctypes.c_size_t)]
+    L.ssv_destroy.argtypes = [P]
+    L.ssv_destroy.restype = None
+    L.ssv_strerror.argtypes = [I]
+    L.ssv_strerror.restype = ctypes.c_char_p
+    L.ssv_last_cuda_error.argtypes = []
+    for f in ("ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced", "ssv_dims",
+              "ssv_footprint", "ssv_handle_bytes", "ssv_last_cuda_error"):
+        getattr(L, f).restype = I
+    _lib = L
+    return L
+
+
+def strerror(code):
+    if _lib is None:
+        return "code %d" % code
+    return _lib.ssv_strerror(code).decode()
+
+
+def _check(rc, what):
+    if rc != SSV_OK:
+        raise SsvError(rc, what)
+
+
+def colmajor(t):
+    """Column-major copy of a 2-D tensor (stride (1, rows))."""
+    return t.t().contiguous().t()
+
+
+def _ld(t, rows):
+    """Leading dimension of a column-major 2-D tensor (strides of size-1 dims are ignored)."""
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    if t.shape[0] > 1 and t.stride(0) != 1:
+        raise ValueError("tensor must be column-major (stride(0) == 1)")
+    ld = t.stride(1) if t.shape[1] > 1 else max(rows, 1)
+    ld = max(ld, 1)
+    if t.shape[1] > 1 and ld < max(rows, 1):
+        raise ValueError("leading dimension %d < rows %d" % (ld, rows))
+    return ld
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s" % (name, dtype))
+
+
+def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=6, tol=1e-13):
+    o = Opts()
+    load().ssv_default_opts(ctypes.byref(o))
+    o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    o.mode = _MODES[mode] if isinstance(mode, str) else int(mode)
+    o.nb = nb
+    o.tile = tile
+    o.max_refine = max_refine
+    o.tol = tol
+    return o
+
+
+class Handle:
+    """A reduced system (H, R, Ct, Q) resident on the GPU."""
+
+    def __init__(self, ptr, n, m, p, stream):
+        self._ptr = ptr
+        self.n, self.m, self.p = n, m, p
+        self._stream = stream
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if getattr(self, "_ptr", None):
+            _lib.ssv_destroy(self._ptr)
+            self._ptr = None
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("handle is closed")
+        return self._ptr
+
+    def out_rows(self, mode):
+        return self.p if _MODES.get(mode, mode) in (G, TF) else self.n
+
+    def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=6, tol=1e-13,
+              out=None, status=None, resid=None, want_resid=False, stream=None):
+        """Solve all shifts.  Returns (out, status, resid).
+
+        out is a column-major complex128 (rows, s*m) tensor, rows = p for
+        mode g/tf and n for xhat/x; block j holds the result for shifts[j].
+        """
+        L = load()
+        _need_cuda(shifts, torch.complex128, "shifts")
+        s = shifts.numel()
+        o = opts(precision, mode, nb, tile, max_refine, tol)
+        rows = self.out_rows(o.mode)
+        dev = shifts.device
+        if out is None:
+            out = torch.empty((s * self.m, max(rows, 1)), dtype=torch.complex128, device=dev).t()
+        _need_cuda(out, torch.complex128, "out")
+        ldo = _ld(out, rows)
+        if status is None:
+            status = torch.empty(s, dtype=torch.int32, device=dev)
+        if resid is None and want_resid:
+            resid = torch.empty(s, dtype=torch.float64, device=dev)
+        rc = L.ssv_solve(self.ptr, s, ctypes.c_void_p(shifts.data_ptr()), ctypes.byref(o),
+                         ctypes.c_void_p(out.data_ptr()), ldo,
+                         ctypes.c_void_p(status.data_ptr()),
+                         ctypes.c_void_p(resid.data_ptr()) if resid is not None else None,
+                         _stream_ptr(stream))
+        _check(rc, "ssv_solve")
+        return out, status, resid
+
+    def apply_q(self, xhat, out=None, stream=None):
+        L = load()
+        _need_cuda(xhat, torch.complex128, "xhat")
+        ncols = xhat.shape[1]
+        if out is None:
+            out = torch.empty((ncols, self.n), dtype=torch.complex128, device=xhat.device).t()
+        rc = L.ssv_apply_q(self.ptr, ncols, ctypes.c_void_p(xhat.data_ptr()), _ld(xhat, self.n),
+                           ctypes.c_void_p(out.data_ptr()), _ld(out, self.n), _stream_ptr(stream))
+        _check(rc, "ssv_apply_q")
+        return out
+
+    def reduced(self, stream=None):
+        """Return (H, R, Ct) as column-major float64 CUDA tensors (explicit zeros)."""
+        L = load()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n, m, p = self.n, self.m, self.p
+        H = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+        R = torch.empty((m, n), dtype=torch.float64, device=dev).t()
+        Ct = torch.empty((n, max(p, 1)), dtype=torch.float64, device=dev).t()
+        rc = L.ssv_get_reduced(self.ptr, ctypes.c_void_p(H.data_ptr()), n,
+                               ctypes.c_void_p(R.data_ptr()), n, ctypes.c_void_p(Ct.data_ptr()),
+                               max(p, 1), _stream_ptr(stream))
+        _check(rc, "ssv_get_reduced")
+        return H, R, Ct[:p]
+
+
+def reduce(A, B, C, stream=None):
+    """Controller-Hessenberg reduction of (A, B, C) on the GPU; returns a Handle."""
+    L = load()
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _need_cuda(t, torch.float64, nm)
+    n = A.shape[0]
+    m = B.shape[1]
+    p = C.shape[0]
+    h = ctypes.c_void_p()
+    rc = L.ssv_reduce(n, m, p, ctypes.c_void_p(A.data_ptr()), _ld(A, n),
+                      ctypes.c_void_p(B.data_ptr()), _ld(B, n), ctypes.c_void_p(C.data_ptr()),
+                      _ld(C, p) if p > 0 else 1, _stream_ptr(stream), ctypes.byref(h))
+    _check(rc, "ssv_reduce")
+    return Handle(h, n, m, p, stream)
+
+
+def footprint(n, m, p, s, **kw):
+    L = load()
+    o = opts(**kw)
+    b = ctypes.c_size_t()
+    _check(L.ssv_footprint(n, m, p, s, ctypes.byref(o), ctypes.byref(b)), "ssv_footprint")
+    return b.value
+
+
+def handle_bytes(n, m, p):
+    L = load()
+    b = ctypes.c_size_t()
+    _check(L.ssv_handle_bytes(n, m, p, ctypes.byref(b)), "ssv_handle_bytes")
+    return b.value
