@@ -46,7 +46,8 @@ extern "C" {
 
 /* ---- per-shift status (device int array, one entry per shift) --------- */
 #define SSV_SHIFT_OK 0
-#define SSV_SHIFT_SINGULAR 1      /* an exactly zero pivot: H - sigma I is singular */
+#define SSV_SHIFT_SINGULAR 1      /* singular to working precision: a diagonal entry of the
+                                     triangular factor has modulus <= n eps ||H - sigma I||_F */
 #define SSV_SHIFT_NOT_CONVERGED 2 /* refinement stopped above the tolerance */
 #define SSV_SHIFT_NONFINITE 3     /* a NaN / Inf appeared */
 
@@ -125,6 +126,18 @@ int ssv_apply_q(ssv_handle h, int ncols, const double* Xhat, long long ldx, doub
 int ssv_get_reduced(ssv_handle h, double* H, long long ldh, double* R, long long ldr, double* Ct,
                     long long ldc, void* stream);
 
+/*
+ * ssv_load_reduced -- build a handle from a stored reduced triple (restoring
+ * a checkpoint written with ssv_get_reduced, or a system already in
+ * controller-Hessenberg form).  H (device) n x n, ldh >= n, read only on and
+ * above the m-th subdiagonal; R (device) n x m, ldr >= n, read only on and
+ * above the diagonal; Ct (device) p x n, ldc >= max(1, p).  The handle has no
+ * Q: ssv_apply_q and SSV_X return SSV_ENOTSUP on it.  Errors as ssv_reduce.
+ */
+int ssv_load_reduced(int n, int m, int p, const double* H, long long ldh, const double* R,
+                     long long ldr, const double* Ct, long long ldc, void* stream,
+                     ssv_handle* out);
+
 /* Dimensions of a handle.  Any output pointer may be NULL. */
 int ssv_dims(ssv_handle h, int* n, int* m, int* p);
 
@@ -147,6 +160,18 @@ const char* ssv_strerror(int code);
 
 /* The last CUDA error code seen by this thread's calls (0 if none). */
 int ssv_last_cuda_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads); differences of two reads count the launches of the calls between
+ * them.  Measurement aid; the paper has no counterpart. */
+long long ssv_kernel_launches(void);
+
+/* Arithmetic peak probe (measurement aid; the paper has no counterpart):
+ * runs independent fused multiply-add chains on every SM of the current
+ * device for a few milliseconds, synchronises `stream`, and stores the best
+ * of three runs in *tflops.  kind 0 = FP64 (DFMA), 1 = FP32 (FFMA).
+ * Errors: SSV_EINVAL, SSV_ENOMEM, SSV_ECUDA. */
+int ssv_peak_probe(int kind, void* stream, double* tflops);
 
 #ifdef __cplusplus
 }

@@ -218,6 +218,7 @@ inline cudaError_t launch_left(double* a, long long ld, int r0, int len, int c0,
   long long warps = c1 - c0;
   int blocks = (int)((warps * 32 + 255) / 256);
   apply_left_kernel<<<blocks, 256, 0, st>>>(a, ld, r0, len, c0, c1, vsrc, tau);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -228,8 +229,10 @@ inline cudaError_t launch_right(double* a, long long ld, int nr, int c0, int len
   int nchunk = (len + kRightCols - 1) / kRightCols;
   dim3 grid((nr + kRightRows - 1) / kRightRows, nchunk);
   apply_right_dot_kernel<<<grid, kRightRows, 0, st>>>(a, ld, nr, c0, len, vsrc, tau, part);
+  count_launch();
   apply_right_update_kernel<<<grid, kRightRows, 0, st>>>(a, ld, nr, c0, len, nchunk, vsrc, tau,
                                                          part);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -264,6 +267,7 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
     int len = n - i;
     double* x = h->R + i + (size_t)i * n;
     house_kernel<<<1, kHouseThreads, 0, st>>>(x, len, h->tauB + i);
+    count_launch();
     chk(cudaGetLastError());
     chk(launch_left(h->R, n, i, len, i + 1, m, x, h->tauB + i, st));
     chk(launch_left(h->H, n, i, len, 0, n, x, h->tauB + i, st));
@@ -276,15 +280,18 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
     int r0 = j + m, len = n - r0;
     double* x = h->H + r0 + (size_t)j * n;
     house_kernel<<<1, kHouseThreads, 0, st>>>(x, len, h->tauA + j);
+    count_launch();
     chk(cudaGetLastError());
     chk(launch_left(h->H, n, r0, len, j + 1, n, x, h->tauA + j, st));
     chk(launch_right(h->H, n, n, r0, len, x, h->tauA + j, part, st));
     chk(launch_right(h->Ct, ldct, p, r0, len, x, h->tauA + j, part, st));
   }
+  h->has_q = 1;
   if (rc == SSV_OK) {
     chk(cudaMemsetAsync(h->hnorm2, 0, 2 * sizeof(double), st));
     hnorm_kernel<<<std::max(1, std::min(1024, (n * n + 255) / 256)), 256, 0, st>>>(h->H, n, m,
                                                                                   h->hnorm2);
+    count_launch();
     chk(cudaGetLastError());
   }
   chk(cudaFreeAsync(part, st));
@@ -300,6 +307,7 @@ int apply_q_fp64(const Handle* h, int ncols, const double* Xhat, long long ldx, 
     int blocks = (int)std::min<long long>(4096, ((long long)n * ncols + 255) / 256);
     copy_cd_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const cd*>(Xhat), ldx, n, ncols, Xc,
                                            ldX);
+    count_launch();
     SSV_CUDA_TRY(cudaGetLastError());
   }
   int blocks = (int)(((long long)ncols * 32 + 255) / 256);
@@ -308,12 +316,39 @@ int apply_q_fp64(const Handle* h, int ncols, const double* Xhat, long long ldx, 
     int r0 = j + m, len = n - r0;
     apply_left_complex_kernel<<<blocks, 256, 0, st>>>(Xc, ldX, r0, len, ncols,
                                                       h->H + r0 + (size_t)j * n, h->tauA + j);
+    count_launch();
   }
   for (int i = h->kb - 1; i >= 0; --i) {
     int len = n - i;
     apply_left_complex_kernel<<<blocks, 256, 0, st>>>(Xc, ldX, i, len, ncols,
                                                       h->R + i + (size_t)i * n, h->tauB + i);
+    count_launch();
   }
+  SSV_CUDA_TRY(cudaGetLastError());
+  return SSV_OK;
+}
+
+int load_reduced(Handle* h, const double* H, long long ldh, const double* R, long long ldr,
+                 const double* Ct, long long ldc, cudaStream_t st) {
+  const int n = h->n, m = h->m, p = h->p;
+  int blocks = (int)std::min<long long>(4096, ((long long)n * n + 255) / 256);
+  copy_masked_kernel<<<blocks, 256, 0, st>>>(H, ldh, n, n, m, h->H, n);
+  count_launch();
+  SSV_CUDA_TRY(cudaGetLastError());
+  blocks = (int)std::min<long long>(4096, ((long long)n * m + 255) / 256);
+  copy_masked_kernel<<<blocks, 256, 0, st>>>(R, ldr, n, m, 0, h->R, n);
+  count_launch();
+  SSV_CUDA_TRY(cudaGetLastError());
+  if (p > 0)
+    SSV_CUDA_TRY(cudaMemcpy2DAsync(h->Ct, sizeof(double) * p, Ct, sizeof(double) * ldc,
+                                   sizeof(double) * p, n, cudaMemcpyDeviceToDevice, st));
+  h->kb = 0;
+  h->ka = 0;
+  h->has_q = 0;
+  SSV_CUDA_TRY(cudaMemsetAsync(h->hnorm2, 0, 2 * sizeof(double), st));
+  hnorm_kernel<<<std::max(1, std::min(1024, (n * n + 255) / 256)), 256, 0, st>>>(h->H, n, m,
+                                                                                h->hnorm2);
+  count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   return SSV_OK;
 }
@@ -324,11 +359,13 @@ int get_reduced(const Handle* h, double* H, long long ldh, double* R, long long 
   if (H) {
     int blocks = (int)std::min<long long>(4096, ((long long)n * n + 255) / 256);
     copy_masked_kernel<<<blocks, 256, 0, st>>>(h->H, n, n, n, m, H, ldh);
+    count_launch();
     SSV_CUDA_TRY(cudaGetLastError());
   }
   if (R) {
     int blocks = (int)std::min<long long>(4096, ((long long)n * m + 255) / 256);
     copy_masked_kernel<<<blocks, 256, 0, st>>>(h->R, n, n, m, 0, R, ldr);
+    count_launch();
     SSV_CUDA_TRY(cudaGetLastError());
   }
   if (Ct && p > 0) {

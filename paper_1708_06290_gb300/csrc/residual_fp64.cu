@@ -89,6 +89,7 @@ int launch(const Handle* h, int s, const double* shifts, const double* Xhat, lon
   residual_kernel<MAXM><<<grid, kRows, 0, st>>>(h->n, h->m, h->H, h->R,
                                                 reinterpret_cast<const cd*>(shifts),
                                                 reinterpret_cast<const cd*>(Xhat), ldx, acc);
+  count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   return SSV_OK;
 }
@@ -116,6 +117,7 @@ int backward_error_fp64(const Handle* h, int s, const double* shifts, const doub
     residual_finish_kernel<<<(s + 127) / 128, 128, 0, st>>>(h->n, m, s, h->hnorm2, h->R,
                                                             reinterpret_cast<const cd*>(shifts),
                                                             acc, resid);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(e); rc = SSV_ECUDA; }
   }

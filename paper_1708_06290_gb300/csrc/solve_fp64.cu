@@ -408,6 +408,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
                                          reinterpret_cast<const cd*>(shifts), mode, scratch, slot,
                                          reinterpret_cast<cd*>(out), ldo, status, xhat_copy, ldxc,
                                          h->hnorm2);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e == cudaSuccess) e = e2;
@@ -419,6 +420,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
     int rows = (mode == SSV_G || mode == SSV_TF) ? p : n;
     if (rows > 0) {
       nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows, m, s, status);
+      count_launch();
       SSV_CUDA_TRY(cudaGetLastError());
     }
   }

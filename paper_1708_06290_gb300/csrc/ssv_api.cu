@@ -1,5 +1,6 @@
 // C ABI entry points (include/ssv.h): argument checks, handle lifetime and
 // dispatch to the FP64 reduction and the solvers.
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -9,8 +10,10 @@
 namespace ssv {
 
 static thread_local int g_last_cuda = 0;
+static std::atomic<long long> g_launches{0};
 
 void set_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
+void count_launch(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 int num_sms() {
   static int cached[64] = {0};
@@ -64,14 +67,7 @@ void ssv_default_opts(ssv_opts* o) {
   o->tol = 1e-13;
 }
 
-int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double* B,
-               long long ldb, const double* C, long long ldc, void* stream, ssv_handle* out) {
-  if (!out) return SSV_EINVAL;
-  *out = nullptr;
-  if (n < 1 || m < 1 || m > n || p < 0) return SSV_EINVAL;
-  if (!A || !B || (p > 0 && !C)) return SSV_EINVAL;
-  if (lda < n || ldb < n || (p > 0 && ldc < p)) return SSV_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+static int make_handle(int n, int m, int p, cudaStream_t st, Handle** out) {
   Handle* h = new (std::nothrow) Handle();
   if (!h) return SSV_ENOMEM;
   std::memset(h, 0, sizeof(Handle));
@@ -90,15 +86,53 @@ int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double
   alloc(&h->tauB, (size_t)m);
   alloc(&h->tauA, (size_t)n);
   alloc(&h->hnorm2, 2);
+  if (e == cudaSuccess && p == 0) e = cudaMemsetAsync(h->Ct, 0, sizeof(double) * n, st);
   if (e != cudaSuccess) {
     set_cuda_error(e);
     free_handle_buffers(h);
     delete h;
     return e == cudaErrorMemoryAllocation ? SSV_ENOMEM : SSV_ECUDA;
   }
-  if (p == 0) cudaMemsetAsync(h->Ct, 0, sizeof(double) * n, st);
   h->bytes = handle_bytes(n, m, p);
-  int rc = reduce_fp64(h, A, lda, B, ldb, C, ldc, st);
+  *out = h;
+  return SSV_OK;
+}
+
+int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double* B,
+               long long ldb, const double* C, long long ldc, void* stream, ssv_handle* out) {
+  if (!out) return SSV_EINVAL;
+  *out = nullptr;
+  if (n < 1 || m < 1 || m > n || p < 0) return SSV_EINVAL;
+  if (!A || !B || (p > 0 && !C)) return SSV_EINVAL;
+  if (lda < n || ldb < n || (p > 0 && ldc < p)) return SSV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Handle* h = nullptr;
+  int rc = make_handle(n, m, p, st, &h);
+  if (rc != SSV_OK) return rc;
+  rc = reduce_fp64(h, A, lda, B, ldb, C, ldc, st);
+  if (rc != SSV_OK) {
+    cudaStreamSynchronize(st);
+    free_handle_buffers(h);
+    delete h;
+    return rc;
+  }
+  *out = reinterpret_cast<ssv_handle>(h);
+  return SSV_OK;
+}
+
+int ssv_load_reduced(int n, int m, int p, const double* H, long long ldh, const double* R,
+                     long long ldr, const double* Ct, long long ldc, void* stream,
+                     ssv_handle* out) {
+  if (!out) return SSV_EINVAL;
+  *out = nullptr;
+  if (n < 1 || m < 1 || m > n || p < 0) return SSV_EINVAL;
+  if (!H || !R || (p > 0 && !Ct)) return SSV_EINVAL;
+  if (ldh < n || ldr < n || (p > 0 && ldc < p)) return SSV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Handle* h = nullptr;
+  int rc = make_handle(n, m, p, st, &h);
+  if (rc != SSV_OK) return rc;
+  rc = load_reduced(h, H, ldh, R, ldr, Ct, ldc, st);
   if (rc != SSV_OK) {
     cudaStreamSynchronize(st);
     free_handle_buffers(h);
@@ -123,6 +157,7 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
   if (gmode && ldo < (h->p > 0 ? h->p : 1)) return SSV_EINVAL;
   if (!gmode && ldo < h->n) return SSV_EINVAL;
   if (o.precision != SSV_FP64) return SSV_ENOTSUP;
+  if (o.mode == SSV_X && !h->has_q) return SSV_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   rc = solve_fp64(h, s, shifts, &o, out, ldo, status, resid, st);
   if (rc == SSV_OK && o.mode == SSV_X) rc = apply_q_fp64(h, s * h->m, out, ldo, out, ldo, st);
@@ -135,6 +170,7 @@ int ssv_apply_q(ssv_handle hh, int ncols, const double* Xhat, long long ldx, dou
   if (!h || ncols < 0) return SSV_EINVAL;
   if (ncols == 0) return SSV_OK;
   if (!Xhat || !X || ldx < h->n || ldX < h->n) return SSV_EINVAL;
+  if (!h->has_q) return SSV_ENOTSUP;
   return apply_q_fp64(h, ncols, Xhat, ldx, X, ldX, (cudaStream_t)stream);
 }
 
@@ -192,5 +228,12 @@ const char* ssv_strerror(int code) {
 }
 
 int ssv_last_cuda_error(void) { return g_last_cuda; }
+
+long long ssv_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int ssv_peak_probe(int kind, void* stream, double* tflops) {
+  if (!tflops || (kind != 0 && kind != 1)) return SSV_EINVAL;
+  return peak_probe(kind, (cudaStream_t)stream, tflops);
+}
 
 }  // extern "C"

@@ -55,6 +55,7 @@ struct Handle {
   double* hnorm2; // 1: ||H||_F^2 (for backward errors)
   int kb;         // number of Q_B reflectors
   int ka;         // number of Q_A reflectors
+  int has_q;      // 0 when built by ssv_load_reduced
   size_t bytes;
 };
 
@@ -75,6 +76,9 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
 // back-transform X = Q Xhat (reduce_fp64.cu)
 int apply_q_fp64(const Handle* h, int ncols, const double* Xhat, long long ldx, double* X,
                  long long ldX, cudaStream_t st);
+// load a stored reduced triple with explicit zeros (reduce_fp64.cu)
+int load_reduced(Handle* h, const double* H, long long ldh, const double* R, long long ldr,
+                 const double* Ct, long long ldc, cudaStream_t st);
 // copy-out with explicit zeros (reduce_fp64.cu)
 int get_reduced(const Handle* h, double* H, long long ldh, double* R, long long ldr, double* Ct,
                 long long ldc, cudaStream_t st);
@@ -89,5 +93,10 @@ int backward_error_fp64(const Handle* h, int s, const double* shifts, const doub
 
 int default_nb(int n, int m);
 int num_sms();
+
+// Kernel-launch counter (every launch site calls count_launch()).
+void count_launch(long long k = 1);
+// DFMA (kind 0) / FFMA (kind 1) throughput probe, TFLOP/s.
+int peak_probe(int kind, cudaStream_t st, double* tflops);
 
 }  // namespace ssv

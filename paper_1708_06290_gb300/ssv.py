@@ -54,7 +54,7 @@ class Opts(ctypes.Structure):
 
 EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced",
            "ssv_dims", "ssv_footprint", "ssv_handle_bytes", "ssv_destroy", "ssv_strerror",
-           "ssv_last_cuda_error")
+           "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced")
 
 _lib = None
 
@@ -80,6 +80,7 @@ def load(build_if_missing=True):
     L.ssv_default_opts.argtypes = [ctypes.POINTER(Opts)]
     L.ssv_default_opts.restype = None
     L.ssv_reduce.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
+    L.ssv_load_reduced.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
     L.ssv_solve.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P, P]
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
@@ -91,8 +92,11 @@ def load(build_if_missing=True):
     L.ssv_strerror.argtypes = [I]
     L.ssv_strerror.restype = ctypes.c_char_p
     L.ssv_last_cuda_error.argtypes = []
-    for f in ("ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced", "ssv_dims",
-              "ssv_footprint", "ssv_handle_bytes", "ssv_last_cuda_error"):
+    L.ssv_kernel_launches.argtypes = []
+    L.ssv_kernel_launches.restype = ctypes.c_longlong
+    L.ssv_peak_probe.argtypes = [I, P, ctypes.POINTER(ctypes.c_double)]
+    for f in ("ssv_reduce", "ssv_load_reduced", "ssv_solve", "ssv_apply_q", "ssv_get_reduced", "ssv_dims",
+              "ssv_footprint", "ssv_handle_bytes", "ssv_last_cuda_error", "ssv_peak_probe"):
         getattr(L, f).restype = I
     _lib = L
     return L
@@ -250,6 +254,23 @@ def reduce(A, B, C, stream=None):
     return Handle(h, n, m, p, stream)
 
 
+def load_reduced(H, R, Ct, stream=None):
+    """Handle from a stored reduced triple (H m-Hessenberg, R upper triangular, Ct); no Q."""
+    L = load()
+    for t, nm in ((H, "H"), (R, "R"), (Ct, "Ct")):
+        _need_cuda(t, torch.float64, nm)
+    n = H.shape[0]
+    m = R.shape[1]
+    p = Ct.shape[0]
+    h = ctypes.c_void_p()
+    rc = L.ssv_load_reduced(n, m, p, ctypes.c_void_p(H.data_ptr()), _ld(H, n),
+                            ctypes.c_void_p(R.data_ptr()), _ld(R, n),
+                            ctypes.c_void_p(Ct.data_ptr()), _ld(Ct, p) if p > 0 else 1,
+                            _stream_ptr(stream), ctypes.byref(h))
+    _check(rc, "ssv_load_reduced")
+    return Handle(h, n, m, p, stream)
+
+
 def footprint(n, m, p, s, **kw):
     L = load()
     o = opts(**kw)
@@ -263,3 +284,17 @@ def handle_bytes(n, m, p):
     b = ctypes.c_size_t()
     _check(L.ssv_handle_bytes(n, m, p, ctypes.byref(b)), "ssv_handle_bytes")
     return b.value
+
+
+def kernel_launches():
+    """Kernels the library has launched in this process so far."""
+    return load().ssv_kernel_launches()
+
+
+def peak_probe(kind="fp64", stream=None):
+    """Measured FMA throughput of the current GPU in TFLOP/s (kind "fp64" or "fp32")."""
+    L = load()
+    v = ctypes.c_double()
+    _check(L.ssv_peak_probe({"fp64": 0, "fp32": 1}[kind], _stream_ptr(stream), ctypes.byref(v)),
+           "ssv_peak_probe")
+    return v.value

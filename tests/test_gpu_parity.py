@@ -174,3 +174,18 @@ def test_precision_workload_sampled_fp64():
             assert relerr(G[j], Go[k]) < REL_TOL, (j, cond[k])
             checked += 1
     assert checked >= 8
+
+
+def test_load_reduced_checkpoint_roundtrip():
+    """A handle restored from ssv_get_reduced's output solves exactly like the original;
+    it has no Q, so SSV_X is refused."""
+    sysr = W.random_system(230, 5, 3, seed=91)
+    h = gpu_system(sysr)
+    Hg, Rg, Cg = h.reduced()
+    h2 = ssv.load_reduced(Hg, Rg, Cg)
+    sig = shifts_dev(np.array([0.3j, -1.9 + 0.2j, 2.0j]))
+    g1, _, _ = h.solve(sig, mode="g")
+    g2, _, _ = h2.solve(sig, mode="g")
+    assert torch.equal(g1, g2)
+    with pytest.raises(ssv.SsvError):
+        h2.solve(sig, mode="x")
