@@ -43,6 +43,7 @@ extern "C" {
 #define SSV_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
 #define SSV_ETIMEOUT (-4) /* a bounded device wait gave up */
 #define SSV_ENOTSUP (-5)  /* option combination not supported */
+#define SSV_ESCRATCH (-6) /* problem too large for ssv_solve_noalloc's fixed scratch */
 
 /* ---- per-shift status (device int array, one entry per shift) --------- */
 #define SSV_SHIFT_OK 0
@@ -107,6 +108,33 @@ int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double
  */
 int ssv_solve(ssv_handle h, int s, const double* shifts, const ssv_opts* o, double* out,
               long long ldo, int* status, double* resid, void* stream);
+
+/*
+ * ssv_solve_noalloc -- ssv_solve without any device allocation.  The paper has
+ * no counterpart; this entry point exists for callers that cannot allocate
+ * device memory when they solve (an external allocator or framework owns all
+ * device memory during their step, a device-memory budget fixed in advance,
+ * or a latency-critical loop where an allocation may not stall or fail).
+ *
+ *   Same arguments and results as ssv_solve with precision SSV_FP64 and mode
+ *   SSV_G, SSV_TF or SSV_XHAT; no resid output.  The handle, shifts, out and
+ *   status are the caller's, allocated beforehand.
+ *   Scratch: a fixed 64 MiB array inside the library, present on every GPU
+ *   that loads the library until the process exits.  One shift's window needs
+ *   16 * (p + n) * m bytes (plus 16 * n * m for SSV_XHAT); sizes where that
+ *   exceeds 64 MiB return SSV_ESCRATCH, and smaller sizes run with as many
+ *   thread blocks as fit (fewer than ssv_solve uses when n * m is large).
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture.
+ *   Every call uses the same array and leaves its contents behind: calls
+ *   whose executions overlap on the GPU (different streams, or different host
+ *   threads) race on it and give wrong results; serialize them.
+ * Errors: SSV_EINVAL, SSV_ENOTSUP (precision, mode, m > 32, resid requested),
+ * SSV_ESCRATCH, SSV_ECUDA.
+ */
+int ssv_solve_noalloc(ssv_handle h, int s, const double* shifts, const ssv_opts* o, double* out,
+                      long long ldo, int* status, void* stream);
 
 /*
  * ssv_apply_q -- X = Q Xhat (Sec. 2: X = Q Xhat in original coordinates).

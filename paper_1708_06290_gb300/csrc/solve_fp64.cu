@@ -477,4 +477,101 @@ int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, 
   return rc;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP64 solve (ssv_solve_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need a
+// solve: code that runs while another component owns the allocator (a custom
+// pool or a framework that forbids cudaMalloc / cudaMallocAsync inside its
+// step), processes with a hard device-memory budget that was fixed up front,
+// or real-time loops where an allocation's latency or failure is not
+// acceptable.  For them the per-thread-block window state lives in one
+// fixed array that is part of the loaded library image, so the call itself
+// allocates nothing: no cudaMalloc / cudaMallocAsync / cudaFree and no
+// allocating library routine.
+//
+// The array below holds kNoAllocScratchBytes (64 MiB) on every GPU that loads
+// the library, for as long as the process lives.  In host code its name is
+// only a host-side stand-in, so the device address is looked up once per
+// device with cudaGetSymbolAddress (with that device current) and cached;
+// the first call on each device performs that lookup.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+int noalloc_scratch_address(void** out) {
+  int dev = 0;
+  SSV_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return SSV_ENOTSUP;
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* ptr = nullptr;
+    SSV_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return SSV_OK;
+}
+
+template <int MAXM>
+int launch_solve_noalloc(const Handle* h, int s, const double* shifts, int nb, int mode,
+                         double* out, long long ldo, int* status, cudaStream_t st) {
+  using L = Layout<MAXM>;
+  const int n = h->n, m = h->m, p = h->p;
+  const bool track_t = (mode == SSV_XHAT);
+  const size_t slot = (size_t)(p + n) * m + (track_t ? (size_t)n * m : 0);
+  const size_t max_slots = kNoAllocScratchBytes / (sizeof(cd) * slot);
+  if (max_slots < 1) return SSV_ESCRATCH;
+  void* base = nullptr;
+  int rc = noalloc_scratch_address(&base);
+  if (rc != SSV_OK) return rc;
+  auto kern = solve_fp64_kernel<MAXM>;
+  SSV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+  int per_sm = 0;
+  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L::bytes));
+  per_sm = std::max(1, std::min(per_sm, 2));
+  const int grid = (int)std::min<size_t>((size_t)std::min(s, num_sms() * per_sm), max_slots);
+  // Every window entry the kernel reads is written earlier in the same call
+  // (the shift setup overwrites the whole slot), so nothing left in the array
+  // by a previous call needs clearing.
+  kern<<<grid, kThreads, L::bytes, st>>>(n, m, p, nb, h->H, h->Ct, p > 0 ? p : 1, h->R, s,
+                                         reinterpret_cast<const cd*>(shifts), mode,
+                                         reinterpret_cast<cd*>(base), slot,
+                                         reinterpret_cast<cd*>(out), ldo, status, nullptr, 0,
+                                         h->hnorm2);
+  count_launch();
+  SSV_CUDA_TRY(cudaGetLastError());
+  if (status != nullptr) {
+    const int rows = (mode == SSV_G || mode == SSV_TF) ? p : n;
+    if (rows > 0) {
+      nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows, m, s, status);
+      count_launch();
+      SSV_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return SSV_OK;
+}
+}  // namespace
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+int solve_fp64_noalloc(const Handle* h, int s, const double* shifts, const ssv_opts* o,
+                       double* out, long long ldo, int* status, cudaStream_t st) {
+  const int m = h->m;
+  const int nb = o->nb > 0 ? o->nb : default_nb(h->n, m);
+  if (nb > kNB) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  if (m <= 1) return launch_solve_noalloc<1>(h, s, shifts, nb, o->mode, out, ldo, status, st);
+  if (m <= 2) return launch_solve_noalloc<2>(h, s, shifts, nb, o->mode, out, ldo, status, st);
+  if (m <= 4) return launch_solve_noalloc<4>(h, s, shifts, nb, o->mode, out, ldo, status, st);
+  if (m <= 8) return launch_solve_noalloc<8>(h, s, shifts, nb, o->mode, out, ldo, status, st);
+  if (m <= 16) return launch_solve_noalloc<16>(h, s, shifts, nb, o->mode, out, ldo, status, st);
+  if (m <= 32) return launch_solve_noalloc<32>(h, s, shifts, nb, o->mode, out, ldo, status, st);
+  return SSV_ENOTSUP;
+}
+
 }  // namespace ssv

@@ -164,6 +164,24 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
   return rc;
 }
 
+int ssv_solve_noalloc(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in,
+                      double* out, long long ldo, int* status, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || s < 0) return SSV_EINVAL;
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc != SSV_OK) return rc;
+  if (o.precision != SSV_FP64 || o.mode == SSV_X) return SSV_ENOTSUP;
+  if (h->m > 32) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  if (!shifts || !out) return SSV_EINVAL;
+  const bool gmode = (o.mode == SSV_G || o.mode == SSV_TF);
+  if (gmode && ldo < (h->p > 0 ? h->p : 1)) return SSV_EINVAL;
+  if (!gmode && ldo < h->n) return SSV_EINVAL;
+  return solve_fp64_noalloc(h, s, shifts, &o, out, ldo, status, (cudaStream_t)stream);
+}
+
 int ssv_apply_q(ssv_handle hh, int ncols, const double* Xhat, long long ldx, double* X,
                 long long ldX, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);
@@ -223,6 +241,7 @@ const char* ssv_strerror(int code) {
     case SSV_ECUDA: return "CUDA runtime error";
     case SSV_ETIMEOUT: return "bounded device wait timed out";
     case SSV_ENOTSUP: return "unsupported option combination";
+    case SSV_ESCRATCH: return "problem exceeds the fixed 64 MiB scratch of ssv_solve_noalloc";
     default: return "unknown error code";
   }
 }

@@ -91,6 +91,11 @@ size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o);
 int backward_error_fp64(const Handle* h, int s, const double* shifts, const double* Xhat,
                         long long ldx, double* resid, cudaStream_t st);
 
+// allocation-free FP64 solve on the library's fixed scratch array (solve_fp64.cu)
+int solve_fp64_noalloc(const Handle* h, int s, const double* shifts, const ssv_opts* o,
+                       double* out, long long ldo, int* status, cudaStream_t st);
+size_t noalloc_scratch_bytes();
+
 int default_nb(int n, int m);
 int num_sms();
 

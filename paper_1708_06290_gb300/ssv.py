@@ -20,6 +20,7 @@ SSV_ENOMEM = -2
 SSV_ECUDA = -3
 SSV_ETIMEOUT = -4
 SSV_ENOTSUP = -5
+SSV_ESCRATCH = -6
 
 SHIFT_OK = 0
 SHIFT_SINGULAR = 1
@@ -54,7 +55,7 @@ class Opts(ctypes.Structure):
 
 EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced",
            "ssv_dims", "ssv_footprint", "ssv_handle_bytes", "ssv_destroy", "ssv_strerror",
-           "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced")
+           "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc")
 
 _lib = None
 
@@ -82,6 +83,7 @@ def load(build_if_missing=True):
     L.ssv_reduce.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
     L.ssv_load_reduced.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
     L.ssv_solve.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P, P]
+    L.ssv_solve_noalloc.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P]
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
     L.ssv_dims.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
@@ -95,7 +97,7 @@ def load(build_if_missing=True):
     L.ssv_kernel_launches.argtypes = []
     L.ssv_kernel_launches.restype = ctypes.c_longlong
     L.ssv_peak_probe.argtypes = [I, P, ctypes.POINTER(ctypes.c_double)]
-    for f in ("ssv_reduce", "ssv_load_reduced", "ssv_solve", "ssv_apply_q", "ssv_get_reduced", "ssv_dims",
+    for f in ("ssv_reduce", "ssv_load_reduced", "ssv_solve", "ssv_solve_noalloc", "ssv_apply_q", "ssv_get_reduced", "ssv_dims",
               "ssv_footprint", "ssv_handle_bytes", "ssv_last_cuda_error", "ssv_peak_probe"):
         getattr(L, f).restype = I
     _lib = L
