@@ -72,8 +72,8 @@ typedef struct ssv_opts {
 
 typedef struct ssv_handle_s* ssv_handle;
 
-/* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 6,
- * tol = 1e-13. */
+/* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 8,
+ * tol = 1e-14. */
 void ssv_default_opts(ssv_opts* o);
 
 /*

@@ -205,6 +205,24 @@ __global__ void copy_cd_kernel(const cd* __restrict__ src, long long lds, int ro
   }
 }
 
+// Hhi = fl32(H), Hlo = fl32(H - Hhi) on and above the m-th subdiagonal; 0 below.
+__global__ void split_h_kernel(const double* __restrict__ H, int n, int m, float* __restrict__ hi,
+                               float* __restrict__ lo) {
+  long long total = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    float a = 0.0f, b = 0.0f;
+    if (i <= j + m) {
+      double v = H[idx];
+      a = (float)v;
+      b = (float)(v - (double)a);
+    }
+    hi[idx] = a;
+    lo[idx] = b;
+  }
+}
+
 struct RightWork {
   double* part;
   size_t cap;  // doubles
@@ -348,6 +366,15 @@ int load_reduced(Handle* h, const double* H, long long ldh, const double* R, lon
   SSV_CUDA_TRY(cudaMemsetAsync(h->hnorm2, 0, 2 * sizeof(double), st));
   hnorm_kernel<<<std::max(1, std::min(1024, (n * n + 255) / 256)), 256, 0, st>>>(h->H, n, m,
                                                                                 h->hnorm2);
+  count_launch();
+  SSV_CUDA_TRY(cudaGetLastError());
+  return SSV_OK;
+}
+
+int split_h(Handle* h, cudaStream_t st) {
+  const int n = h->n;
+  int blocks = (int)std::min<long long>(8192, ((long long)n * n + 255) / 256);
+  split_h_kernel<<<blocks, 256, 0, st>>>(h->H, n, h->m, h->Hhi, h->Hlo);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   return SSV_OK;

@@ -16,8 +16,10 @@ __global__ void __launch_bounds__(kRows) residual_kernel(int n, int m, const dou
                                                          const double* __restrict__ R,
                                                          const cd* __restrict__ shifts,
                                                          const cd* __restrict__ X, long long ldx,
-                                                         double* __restrict__ acc) {
+                                                         double* __restrict__ acc,
+                                                         const int* __restrict__ mask) {
   const int sh = blockIdx.y;
+  if (mask != nullptr && mask[sh] == 0) return;
   const int i = blockIdx.x * kRows + threadIdx.x;
   const cd sigma = shifts[sh];
   const cd* Xs = X + (size_t)sh * m * ldx;
@@ -69,9 +71,11 @@ __global__ void __launch_bounds__(kRows) residual_kernel(int n, int m, const dou
 
 __global__ void residual_finish_kernel(int n, int m, int s, const double* __restrict__ hn,
                                        const double* __restrict__ R, const cd* __restrict__ shifts,
-                                       const double* __restrict__ acc, double* __restrict__ resid) {
+                                       const double* __restrict__ acc, double* __restrict__ resid,
+                                       const int* __restrict__ mask) {
   int sh = blockIdx.x * blockDim.x + threadIdx.x;
   if (sh >= s) return;
+  if (mask != nullptr && mask[sh] == 0) return;
   double r2 = 0.0;
   for (int q = 0; q < m; ++q)
     for (int i = 0; i <= q && i < n; ++i) r2 = fma(R[i + (size_t)q * n], R[i + (size_t)q * n], r2);
@@ -84,11 +88,11 @@ __global__ void residual_finish_kernel(int n, int m, int s, const double* __rest
 
 template <int MAXM>
 int launch(const Handle* h, int s, const double* shifts, const double* Xhat, long long ldx,
-           double* resid, double* acc, cudaStream_t st) {
+           double* resid, double* acc, const int* mask, cudaStream_t st) {
   dim3 grid((h->n + kRows - 1) / kRows, s);
   residual_kernel<MAXM><<<grid, kRows, 0, st>>>(h->n, h->m, h->H, h->R,
                                                 reinterpret_cast<const cd*>(shifts),
-                                                reinterpret_cast<const cd*>(Xhat), ldx, acc);
+                                                reinterpret_cast<const cd*>(Xhat), ldx, acc, mask);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   return SSV_OK;
@@ -98,6 +102,11 @@ int launch(const Handle* h, int s, const double* shifts, const double* Xhat, lon
 
 int backward_error_fp64(const Handle* h, int s, const double* shifts, const double* Xhat,
                         long long ldx, double* resid, cudaStream_t st) {
+  return backward_error_fp64_masked(h, s, shifts, Xhat, ldx, resid, nullptr, st);
+}
+
+int backward_error_fp64_masked(const Handle* h, int s, const double* shifts, const double* Xhat,
+                               long long ldx, double* resid, const int* mask, cudaStream_t st) {
   if (s == 0) return SSV_OK;
   double* acc = nullptr;
   SSV_CUDA_TRY(cudaMallocAsync((void**)&acc, sizeof(double) * 2 * s, st));
@@ -106,17 +115,17 @@ int backward_error_fp64(const Handle* h, int s, const double* shifts, const doub
   if (e != cudaSuccess) { set_cuda_error(e); rc = SSV_ECUDA; }
   const int m = h->m;
   if (rc == SSV_OK) {
-    if (m <= 1) rc = launch<1>(h, s, shifts, Xhat, ldx, resid, acc, st);
-    else if (m <= 2) rc = launch<2>(h, s, shifts, Xhat, ldx, resid, acc, st);
-    else if (m <= 4) rc = launch<4>(h, s, shifts, Xhat, ldx, resid, acc, st);
-    else if (m <= 8) rc = launch<8>(h, s, shifts, Xhat, ldx, resid, acc, st);
-    else if (m <= 16) rc = launch<16>(h, s, shifts, Xhat, ldx, resid, acc, st);
-    else rc = launch<32>(h, s, shifts, Xhat, ldx, resid, acc, st);
+    if (m <= 1) rc = launch<1>(h, s, shifts, Xhat, ldx, resid, acc, mask, st);
+    else if (m <= 2) rc = launch<2>(h, s, shifts, Xhat, ldx, resid, acc, mask, st);
+    else if (m <= 4) rc = launch<4>(h, s, shifts, Xhat, ldx, resid, acc, mask, st);
+    else if (m <= 8) rc = launch<8>(h, s, shifts, Xhat, ldx, resid, acc, mask, st);
+    else if (m <= 16) rc = launch<16>(h, s, shifts, Xhat, ldx, resid, acc, mask, st);
+    else rc = launch<32>(h, s, shifts, Xhat, ldx, resid, acc, mask, st);
   }
   if (rc == SSV_OK) {
     residual_finish_kernel<<<(s + 127) / 128, 128, 0, st>>>(h->n, m, s, h->hnorm2, h->R,
                                                             reinterpret_cast<const cd*>(shifts),
-                                                            acc, resid);
+                                                            acc, resid, mask);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(e); rc = SSV_ECUDA; }

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
     int ldct, const double* __restrict__ R, int s, const cd* __restrict__ shifts, int mode,
     cd* __restrict__ scratch, size_t slot_stride, cd* __restrict__ out, long long ldo,
     int* __restrict__ status, cd* __restrict__ xhat_copy, long long ldxc,
-    const double* __restrict__ hnorm) {
+    const double* __restrict__ hnorm, const int* __restrict__ mask) {
   using L = Layout<MAXM>;
   constexpr int S = L::kSlots;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
   cd* ZT = Z2 + (size_t)ldz * m;  // n x m, valid when track_t
 
   for (int sh = blockIdx.x; sh < s; sh += gridDim.x) {
+    if (mask != nullptr && mask[sh] == 0) continue;  // uniform across the block
     const cd sigma = shifts[sh];
     // ||H - sigma I||_F from ||H||_F^2 and trace(H); a finalized diagonal entry
     // of magnitude <= n eps ||H - sigma I||_F marks the shift singular.
@@ -389,7 +390,8 @@ __global__ void nonfinite_kernel(const cd* __restrict__ out, long long ldo, int 
 
 template <int MAXM>
 int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode, double* out,
-                 long long ldo, int* status, cd* xhat_copy, long long ldxc, cudaStream_t st) {
+                 long long ldo, int* status, cd* xhat_copy, long long ldxc, cudaStream_t st,
+                 const int* mask = nullptr) {
   using L = Layout<MAXM>;
   const int n = h->n, m = h->m, p = h->p;
   const bool track_t = (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
@@ -407,7 +409,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
   kern<<<grid, kThreads, L::bytes, st>>>(n, m, p, nb, h->H, h->Ct, p > 0 ? p : 1, h->R, s,
                                          reinterpret_cast<const cd*>(shifts), mode, scratch, slot,
                                          reinterpret_cast<cd*>(out), ldo, status, xhat_copy, ldxc,
-                                         h->hnorm2);
+                                         h->hnorm2, mask);
   count_launch();
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaFreeAsync(scratch, st);
@@ -416,7 +418,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
     set_cuda_error(e);
     return SSV_ECUDA;
   }
-  if (status != nullptr) {
+  if (status != nullptr && mask == nullptr) {
     int rows = (mode == SSV_G || mode == SSV_TF) ? p : n;
     if (rows > 0) {
       nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows, m, s, status);
@@ -433,6 +435,23 @@ int default_nb(int n, int m) {
   (void)n;
   (void)m;
   return kNB;
+}
+
+int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, int nb,
+                      double* out, long long ldo, int* status, const int* mask, void* xhat_copy,
+                      long long ldxc, cudaStream_t st) {
+  const int m = h->m;
+  if (nb <= 0) nb = default_nb(h->n, m);
+  if (nb > kNB) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  cd* xc = reinterpret_cast<cd*>(xhat_copy);
+  if (m <= 1) return launch_solve<1>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
+  if (m <= 2) return launch_solve<2>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
+  if (m <= 4) return launch_solve<4>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
+  if (m <= 8) return launch_solve<8>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
+  if (m <= 16) return launch_solve<16>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
+  if (m <= 32) return launch_solve<32>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
+  return SSV_ENOTSUP;
 }
 
 size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) {
@@ -542,7 +561,7 @@ int launch_solve_noalloc(const Handle* h, int s, const double* shifts, int nb, i
                                          reinterpret_cast<const cd*>(shifts), mode,
                                          reinterpret_cast<cd*>(base), slot,
                                          reinterpret_cast<cd*>(out), ldo, status, nullptr, 0,
-                                         h->hnorm2);
+                                         h->hnorm2, nullptr);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   if (status != nullptr) {

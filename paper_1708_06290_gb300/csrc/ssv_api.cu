@@ -36,11 +36,14 @@ static void free_handle_buffers(Handle* h) {
   cudaFree(h->tauB);
   cudaFree(h->tauA);
   cudaFree(h->hnorm2);
+  cudaFree(h->Hhi);
+  cudaFree(h->Hlo);
 }
 
 static size_t handle_bytes(int n, int m, int p) {
   size_t b = sizeof(double) * ((size_t)n * n + (size_t)n * m + (size_t)(p > 0 ? p : 1) * n +
-                               (size_t)m + (size_t)n + 2);
+                               (size_t)m + (size_t)n + 2) +
+             2 * sizeof(float) * (size_t)n * n;
   return b;
 }
 
@@ -63,8 +66,8 @@ void ssv_default_opts(ssv_opts* o) {
   o->mode = SSV_G;
   o->nb = 0;
   o->tile = 0;
-  o->max_refine = 6;
-  o->tol = 1e-13;
+  o->max_refine = 8;
+  o->tol = 1e-14;
 }
 
 static int make_handle(int n, int m, int p, cudaStream_t st, Handle** out) {
@@ -86,6 +89,8 @@ static int make_handle(int n, int m, int p, cudaStream_t st, Handle** out) {
   alloc(&h->tauB, (size_t)m);
   alloc(&h->tauA, (size_t)n);
   alloc(&h->hnorm2, 2);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->Hhi, sizeof(float) * (size_t)n * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->Hlo, sizeof(float) * (size_t)n * n);
   if (e == cudaSuccess && p == 0) e = cudaMemsetAsync(h->Ct, 0, sizeof(double) * n, st);
   if (e != cudaSuccess) {
     set_cuda_error(e);
@@ -110,6 +115,7 @@ int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double
   int rc = make_handle(n, m, p, st, &h);
   if (rc != SSV_OK) return rc;
   rc = reduce_fp64(h, A, lda, B, ldb, C, ldc, st);
+  if (rc == SSV_OK) rc = split_h(h, st);
   if (rc != SSV_OK) {
     cudaStreamSynchronize(st);
     free_handle_buffers(h);
@@ -133,6 +139,7 @@ int ssv_load_reduced(int n, int m, int p, const double* H, long long ldh, const 
   int rc = make_handle(n, m, p, st, &h);
   if (rc != SSV_OK) return rc;
   rc = load_reduced(h, H, ldh, R, ldr, Ct, ldc, st);
+  if (rc == SSV_OK) rc = split_h(h, st);
   if (rc != SSV_OK) {
     cudaStreamSynchronize(st);
     free_handle_buffers(h);
@@ -156,10 +163,10 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
   const bool gmode = (o.mode == SSV_G || o.mode == SSV_TF);
   if (gmode && ldo < (h->p > 0 ? h->p : 1)) return SSV_EINVAL;
   if (!gmode && ldo < h->n) return SSV_EINVAL;
-  if (o.precision != SSV_FP64) return SSV_ENOTSUP;
   if (o.mode == SSV_X && !h->has_q) return SSV_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
-  rc = solve_fp64(h, s, shifts, &o, out, ldo, status, resid, st);
+  if (o.precision == SSV_MIXED) rc = solve_mixed(h, s, shifts, &o, out, ldo, status, resid, st);
+  else rc = solve_fp64(h, s, shifts, &o, out, ldo, status, resid, st);
   if (rc == SSV_OK && o.mode == SSV_X) rc = apply_q_fp64(h, s * h->m, out, ldo, out, ldo, st);
   return rc;
 }
@@ -215,7 +222,8 @@ int ssv_footprint(int n, int m, int p, int s, const ssv_opts* o_in, size_t* byte
   if (o_in) o = *o_in; else ssv_default_opts(&o);
   int rc = check_opts(&o);
   if (rc != SSV_OK) return rc;
-  *bytes = solve_fp64_scratch_bytes(n, m, p, s, &o);
+  *bytes = o.precision == SSV_MIXED ? solve_mixed_scratch_bytes(n, m, p, s, &o)
+                                    : solve_fp64_scratch_bytes(n, m, p, s, &o);
   return SSV_OK;
 }
 

@@ -52,7 +52,9 @@ struct Handle {
   double* Ct;     // max(p,1) x n, ld max(p,1)
   double* tauB;   // m
   double* tauA;   // n
-  double* hnorm2; // 1: ||H||_F^2 (for backward errors)
+  double* hnorm2; // 2: ||H||_F^2 and trace(H) of the structural part
+  float* Hhi;     // n x n: fl32(H) on and above the m-th subdiagonal, 0 below
+  float* Hlo;     // n x n: fl32(H - Hhi), 0 below (Hhi + Hlo carries 48 bits of H)
   int kb;         // number of Q_B reflectors
   int ka;         // number of Q_A reflectors
   int has_q;      // 0 when built by ssv_load_reduced
@@ -86,10 +88,23 @@ int get_reduced(const Handle* h, double* H, long long ldh, double* R, long long 
 // solver (solve_fp64.cu)
 int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                long long ldo, int* status, double* resid, cudaStream_t st);
+// FP64 solve restricted to the shifts with mask[j] != 0 (others untouched)
+int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, int nb,
+                      double* out, long long ldo, int* status, const int* mask, void* xhat_copy,
+                      long long ldxc, cudaStream_t st);
+// mixed-precision solve with FP64-accurate refinement (solve_mixed.cu)
+int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
+                long long ldo, int* status, double* resid, cudaStream_t st);
+size_t solve_mixed_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o);
+// split H into the FP32 pair (Hhi, Hlo) (reduce_fp64.cu)
+int split_h(Handle* h, cudaStream_t st);
 size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o);
 // normwise backward error of computed Xhat (residual_fp64.cu)
 int backward_error_fp64(const Handle* h, int s, const double* shifts, const double* Xhat,
                         long long ldx, double* resid, cudaStream_t st);
+// same, only for the shifts with mask[j] != 0
+int backward_error_fp64_masked(const Handle* h, int s, const double* shifts, const double* Xhat,
+                               long long ldx, double* resid, const int* mask, cudaStream_t st);
 
 // allocation-free FP64 solve on the library's fixed scratch array (solve_fp64.cu)
 int solve_fp64_noalloc(const Handle* h, int s, const double* shifts, const ssv_opts* o,

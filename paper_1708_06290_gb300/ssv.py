@@ -145,7 +145,7 @@ def _need_cuda(t, dtype, name):
         raise ValueError("%s must be %s" % (name, dtype))
 
 
-def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=6, tol=1e-13):
+def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-14):
     o = Opts()
     load().ssv_default_opts(ctypes.byref(o))
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
@@ -185,7 +185,7 @@ class Handle:
     def out_rows(self, mode):
         return self.p if _MODES.get(mode, mode) in (G, TF) else self.n
 
-    def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=6, tol=1e-13,
+    def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=8, tol=1e-14,
               out=None, status=None, resid=None, want_resid=False, stream=None):
         """Solve all shifts.  Returns (out, status, resid).
 
