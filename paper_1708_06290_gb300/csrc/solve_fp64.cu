@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
     int ldct, const double* __restrict__ R, int s, const cd* __restrict__ shifts, int mode,
     cd* __restrict__ scratch, size_t slot_stride, cd* __restrict__ out, long long ldo,
     int* __restrict__ status, cd* __restrict__ xhat_copy, long long ldxc,
-    const double* __restrict__ hnorm, const int* __restrict__ mask) {
+    const double* __restrict__ hnorm, const int* __restrict__ list,
+    const int* __restrict__ count) {
   using L = Layout<MAXM>;
   constexpr int S = L::kSlots;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -75,8 +76,10 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
   cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
   cd* ZT = Z2 + (size_t)ldz * m;  // n x m, valid when track_t
 
-  for (int sh = blockIdx.x; sh < s; sh += gridDim.x) {
-    if (mask != nullptr && mask[sh] == 0) continue;  // uniform across the block
+  // With a work list, the block takes list entries blockIdx.x, +gridDim.x, ...
+  const int nwork = list != nullptr ? *count : s;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int sh = list != nullptr ? list[w] : w;
     const cd sigma = shifts[sh];
     // ||H - sigma I||_F from ||H||_F^2 and trace(H); a finalized diagonal entry
     // of magnitude <= n eps ||H - sigma I||_F marks the shift singular.
@@ -391,7 +394,7 @@ __global__ void nonfinite_kernel(const cd* __restrict__ out, long long ldo, int 
 template <int MAXM>
 int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode, double* out,
                  long long ldo, int* status, cd* xhat_copy, long long ldxc, cudaStream_t st,
-                 const int* mask = nullptr) {
+                 const int* list = nullptr, const int* count = nullptr) {
   using L = Layout<MAXM>;
   const int n = h->n, m = h->m, p = h->p;
   const bool track_t = (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
@@ -409,7 +412,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
   kern<<<grid, kThreads, L::bytes, st>>>(n, m, p, nb, h->H, h->Ct, p > 0 ? p : 1, h->R, s,
                                          reinterpret_cast<const cd*>(shifts), mode, scratch, slot,
                                          reinterpret_cast<cd*>(out), ldo, status, xhat_copy, ldxc,
-                                         h->hnorm2, mask);
+                                         h->hnorm2, list, count);
   count_launch();
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaFreeAsync(scratch, st);
@@ -418,7 +421,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
     set_cuda_error(e);
     return SSV_ECUDA;
   }
-  if (status != nullptr && mask == nullptr) {
+  if (status != nullptr && list == nullptr) {
     int rows = (mode == SSV_G || mode == SSV_TF) ? p : n;
     if (rows > 0) {
       nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows, m, s, status);
@@ -437,6 +440,30 @@ int default_nb(int n, int m) {
   return kNB;
 }
 
+// Work list of the shifts with mask[j] != 0 (single block, order preserved).
+__global__ void __launch_bounds__(1024) mask_to_list_kernel(int s, const int* __restrict__ mask,
+                                                            int* __restrict__ list,
+                                                            int* __restrict__ count) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x;
+  const int chunk = (s + 1023) / 1024;
+  const int b = tid * chunk, e = min(s, b + chunk);
+  int c = 0;
+  for (int j = b; j < e; ++j) c += mask[j] != 0;
+  part[tid] = c;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int v = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int pos = part[tid] - c;
+  for (int j = b; j < e; ++j)
+    if (mask[j] != 0) list[pos++] = j;
+  if (tid == 1023) *count = part[1023];
+}
+
 int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, int nb,
                       double* out, long long ldo, int* status, const int* mask, void* xhat_copy,
                       long long ldxc, cudaStream_t st) {
@@ -444,14 +471,26 @@ int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, in
   if (nb <= 0) nb = default_nb(h->n, m);
   if (nb > kNB) return SSV_ENOTSUP;
   if (s == 0) return SSV_OK;
+  int* list = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&list, sizeof(int) * ((size_t)s + 1), st));
+  int* count = list + s;
+  mask_to_list_kernel<<<1, 1024, 0, st>>>(s, mask, list, count);
+  count_launch();
   cd* xc = reinterpret_cast<cd*>(xhat_copy);
-  if (m <= 1) return launch_solve<1>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
-  if (m <= 2) return launch_solve<2>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
-  if (m <= 4) return launch_solve<4>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
-  if (m <= 8) return launch_solve<8>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
-  if (m <= 16) return launch_solve<16>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
-  if (m <= 32) return launch_solve<32>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, mask);
-  return SSV_ENOTSUP;
+  int rc;
+  if (m <= 1) rc = launch_solve<1>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, list, count);
+  else if (m <= 2) rc = launch_solve<2>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, list, count);
+  else if (m <= 4) rc = launch_solve<4>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, list, count);
+  else if (m <= 8) rc = launch_solve<8>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, list, count);
+  else if (m <= 16) rc = launch_solve<16>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, list, count);
+  else if (m <= 32) rc = launch_solve<32>(h, s, shifts, nb, mode, out, ldo, status, xc, ldxc, st, list, count);
+  else rc = SSV_ENOTSUP;
+  cudaError_t e = cudaFreeAsync(list, st);
+  if (e != cudaSuccess && rc == SSV_OK) {
+    set_cuda_error(e);
+    rc = SSV_ECUDA;
+  }
+  return rc;
 }
 
 size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) {
@@ -561,7 +600,7 @@ int launch_solve_noalloc(const Handle* h, int s, const double* shifts, int nb, i
                                          reinterpret_cast<const cd*>(shifts), mode,
                                          reinterpret_cast<cd*>(base), slot,
                                          reinterpret_cast<cd*>(out), ldo, status, nullptr, 0,
-                                         h->hnorm2, nullptr);
+                                         h->hnorm2, nullptr, nullptr);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   if (status != nullptr) {

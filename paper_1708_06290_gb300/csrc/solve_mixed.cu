@@ -134,6 +134,127 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
   __syncthreads();
 }
 
+// a0/a1 (rows ia, ib < r) += sum_c Hhi(row, j0 + c) * P(c, :), P rows of `ps`
+// complex entries in shared memory (16-byte aligned rows when MAXM >= 2).
+template <int MAXM>
+__device__ __forceinline__ void rows_real_times(const float* __restrict__ Hhi, int n, int j0,
+                                                int nbe, int ia, int ib, int r, const cf* P,
+                                                int ps, cf* a0, cf* a1) {
+  const bool va = ia < r, vb = ib < r;
+  for (int c0 = 0; c0 < nbe; c0 += 4) {
+    float za[4], zb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      za[u] = (va && c < nbe) ? Hhi[ia + (size_t)(j0 + c) * n] : 0.f;
+      zb[u] = (vb && c < nbe) ? Hhi[ib + (size_t)(j0 + c) * n] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      if (c >= nbe) break;
+      const cf* pr = P + c * ps;
+      if constexpr (MAXM >= 2) {
+        const float4* p4 = reinterpret_cast<const float4*>(pr);
+#pragma unroll
+        for (int q2 = 0; q2 < MAXM / 2; ++q2) {
+          const float4 w = p4[q2];
+          a0[2 * q2].x = fmaf(za[u], w.x, a0[2 * q2].x);
+          a0[2 * q2].y = fmaf(za[u], w.y, a0[2 * q2].y);
+          a0[2 * q2 + 1].x = fmaf(za[u], w.z, a0[2 * q2 + 1].x);
+          a0[2 * q2 + 1].y = fmaf(za[u], w.w, a0[2 * q2 + 1].y);
+          a1[2 * q2].x = fmaf(zb[u], w.x, a1[2 * q2].x);
+          a1[2 * q2].y = fmaf(zb[u], w.y, a1[2 * q2].y);
+          a1[2 * q2 + 1].x = fmaf(zb[u], w.z, a1[2 * q2 + 1].x);
+          a1[2 * q2 + 1].y = fmaf(zb[u], w.w, a1[2 * q2 + 1].y);
+        }
+      } else {
+        const cf w = pr[0];
+        a0[0].x = fmaf(za[u], w.x, a0[0].x);
+        a0[0].y = fmaf(za[u], w.y, a0[0].y);
+        a1[0].x = fmaf(zb[u], w.x, a1[0].x);
+        a1[0].y = fmaf(zb[u], w.y, a1[0].y);
+      }
+    }
+  }
+}
+
+// a0/a1 += sum_qq Z(row, qq) * P(qq, :) for complex Z (n x m, ld n), rows < lim.
+template <int MAXM>
+__device__ __forceinline__ void rows_complex_times(const cf* __restrict__ Z, int n, int m, int ia,
+                                                   int ib, int lim, const cf* P, int ps, cf* a0,
+                                                   cf* a1) {
+  const bool va = ia < lim, vb = ib < lim;
+  for (int qq = 0; qq < m; ++qq) {
+    const cf za = va ? Z[ia + (size_t)qq * n] : mkcf(0.f, 0.f);
+    const cf zb = vb ? Z[ib + (size_t)qq * n] : mkcf(0.f, 0.f);
+    const cf* pr = P + qq * ps;
+    if constexpr (MAXM >= 2) {
+      const float4* p4 = reinterpret_cast<const float4*>(pr);
+#pragma unroll
+      for (int q2 = 0; q2 < MAXM / 2; ++q2) {
+        const float4 w = p4[q2];
+        const cf w0 = mkcf(w.x, w.y), w1 = mkcf(w.z, w.w);
+        a0[2 * q2] = cfmaf(za, w0, a0[2 * q2]);
+        a0[2 * q2 + 1] = cfmaf(za, w1, a0[2 * q2 + 1]);
+        a1[2 * q2] = cfmaf(zb, w0, a1[2 * q2]);
+        a1[2 * q2 + 1] = cfmaf(zb, w1, a1[2 * q2 + 1]);
+      }
+    } else {
+      a0[0] = cfmaf(za, pr[0], a0[0]);
+      a1[0] = cfmaf(zb, pr[0], a1[0]);
+    }
+  }
+}
+
+// Same for T rows: only rows >= lo (and < n) are multiplied.
+template <int MAXM>
+__device__ __forceinline__ void rows_complex_times_from(const cf* __restrict__ Z, int n, int m,
+                                                        int ia, int ib, int lo, const cf* P, int ps,
+                                                        cf* a0, cf* a1) {
+  const bool va = ia < n && ia >= lo, vb = ib < n && ib >= lo;
+  for (int qq = 0; qq < m; ++qq) {
+    const cf za = va ? Z[ia + (size_t)qq * n] : mkcf(0.f, 0.f);
+    const cf zb = vb ? Z[ib + (size_t)qq * n] : mkcf(0.f, 0.f);
+    const cf* pr = P + qq * ps;
+    if constexpr (MAXM >= 2) {
+      const float4* p4 = reinterpret_cast<const float4*>(pr);
+#pragma unroll
+      for (int q2 = 0; q2 < MAXM / 2; ++q2) {
+        const float4 w = p4[q2];
+        const cf w0 = mkcf(w.x, w.y), w1 = mkcf(w.z, w.w);
+        a0[2 * q2] = cfmaf(za, w0, a0[2 * q2]);
+        a0[2 * q2 + 1] = cfmaf(za, w1, a0[2 * q2 + 1]);
+        a1[2 * q2] = cfmaf(zb, w0, a1[2 * q2]);
+        a1[2 * q2 + 1] = cfmaf(zb, w1, a1[2 * q2 + 1]);
+      }
+    } else {
+      a0[0] = cfmaf(za, pr[0], a0[0]);
+      a1[0] = cfmaf(zb, pr[0], a1[0]);
+    }
+  }
+}
+
+// Shifted diagonal of fresh column c (< min(m, nbe)) lies in window row r - m + c.
+template <int MAXM>
+__device__ __forceinline__ void diag_correction(int ia, int ib, int r, int m, int nbe, cf sigma,
+                                                const cf* P, int ps, cf* a0, cf* a1) {
+  const int ca = ia - (r - m), cb = ib - (r - m);
+  const int lim = min(m, nbe);
+  if (ia < r && ca >= 0 && ca < lim) {
+    const cf* pr = P + ca * ps;
+#pragma unroll
+    for (int q = 0; q < MAXM; ++q)
+      if (q < m) a0[q] = cfmsf(sigma, pr[q], a0[q]);
+  }
+  if (ib < r && cb >= 0 && cb < lim) {
+    const cf* pr = P + cb * ps;
+#pragma unroll
+    for (int q = 0; q < MAXM; ++q)
+      if (q < m) a1[q] = cfmsf(sigma, pr[q], a1[q]);
+  }
+}
+
 // One complex64 elimination sweep over H - sigma I (rows n-1 .. m).
 // Live columns Zl (n x m), their T rows Tl (n x m).  With RHS, the dense
 // right-hand side Zr (n x m) is back-substituted on the fly and its T rows
@@ -280,112 +401,81 @@ __device__ void sweep(const int n, const int m, const int nb, const float* __res
       __syncthreads();
     }
 
-    // ---- rows above the block
-    for (int i = tid; i < r; i += kThreads) {
-      cf al[MAXM];
-      cf ar[RHS ? MAXM : 1];
+    // ---- rows above the block, two rows per thread (i, i + kThreads).  With
+    // a right-hand side its pass runs first (it reads the old live columns);
+    // each thread owns its rows in both passes, so no barrier is needed between.
+    if (RHS) {
+      for (int i0 = 0; i0 < r; i0 += 2 * kThreads) {
+        const int ia = i0 + tid, ib = ia + kThreads;
+        cf a0[MAXM], a1[MAXM];
 #pragma unroll
-      for (int q = 0; q < MAXM; ++q) al[q] = mkcf(0.0f, 0.0f);
-      if (RHS) {
-#pragma unroll
-        for (int q = 0; q < MAXM; ++q)
-          if (q < m) ar[q] = Zr[i + (size_t)q * n];
-      }
-      for (int c = 0; c < nbe; ++c) {
-        const float z = Hhi[i + (size_t)(j0 + c) * n];
-        const cf* cr = sm.coef + c * S;
+        for (int q = 0; q < MAXM; ++q) {
+          a0[q] = (ia < r && q < m) ? Zr[ia + (size_t)q * n] : mkcf(0.f, 0.f);
+          a1[q] = (ib < r && q < m) ? Zr[ib + (size_t)q * n] : mkcf(0.f, 0.f);
+        }
+        rows_real_times<MAXM>(Hhi, n, j0, nbe, ia, ib, r, sm.coefr, MAXM, a0, a1);
+        rows_complex_times<MAXM>(Zl, n, m, ia, ib, r, sm.coefr + kNB * MAXM, MAXM, a0, a1);
+        diag_correction<MAXM>(ia, ib, r, m, nbe, sigma, sm.coefr, MAXM, a0, a1);
 #pragma unroll
         for (int q = 0; q < MAXM; ++q) {
           if (q < m) {
-            al[q].x = fmaf(z, cr[q].x, al[q].x);
-            al[q].y = fmaf(z, cr[q].y, al[q].y);
+            if (ia < r) Zr[ia + (size_t)q * n] = a0[q];
+            if (ib < r) Zr[ib + (size_t)q * n] = a1[q];
           }
-        }
-        if (RHS) {
-          const cf* rr = sm.coefr + c * MAXM;
-#pragma unroll
-          for (int q = 0; q < MAXM; ++q) {
-            if (q < m) {
-              ar[q].x = fmaf(z, rr[q].x, ar[q].x);
-              ar[q].y = fmaf(z, rr[q].y, ar[q].y);
-            }
-          }
-        }
-      }
-      for (int qq = 0; qq < m; ++qq) {
-        const cf zz = Zl[i + (size_t)qq * n];
-        const cf* cr = sm.coef + (kNB + qq) * S;
-#pragma unroll
-        for (int q = 0; q < MAXM; ++q)
-          if (q < m) al[q] = cfmaf(zz, cr[q], al[q]);
-        if (RHS) {
-          const cf* rr = sm.coefr + (kNB + qq) * MAXM;
-#pragma unroll
-          for (int q = 0; q < MAXM; ++q)
-            if (q < m) ar[q] = cfmaf(zz, rr[q], ar[q]);
-        }
-      }
-      const int cd_ = i - (r - m);
-      if (cd_ >= 0 && cd_ < min(m, nbe)) {
-        const cf* cr = sm.coef + cd_ * S;
-#pragma unroll
-        for (int q = 0; q < MAXM; ++q)
-          if (q < m) al[q] = cfmsf(sigma, cr[q], al[q]);
-        if (RHS) {
-          const cf* rr = sm.coefr + cd_ * MAXM;
-#pragma unroll
-          for (int q = 0; q < MAXM; ++q)
-            if (q < m) ar[q] = cfmsf(sigma, rr[q], ar[q]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < MAXM; ++q) {
-        if (q < m) {
-          Zl[i + (size_t)q * n] = al[q];
-          if (RHS) Zr[i + (size_t)q * n] = ar[q];
         }
       }
     }
-    // ---- T rows j0 .. n-1
+    for (int i0 = 0; i0 < r; i0 += 2 * kThreads) {
+      const int ia = i0 + tid, ib = ia + kThreads;
+      cf a0[MAXM], a1[MAXM];
+#pragma unroll
+      for (int q = 0; q < MAXM; ++q) { a0[q] = mkcf(0.f, 0.f); a1[q] = mkcf(0.f, 0.f); }
+      rows_real_times<MAXM>(Hhi, n, j0, nbe, ia, ib, r, sm.coef, S, a0, a1);
+      rows_complex_times<MAXM>(Zl, n, m, ia, ib, r, sm.coef + kNB * S, S, a0, a1);
+      diag_correction<MAXM>(ia, ib, r, m, nbe, sigma, sm.coef, S, a0, a1);
+#pragma unroll
+      for (int q = 0; q < MAXM; ++q) {
+        if (q < m) {
+          if (ia < r) Zl[ia + (size_t)q * n] = a0[q];
+          if (ib < r) Zl[ib + (size_t)q * n] = a1[q];
+        }
+      }
+    }
+    // ---- T rows j0 .. n-1: fresh rows take the coefficients, the others
+    // are multiplied by the old-live block (RHS pass first, as above).
     {
       const int lo = k - m;
-      for (int i = j0 + tid; i < n; i += kThreads) {
-        cf al[MAXM];
-        cf ar[RHS ? MAXM : 1];
-        if (i < lo) {
+      const int nt = n - j0;
+      if (RHS) {
+        for (int t0 = 0; t0 < nt; t0 += 2 * kThreads) {
+          const int ia = j0 + t0 + tid, ib = ia + kThreads;
+          cf a0[MAXM], a1[MAXM];
 #pragma unroll
-          for (int q = 0; q < MAXM; ++q) al[q] = sm.coef[(i - j0) * S + q];
-          if (RHS) {
-#pragma unroll
-            for (int q = 0; q < MAXM; ++q) ar[q] = sm.coefr[(i - j0) * MAXM + q];
+          for (int q = 0; q < MAXM; ++q) {
+            a0[q] = (ia < n && ia >= lo && q < m) ? Tr[ia + (size_t)q * n] : mkcf(0.f, 0.f);
+            a1[q] = (ib < n && ib >= lo && q < m) ? Tr[ib + (size_t)q * n] : mkcf(0.f, 0.f);
           }
-        } else {
+          rows_complex_times_from<MAXM>(Tl, n, m, ia, ib, lo, sm.coefr + kNB * MAXM, MAXM, a0, a1);
 #pragma unroll
-          for (int q = 0; q < MAXM; ++q) al[q] = mkcf(0.0f, 0.0f);
-          if (RHS) {
-#pragma unroll
-            for (int q = 0; q < MAXM; ++q)
-              if (q < m) ar[q] = Tr[i + (size_t)q * n];
-          }
-          for (int qq = 0; qq < m; ++qq) {
-            const cf tt = Tl[i + (size_t)qq * n];
-            const cf* cr = sm.coef + (kNB + qq) * S;
-#pragma unroll
-            for (int q = 0; q < MAXM; ++q)
-              if (q < m) al[q] = cfmaf(tt, cr[q], al[q]);
-            if (RHS) {
-              const cf* rr = sm.coefr + (kNB + qq) * MAXM;
-#pragma unroll
-              for (int q = 0; q < MAXM; ++q)
-                if (q < m) ar[q] = cfmaf(tt, rr[q], ar[q]);
+          for (int q = 0; q < MAXM; ++q) {
+            if (q < m) {
+              if (ia < n) Tr[ia + (size_t)q * n] = ia < lo ? sm.coefr[(ia - j0) * MAXM + q] : a0[q];
+              if (ib < n) Tr[ib + (size_t)q * n] = ib < lo ? sm.coefr[(ib - j0) * MAXM + q] : a1[q];
             }
           }
         }
+      }
+      for (int t0 = 0; t0 < nt; t0 += 2 * kThreads) {
+        const int ia = j0 + t0 + tid, ib = ia + kThreads;
+        cf a0[MAXM], a1[MAXM];
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q) { a0[q] = mkcf(0.f, 0.f); a1[q] = mkcf(0.f, 0.f); }
+        rows_complex_times_from<MAXM>(Tl, n, m, ia, ib, lo, sm.coef + kNB * S, S, a0, a1);
 #pragma unroll
         for (int q = 0; q < MAXM; ++q) {
           if (q < m) {
-            Tl[i + (size_t)q * n] = al[q];
-            if (RHS) Tr[i + (size_t)q * n] = ar[q];
+            if (ia < n) Tl[ia + (size_t)q * n] = ia < lo ? sm.coef[(ia - j0) * S + q] : a0[q];
+            if (ib < n) Tl[ib + (size_t)q * n] = ib < lo ? sm.coef[(ib - j0) * S + q] : a1[q];
           }
         }
       }
@@ -460,25 +550,110 @@ __device__ void final_solve(const int n, const int m, const cf* Zl, const cf* Zr
   __syncthreads();
 }
 
-// E = R - (H - sigma I) Xhat, FP64-accurate; E rounded to complex64 into Zr.
-// Returns ||E||_F^2 and ||Xhat||_F^2 (all threads).
-template <int MAXM>
-__device__ void residual(const int n, const int m, const float* __restrict__ Hhi,
-                         const float* __restrict__ Hlo, const double* __restrict__ R,
-                         const cd sigma, const cd* __restrict__ Xh, cf* __restrict__ Zr,
-                         Smem<MAXM>& sm, double& e2, double& x2) {
+// ---------------------------------------------------------------------------
+// Phase kernels.  All per-shift state lives in global arrays indexed by shift
+// (Xhat in complex128, E in complex64, flags, eta); the host runs sweep 0,
+// then rounds of {residual, check, compact, correction sweep}.  Shifts that are
+// finished are dropped from the active list, so later rounds cost one small
+// launch each.
+// ---------------------------------------------------------------------------
+constexpr int kFlagOk = 1;      // converged: backward error <= tol
+constexpr int kFlagFail = 2;    // stagnated / iteration limit / singular: FP64 re-solve
+constexpr int kFlagSing = 4;    // a finalised diagonal fell below the FP32 threshold
+constexpr int kRT = 128;        // residual rows per work item
+
+__device__ __forceinline__ double shifted_norm(const double* hnorm, int n, cd sigma) {
+  return sqrt(fmax(hnorm[0] - 2.0 * sigma.x * hnorm[1] +
+                       (double)n * (sigma.x * sigma.x + sigma.y * sigma.y), 0.0));
+}
+
+// Sweep 0 (RHS = false: Xhat = T(:, live) Wm^{-1} R1) or a correction sweep
+// (RHS = true: E, in place, is the dense right-hand side; Xhat += T Y - Tr).
+template <int MAXM, bool RHS>
+__global__ void __launch_bounds__(kThreads, 2) mixed_sweep_kernel(
+    int n, int m, int nb, const float* __restrict__ Hhi, const double* __restrict__ R,
+    const cd* __restrict__ shifts, const int* __restrict__ list, const int* __restrict__ count,
+    unsigned char* __restrict__ slots, size_t slot_bytes, cd* __restrict__ Xall,
+    cf* __restrict__ Eall, int* __restrict__ flags, const double* __restrict__ hnorm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<MAXM> sm;
+  sm.bind(smem_raw);
+  __shared__ int s_flag;
+  __shared__ int s_piv;
   const int tid = threadIdx.x;
-  e2 = 0.0;
-  x2 = 0.0;
-  for (int i0 = 0; i0 < n; i0 += kThreads) {
+  const size_t nm = (size_t)n * m;
+  cf* Zl = reinterpret_cast<cf*>(slots + (size_t)blockIdx.x * slot_bytes);
+  cf* Tl = Zl + nm;
+  cf* Tr = Tl + nm;
+  const int cnt = *count;
+  for (int w = blockIdx.x; w < cnt; w += gridDim.x) {
+    const int sh = list[w];
+    const cd sigma = shifts[sh];
+    const cf sigf = mkcf((float)sigma.x, (float)sigma.y);
+    const float sing_tol = (float)((double)n * 1.1920928955078125e-07 * shifted_norm(hnorm, n, sigma));
+    cf* Zr = Eall + (size_t)sh * nm;
+    cd* Xh = Xall + (size_t)sh * nm;
+    if (tid == 0) s_flag = 0;
+    __syncthreads();
+    sweep<MAXM, RHS>(n, m, nb, Hhi, sigf, Zl, Zr, Tl, Tr, sm, sing_tol, &s_flag);
+    final_solve<MAXM, RHS>(n, m, Zl, Zr, R, sm, sing_tol, &s_flag, &s_piv);
+    for (long long idx = tid; idx < (long long)nm; idx += kThreads) {
+      const int i = (int)(idx % n), q = (int)(idx / n);
+      float ar = 0.f, ai = 0.f;
+      if (RHS) {
+        const cf tr = Tr[idx];
+        ar = -tr.x;
+        ai = -tr.y;
+      }
+      for (int t = 0; t < m; ++t) {
+        const cf a = Tl[i + (size_t)t * n];
+        const cf y = sm.yb[t + q * MAXM];
+        ar = fmaf(a.x, y.x, fmaf(-a.y, y.y, ar));
+        ai = fmaf(a.x, y.y, fmaf(a.y, y.x, ai));
+      }
+      if (RHS) {
+        cd x = Xh[idx];
+        x.x += (double)ar;
+        x.y += (double)ai;
+        Xh[idx] = x;
+      } else {
+        Xh[idx] = mkcd(ar, ai);
+      }
+    }
+    if (tid == 0 && s_flag) flags[sh] |= kFlagSing;
+    __syncthreads();
+  }
+}
+
+// E = R - (H - sigma I) Xhat for rows [i0, i0 + kRT) of one shift, with
+// H = Hhi + Hlo and Xhat split into FP32 pairs, exact FMA products and
+// double-float accumulation.  E is stored as complex64; ||E||_F^2 and
+// ||Xhat||_F^2 are accumulated per shift in acc (FP64 atomics).
+template <int MAXM>
+__global__ void __launch_bounds__(kRT) mixed_residual_kernel(
+    int n, int m, const float* __restrict__ Hhi, const float* __restrict__ Hlo,
+    const double* __restrict__ R, const cd* __restrict__ shifts, const int* __restrict__ list,
+    const int* __restrict__ count, const cd* __restrict__ Xall, cf* __restrict__ Eall,
+    double* __restrict__ acc) {
+  __shared__ float4 xs[kJT * MAXM];
+  __shared__ double red[2][kRT / 32];
+  const int tid = threadIdx.x;
+  const int rt = (n + kRT - 1) / kRT;
+  const int cnt = *count;
+  const size_t nm = (size_t)n * m;
+  for (long long w = blockIdx.x; w < (long long)cnt * rt; w += gridDim.x) {
+    const int sh = list[w / rt];
+    const int i0 = (int)(w % rt) * kRT;
     const int i = i0 + tid;
+    const cd sigma = shifts[sh];
+    const cd* Xh = Xall + (size_t)sh * nm;
     float rh[MAXM], rl[MAXM], ih[MAXM], il[MAXM];
 #pragma unroll
     for (int q = 0; q < MAXM; ++q) { rh[q] = 0.f; rl[q] = 0.f; ih[q] = 0.f; il[q] = 0.f; }
     const int jlo = max(0, i0 - m);
     for (int jt = jlo; jt < n; jt += kJT) {
       __syncthreads();
-      for (int idx = tid; idx < kJT * m; idx += kThreads) {
+      for (int idx = tid; idx < kJT * m; idx += kRT) {
         const int jj = idx % kJT, q = idx / kJT;
         const int j = jt + jj;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -487,191 +662,281 @@ __device__ void residual(const int n, const int m, const float* __restrict__ Hhi
           const float a = (float)x.x, b = (float)x.y;
           v = make_float4(a, (float)(x.x - (double)a), b, (float)(x.y - (double)b));
         }
-        sm.xs[jj * MAXM + q] = v;
+        xs[jj * MAXM + q] = v;
       }
       __syncthreads();
       if (i < n) {
         const int jend = min(kJT, n - jt);
-        for (int jj = 0; jj < jend; ++jj) {
-          const int j = jt + jj;
-          float hh = 0.f, hl = 0.f;
-          if (j >= i - m) {
-            hh = Hhi[i + (size_t)j * n];
-            hl = Hlo[i + (size_t)j * n];
+        for (int jj0 = 0; jj0 < jend; jj0 += 4) {
+          float hh[4], hl[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = jt + jj0 + u;
+            hh[u] = 0.f;
+            hl[u] = 0.f;
+            if (jj0 + u < jend && j >= i - m) {
+              hh[u] = Hhi[i + (size_t)j * n];
+              hl[u] = Hlo[i + (size_t)j * n];
+            }
           }
 #pragma unroll
-          for (int q = 0; q < MAXM; ++q) {
-            if (q < m) {
-              const float4 x = sm.xs[jj * MAXM + q];
-              df_mac(rh[q], rl[q], hh, hl, x.x, x.y);
-              df_mac(ih[q], il[q], hh, hl, x.z, x.w);
+          for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) {
+              if (q < m) {
+                const float4 x = xs[(jj0 + u) * MAXM + q];
+                df_mac(rh[q], rl[q], hh[u], hl[u], x.x, x.y);
+                df_mac(ih[q], il[q], hh[u], hl[u], x.z, x.w);
+              }
             }
           }
         }
       }
     }
+    double e2 = 0.0, x2 = 0.0;
     if (i < n) {
+      cf* E = Eall + (size_t)sh * nm;
 #pragma unroll
       for (int q = 0; q < MAXM; ++q) {
         if (q < m) {
           const cd x = Xh[i + (size_t)q * n];
           const double hxr = (double)rh[q] + (double)rl[q];
           const double hxi = (double)ih[q] + (double)il[q];
-          // E = R - H x + sigma x
           double er = -hxr + (sigma.x * x.x - sigma.y * x.y);
           double ei = -hxi + (sigma.x * x.y + sigma.y * x.x);
           if (i <= q) er += R[i + (size_t)q * n];
           e2 += er * er + ei * ei;
           x2 += x.x * x.x + x.y * x.y;
-          Zr[i + (size_t)q * n] = mkcf((float)er, (float)ei);
+          E[i + (size_t)q * n] = mkcf((float)er, (float)ei);
         }
       }
     }
+    for (int o = 16; o > 0; o >>= 1) {
+      e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+      x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = e2;
+      red[1][tid >> 5] = x2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < kRT / 32; ++k) { a += red[0][k]; b += red[1][k]; }
+      atomicAdd(acc + 2 * (size_t)sh, a);
+      atomicAdd(acc + 2 * (size_t)sh + 1, b);
+    }
   }
-  block_sum2(e2, x2, sm.red);
 }
 
-template <int MAXM>
-__global__ void __launch_bounds__(kThreads) solve_mixed_kernel(
-    int n, int m, int p, int nb, const float* __restrict__ Hhi, const float* __restrict__ Hlo,
-    const double* __restrict__ R, const double* __restrict__ Ct, int ldct, int s,
-    const cd* __restrict__ shifts, int mode, unsigned char* __restrict__ scratch,
-    size_t slot_bytes, cd* __restrict__ out, long long ldo, int* __restrict__ status,
-    double* __restrict__ resid, int* __restrict__ fallback, const double* __restrict__ hnorm,
-    int max_refine, double tol) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<MAXM> sm;
-  sm.bind(smem_raw);
-  __shared__ int s_flag;
-  __shared__ int s_piv;
-  const int tid = threadIdx.x;
-  unsigned char* base = scratch + (size_t)blockIdx.x * slot_bytes;
-  const size_t nm = (size_t)n * m;
-  cd* Xh = reinterpret_cast<cd*>(base);
-  cf* Zl = reinterpret_cast<cf*>(base + nm * sizeof(cd));
-  cf* Zr = Zl + nm;
-  cf* Tl = Zr + nm;
-  cf* Tr = Tl + nm;
-
-  double r2 = 0.0;  // ||R(0:m,0:m)||_F^2
+// Per active shift: backward error eta from the accumulated norms; decide
+// converged (eta <= tol), failed (iteration limit, slow contraction:
+// eta > eta_prev / 4, or singular), or another correction.  Resets the
+// accumulators.
+__global__ void mixed_check_kernel(int n, int m, const double* __restrict__ R,
+                                   const cd* __restrict__ shifts, const int* __restrict__ list,
+                                   const int* __restrict__ count, double* __restrict__ acc,
+                                   double* __restrict__ eta, int* __restrict__ flags,
+                                   const double* __restrict__ hnorm, int it, int max_refine,
+                                   double tol) {
+  const int cnt = *count;
+  double r2 = 0.0;
   for (int q = 0; q < m; ++q)
     for (int i = 0; i <= q; ++i) r2 += R[i + (size_t)q * n] * R[i + (size_t)q * n];
-  const double rnorm = sqrt(r2);
-
-  for (int sh = blockIdx.x; sh < s; sh += gridDim.x) {
-    const cd sigma = shifts[sh];
-    const cf sigf = mkcf((float)sigma.x, (float)sigma.y);
-    const double mnorm = sqrt(fmax(hnorm[0] - 2.0 * sigma.x * hnorm[1] +
-                                       (double)n * (sigma.x * sigma.x + sigma.y * sigma.y), 0.0));
-    const float sing_tol = (float)((double)n * 1.1920928955078125e-07 * mnorm);
-    if (tid == 0) s_flag = 0;
-    __syncthreads();
-    // ---- sweep 0 -> Xhat0
-    sweep<MAXM, false>(n, m, nb, Hhi, sigf, Zl, Zr, Tl, Tr, sm, sing_tol, &s_flag);
-    final_solve<MAXM, false>(n, m, Zl, Zr, R, sm, sing_tol, &s_flag, &s_piv);
-    for (long long idx = tid; idx < (long long)nm; idx += kThreads) {
-      const int i = (int)(idx % n), q = (int)(idx / n);
-      float ar = 0.f, ai = 0.f;
-      for (int t = 0; t < m; ++t) {
-        const cf a = Tl[i + (size_t)t * n];
-        const cf y = sm.yb[t + q * MAXM];
-        ar = fmaf(a.x, y.x, fmaf(-a.y, y.y, ar));
-        ai = fmaf(a.x, y.y, fmaf(a.y, y.x, ai));
-      }
-      Xh[idx] = mkcd(ar, ai);
-    }
-    __syncthreads();
-    // ---- refinement
-    double eta = INFINITY, eta_prev = INFINITY;
-    bool ok = false;
-    for (int it = 0;; ++it) {
-      double e2, x2;
-      residual<MAXM>(n, m, Hhi, Hlo, R, sigma, Xh, Zr, sm, e2, x2);
-      eta = sqrt(e2) / (mnorm * sqrt(x2) + rnorm);
-      if (!(eta == eta)) break;  // NaN
-      if (eta <= tol) { ok = true; break; }
-      if (it >= max_refine || eta > 0.5 * eta_prev || s_flag) break;
-      eta_prev = eta;
-      sweep<MAXM, true>(n, m, nb, Hhi, sigf, Zl, Zr, Tl, Tr, sm, sing_tol, &s_flag);
-      final_solve<MAXM, true>(n, m, Zl, Zr, R, sm, sing_tol, &s_flag, &s_piv);
-      // Xhat += Tl Y - Tr
-      for (long long idx = tid; idx < (long long)nm; idx += kThreads) {
-        const int i = (int)(idx % n), q = (int)(idx / n);
-        const cf tr = Tr[idx];
-        float ar = -tr.x, ai = -tr.y;
-        for (int t = 0; t < m; ++t) {
-          const cf a = Tl[i + (size_t)t * n];
-          const cf y = sm.yb[t + q * MAXM];
-          ar = fmaf(a.x, y.x, fmaf(-a.y, y.y, ar));
-          ai = fmaf(a.x, y.y, fmaf(a.y, y.x, ai));
-        }
-        cd x = Xh[idx];
-        x.x += (double)ar;
-        x.y += (double)ai;
-        Xh[idx] = x;
-      }
-      __syncthreads();
-    }
-    // ---- outputs
-    if (ok) {
-      if (mode == SSV_G || mode == SSV_TF) {
-        const double sg = mode == SSV_TF ? -1.0 : 1.0;
-        cd* o = out + (size_t)sh * m * ldo;
-        for (int idx = tid; idx < p * m; idx += kThreads) {
-          const int i = idx % p, q = idx / p;
-          double ar = 0.0, ai = 0.0;
-          for (int t = 0; t < n; ++t) {
-            const double c = Ct[i + (size_t)t * ldct];
-            const cd x = Xh[t + (size_t)q * n];
-            ar = fma(c, x.x, ar);
-            ai = fma(c, x.y, ai);
-          }
-          o[i + (size_t)q * ldo] = mkcd(sg * ar, sg * ai);
-        }
-      } else {
-        cd* o = out + (size_t)sh * m * ldo;
-        for (long long idx = tid; idx < (long long)nm; idx += kThreads) {
-          const int i = (int)(idx % n), q = (int)(idx / n);
-          o[i + (size_t)q * ldo] = Xh[idx];
-        }
-      }
-    }
-    if (tid == 0) {
-      if (status) status[sh] = ok ? SSV_SHIFT_OK : SSV_SHIFT_NOT_CONVERGED;
-      if (resid) resid[sh] = eta;
-      fallback[sh] = ok ? 0 : 1;
-    }
-    __syncthreads();
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x) {
+    const int sh = list[w];
+    const double mn = shifted_norm(hnorm, n, shifts[sh]);
+    const double e2 = acc[2 * (size_t)sh], x2 = acc[2 * (size_t)sh + 1];
+    acc[2 * (size_t)sh] = 0.0;
+    acc[2 * (size_t)sh + 1] = 0.0;
+    const double den = mn * sqrt(x2) + sqrt(r2);
+    const double e = den > 0.0 ? sqrt(e2) / den : 0.0;
+    const double prev = eta[sh];
+    eta[sh] = e;
+    int f = flags[sh];
+    // A correction must shrink the backward error by at least 4x (the
+    // contraction factor of FP32-based refinement is ~kappa * u32 * growth);
+    // slower shifts go to the FP64 sweep at once instead of iterating.
+    if (e <= tol) f |= kFlagOk;
+    else if (!(e == e) || it >= max_refine || (it > 0 && e > 0.25 * prev) || (f & kFlagSing))
+      f |= kFlagFail;
+    flags[sh] = f;
   }
 }
 
+// Active list: shifts whose flags have neither kFlagOk nor kFlagFail.
+__global__ void __launch_bounds__(1024) mixed_compact_kernel(int s, const int* __restrict__ flags,
+                                                             int* __restrict__ list,
+                                                             int* __restrict__ count) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x;
+  const int chunk = (s + 1023) / 1024;
+  const int b = tid * chunk, e = min(s, b + chunk);
+  int c = 0;
+  for (int j = b; j < e; ++j) c += (flags[j] & (kFlagOk | kFlagFail)) ? 0 : 1;
+  part[tid] = c;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan
+    int v = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int pos = part[tid] - c;
+  for (int j = b; j < e; ++j)
+    if (!(flags[j] & (kFlagOk | kFlagFail))) list[pos++] = j;
+  if (tid == 1023) *count = part[1023];
+}
+
+// Outputs of converged shifts (G = +-Ct Xhat in FP64, or Xhat); the others are
+// marked for the FP64 re-solve.
+__global__ void mixed_output_kernel(int n, int m, int p, int s, int mode,
+                                    const double* __restrict__ Ct, int ldct,
+                                    const cd* __restrict__ Xall, const int* __restrict__ flags,
+                                    const double* __restrict__ eta, cd* __restrict__ out,
+                                    long long ldo, int* __restrict__ status,
+                                    double* __restrict__ resid, int* __restrict__ fallback) {
+  const size_t nm = (size_t)n * m;
+  for (int sh = blockIdx.x; sh < s; sh += gridDim.x) {
+    const bool ok = (flags[sh] & kFlagOk) != 0;
+    if (threadIdx.x == 0) {
+      fallback[sh] = ok ? 0 : 1;
+      if (ok && status) status[sh] = SSV_SHIFT_OK;
+      if (ok && resid) resid[sh] = eta[sh];
+    }
+    if (!ok) continue;
+    const cd* Xh = Xall + (size_t)sh * nm;
+    cd* o = out + (size_t)sh * m * ldo;
+    if (mode == SSV_G || mode == SSV_TF) {
+      const double sg = mode == SSV_TF ? -1.0 : 1.0;
+      for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
+        const int i = idx % p, q = idx / p;
+        double ar = 0.0, ai = 0.0;
+        for (int t = 0; t < n; ++t) {
+          const double c = Ct[i + (size_t)t * ldct];
+          const cd x = Xh[t + (size_t)q * n];
+          ar = fma(c, x.x, ar);
+          ai = fma(c, x.y, ai);
+        }
+        o[i + (size_t)q * ldo] = mkcd(sg * ar, sg * ai);
+      }
+    } else {
+      for (long long idx = threadIdx.x; idx < (long long)nm; idx += blockDim.x) {
+        const int i = (int)(idx % n), q = (int)(idx / n);
+        o[i + (size_t)q * ldo] = Xh[idx];
+      }
+    }
+  }
+}
+
+__global__ void mixed_init_kernel(int s, int* __restrict__ flags, double* __restrict__ eta,
+                                  double* __restrict__ acc, int* __restrict__ list,
+                                  int* __restrict__ count) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < s; j += gridDim.x * blockDim.x) {
+    flags[j] = 0;
+    eta[j] = INFINITY;
+    acc[2 * (size_t)j] = 0.0;
+    acc[2 * (size_t)j + 1] = 0.0;
+    list[j] = j;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = s;
+}
+
+// Scratch of one mixed solve, carved from one stream-ordered allocation.
+struct MixedScratch {
+  cd* X;         // s * n * m
+  cf* E;         // s * n * m
+  unsigned char* slots;  // grid * slot_bytes
+  double* acc;   // 2 s
+  double* eta;   // s
+  int* flags;    // s
+  int* list;     // s
+  int* fallback; // s
+  int* count;    // 1
+  size_t bytes;
+};
+
+size_t mixed_layout(int n, int m, int s, int grid, size_t slot_bytes, MixedScratch* ms,
+                    unsigned char* base) {
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += (b + 255) / 256 * 256;
+    return o;
+  };
+  const size_t nm = (size_t)n * m;
+  size_t oX = take(sizeof(cd) * nm * s), oE = take(sizeof(cf) * nm * s);
+  size_t oS = take(slot_bytes * grid), oA = take(sizeof(double) * 2 * s),
+         oT = take(sizeof(double) * s), oF = take(sizeof(int) * s), oL = take(sizeof(int) * s),
+         oB = take(sizeof(int) * s), oC = take(sizeof(int));
+  if (ms && base) {
+    ms->X = reinterpret_cast<cd*>(base + oX);
+    ms->E = reinterpret_cast<cf*>(base + oE);
+    ms->slots = base + oS;
+    ms->acc = reinterpret_cast<double*>(base + oA);
+    ms->eta = reinterpret_cast<double*>(base + oT);
+    ms->flags = reinterpret_cast<int*>(base + oF);
+    ms->list = reinterpret_cast<int*>(base + oL);
+    ms->fallback = reinterpret_cast<int*>(base + oB);
+    ms->count = reinterpret_cast<int*>(base + oC);
+    ms->bytes = off;
+  }
+  return off;
+}
+
+constexpr int kSweepBlocksPerSm = 2;
+constexpr int kResidBlocksPerSm = 8;
+
 template <int MAXM>
-int launch_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, double* out,
-                 long long ldo, int* status, double* resid, int* fallback, int max_refine,
-                 double tol, cudaStream_t st) {
+int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, double* out,
+              long long ldo, int* status, double* resid, int max_refine, double tol,
+              int** fallback_out, void** scratch_out, cudaStream_t st) {
   using L = LayoutM<MAXM>;
   const int n = h->n, m = h->m, p = h->p;
-  const size_t slot = (size_t)n * m * (sizeof(cd) + 4 * sizeof(cf));
-  auto kern = solve_mixed_kernel<MAXM>;
-  SSV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
-  int per_sm = 0;
-  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L::bytes));
-  per_sm = std::max(1, std::min(per_sm, 4));
-  const int grid = std::min(s, num_sms() * per_sm);
-  unsigned char* scratch = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&scratch, slot * grid, st));
-  kern<<<grid, kThreads, L::bytes, st>>>(n, m, p, nb, h->Hhi, h->Hlo, h->R, h->Ct, p > 0 ? p : 1, s,
-                                         reinterpret_cast<const cd*>(shifts), mode, scratch, slot,
-                                         reinterpret_cast<cd*>(out), ldo, status, resid, fallback,
-                                         h->hnorm2, max_refine, tol);
+  const size_t slot_bytes = (size_t)n * m * 3 * sizeof(cf);
+  auto k0 = mixed_sweep_kernel<MAXM, false>;
+  auto k1 = mixed_sweep_kernel<MAXM, true>;
+  SSV_CUDA_TRY(cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+  SSV_CUDA_TRY(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+  int occ0 = 0, occ1 = 0;
+  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k0, kThreads, L::bytes));
+  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k1, kThreads, L::bytes));
+  const int per_sm = std::max(1, std::min(std::max(occ0, occ1), kSweepBlocksPerSm));
+  const int grid = std::max(1, std::min(s, num_sms() * per_sm));
+  const size_t total = mixed_layout(n, m, s, grid, slot_bytes, nullptr, nullptr);
+  unsigned char* base = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&base, total, st));
+  *scratch_out = base;
+  MixedScratch ms;
+  mixed_layout(n, m, s, grid, slot_bytes, &ms, base);
+  *fallback_out = ms.fallback;
+  const cd* sd = reinterpret_cast<const cd*>(shifts);
+  mixed_init_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(s, ms.flags, ms.eta, ms.acc,
+                                                                     ms.list, ms.count);
   count_launch();
-  cudaError_t e = cudaGetLastError();
-  cudaError_t e2 = cudaFreeAsync(scratch, st);
-  if (e == cudaSuccess) e = e2;
-  if (e != cudaSuccess) {
-    set_cuda_error(e);
-    return SSV_ECUDA;
+  k0<<<grid, kThreads, L::bytes, st>>>(n, m, nb, h->Hhi, h->R, sd, ms.list, ms.count, ms.slots,
+                                      slot_bytes, ms.X, ms.E, ms.flags, h->hnorm2);
+  count_launch();
+  const int rgrid = num_sms() * kResidBlocksPerSm;
+  for (int it = 0; it <= max_refine; ++it) {
+    mixed_residual_kernel<MAXM><<<rgrid, kRT, 0, st>>>(n, m, h->Hhi, h->Hlo, h->R, sd, ms.list,
+                                                      ms.count, ms.X, ms.E, ms.acc);
+    count_launch();
+    mixed_check_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(
+        n, m, h->R, sd, ms.list, ms.count, ms.acc, ms.eta, ms.flags, h->hnorm2, it, max_refine, tol);
+    count_launch();
+    mixed_compact_kernel<<<1, 1024, 0, st>>>(s, ms.flags, ms.list, ms.count);
+    count_launch();
+    if (it == max_refine) break;
+    k1<<<grid, kThreads, L::bytes, st>>>(n, m, nb, h->Hhi, h->R, sd, ms.list, ms.count, ms.slots,
+                                        slot_bytes, ms.X, ms.E, ms.flags, h->hnorm2);
+    count_launch();
   }
+  mixed_output_kernel<<<std::min(s, num_sms() * 8), 256, 0, st>>>(
+      n, m, p, s, mode, h->Ct, p > 0 ? p : 1, ms.X, ms.flags, ms.eta,
+      reinterpret_cast<cd*>(out), ldo, status, resid, ms.fallback);
+  count_launch();
+  SSV_CUDA_TRY(cudaGetLastError());
   return SSV_OK;
 }
 
@@ -680,9 +945,9 @@ int launch_mixed(const Handle* h, int s, const double* shifts, int nb, int mode,
 size_t solve_mixed_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) {
   (void)p;
   (void)o;
-  const size_t slot = (size_t)n * m * (sizeof(cd) + 4 * sizeof(cf));
-  const size_t grid = (size_t)std::min(s, num_sms() * 4);
-  return slot * grid + sizeof(int) * (size_t)s + 256;
+  const size_t slot_bytes = (size_t)n * m * 3 * sizeof(cf);
+  const int grid = std::max(1, std::min(s, num_sms() * kSweepBlocksPerSm));
+  return mixed_layout(n, m, s, grid, slot_bytes, nullptr, nullptr) + 256;
 }
 
 int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
@@ -692,15 +957,17 @@ int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o,
   if (nb > kNB) return SSV_ENOTSUP;
   if (s == 0) return SSV_OK;
   int* fallback = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&fallback, sizeof(int) * (size_t)s, st));
+  void* scratch = nullptr;
   int rc;
   const int mode = o->mode == SSV_X ? SSV_XHAT : o->mode;
-  if (m <= 1) rc = launch_mixed<1>(h, s, shifts, nb, mode, out, ldo, status, resid, fallback, o->max_refine, o->tol, st);
-  else if (m <= 2) rc = launch_mixed<2>(h, s, shifts, nb, mode, out, ldo, status, resid, fallback, o->max_refine, o->tol, st);
-  else if (m <= 4) rc = launch_mixed<4>(h, s, shifts, nb, mode, out, ldo, status, resid, fallback, o->max_refine, o->tol, st);
-  else if (m <= 8) rc = launch_mixed<8>(h, s, shifts, nb, mode, out, ldo, status, resid, fallback, o->max_refine, o->tol, st);
-  else if (m <= 16) rc = launch_mixed<16>(h, s, shifts, nb, mode, out, ldo, status, resid, fallback, o->max_refine, o->tol, st);
-  else if (m <= 32) rc = launch_mixed<32>(h, s, shifts, nb, mode, out, ldo, status, resid, fallback, o->max_refine, o->tol, st);
+  const int mr = o->max_refine;
+  const double tol = o->tol;
+  if (m <= 1) rc = run_mixed<1>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
+  else if (m <= 2) rc = run_mixed<2>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
+  else if (m <= 4) rc = run_mixed<4>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
+  else if (m <= 8) rc = run_mixed<8>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
+  else if (m <= 16) rc = run_mixed<16>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
+  else if (m <= 32) rc = run_mixed<32>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
   else rc = SSV_ENOTSUP;
   // shifts that did not converge: FP64 sweep (status and output overwritten);
   // their backward errors come from the FP64 solution
@@ -720,10 +987,12 @@ int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o,
                                       gm ? h->n : ldo, resid, fallback, st);
     if (xcopy) cudaFreeAsync(xcopy, st);
   }
-  cudaError_t e = cudaFreeAsync(fallback, st);
-  if (e != cudaSuccess && rc == SSV_OK) {
-    set_cuda_error(e);
-    rc = SSV_ECUDA;
+  if (scratch) {
+    cudaError_t e = cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess && rc == SSV_OK) {
+      set_cuda_error(e);
+      rc = SSV_ECUDA;
+    }
   }
   return rc;
 }
