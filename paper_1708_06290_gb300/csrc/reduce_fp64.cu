@@ -83,47 +83,195 @@ __global__ void __launch_bounds__(256) apply_left_kernel(double* __restrict__ a,
   }
 }
 
-constexpr int kRightRows = 128;  // rows per CTA
-constexpr int kRightCols = 128;  // columns per chunk
+// ---------------------------------------------------------------------------
+// Two-sided application of one reflector H = I - tau v v^T (v(r0) = 1,
+// support rows/columns r0 .. n-1) to A (n x n) and, from the right, to C
+// (p x n), in two passes over the matrix:
+//   u_c = sum_{i >= r0} v_i A(i, c)       (c >= cl: the left-update columns)
+//   w_i = sum_{c >= r0} A(i, c) v_c       (all rows of A, then the rows of C)
+//   s   = u^T v
+//   A <- A - tau v u^T - tau w' v^T,  w' = w - tau s v   (= H A H),
+//   C <- C - tau w_C v^T.
+// The left update touches rows >= r0 of columns >= cl only (columns left of
+// cl hold stored reflectors there).  Rows of C follow the rows of A as
+// "virtual" rows n .. n+p-1.  Partial sums are reduced in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kFR = 64;   // tile rows
+constexpr int kFC = 128;  // tile columns
+constexpr int kFLD = kFR + 1;  // padded shared-memory column stride (odd: conflict-free)
 
-// Right application, pass 1: partial dot products
-// part[chunk * nr + i] = sum_{j in chunk} a(i, c0 + j) v_j.
-__global__ void __launch_bounds__(kRightRows) apply_right_dot_kernel(
-    const double* __restrict__ a, long long ld, int nr, int c0, int len,
-    const double* __restrict__ vsrc, const double* __restrict__ tau_p, double* __restrict__ part) {
+__device__ __forceinline__ double vrow(int i, int r0, int n, const double* __restrict__ vsrc) {
+  return (i >= r0 && i < n) ? (i == r0 ? 1.0 : vsrc[i - r0]) : 0.0;
+}
+
+// Pass 1: the tile is staged once in shared memory (coalesced loads); row dots
+// w and column dots u are both read from there.
+__global__ void __launch_bounds__(256) fused_dots_kernel(
+    const double* __restrict__ A, int n, const double* __restrict__ C, int ldc, int p, int r0,
+    int cl, const double* __restrict__ vsrc, const double* __restrict__ tau_p,
+    double* __restrict__ upart, double* __restrict__ wpart, double* __restrict__ spart) {
   if (*tau_p == 0.0) return;
-  int i = blockIdx.x * kRightRows + threadIdx.x;
-  int j0 = blockIdx.y * kRightCols, j1 = min(len, j0 + kRightCols);
-  __shared__ double vs[kRightCols];
-  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vs[j - j0] = j == 0 ? 1.0 : vsrc[j];
+  extern __shared__ double fsm[];
+  double* tile = fsm;                       // kFC columns x kFLD
+  double* vc_s = tile + kFC * kFLD;         // kFC
+  double* vr_s = vc_s + kFC;                // kFR
+  double* wq = vr_s + kFR;                  // 4 x kFR
+  double* red = wq + 4 * kFR;               // 8
+  const int tid = threadIdx.x;
+  const int rt = blockIdx.y, ct = blockIdx.x;
+  const int c0 = cl + ct * kFC, i0 = rt * kFR;
+  const int np = n + p;
+  if (tid < kFC) vc_s[tid] = (c0 + tid < n) ? vrow(c0 + tid, r0, n, vsrc) : 0.0;
+  if (tid < kFR) vr_s[tid] = vrow(i0 + tid, r0, n, vsrc);
+#pragma unroll 8
+  for (int k = 0; k < (kFR * kFC) / 256; ++k) {
+    const int idx = k * 256 + tid;
+    const int r = idx % kFR, c = idx / kFR;
+    const int i = i0 + r, cg = c0 + c;
+    double a = 0.0;
+    if (cg < n) {
+      if (i < n) a = A[i + (size_t)cg * n];
+      else if (i < np) a = C[(i - n) + (size_t)cg * ldc];
+    }
+    tile[c * kFLD + r] = a;
+  }
   __syncthreads();
-  if (i >= nr) return;
-  const double* row = a + i + (size_t)c0 * ld;
-  double acc = 0.0;
-  for (int j = j0; j < j1; ++j) acc = fma(row[(size_t)j * ld], vs[j - j0], acc);
-  part[(size_t)blockIdx.y * nr + i] = acc;
+  // row dots: thread (r, quarter) sums 32 columns
+  {
+    const int r = tid % kFR, qtr = tid / kFR;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int c = qtr * 32; c < qtr * 32 + 32; ++c) acc = fma(tile[c * kFLD + r], vc_s[c], acc);
+    wq[qtr * kFR + r] = acc;
+  }
+  // column dots: threads 0..127, one column each over the 64 rows
+  double u = 0.0;
+  if (tid < kFC) {
+#pragma unroll 8
+    for (int r = 0; r < kFR; ++r) u = fma(vr_s[r], tile[tid * kFLD + r], u);
+  }
+  __syncthreads();
+  if (tid < kFR) {
+    const int ii = i0 + tid;
+    if (ii < np) wpart[(size_t)ct * np + ii] = wq[tid] + wq[kFR + tid] + wq[2 * kFR + tid] + wq[3 * kFR + tid];
+  }
+  double sp = 0.0;
+  if (tid < kFC) {
+    if (c0 + tid < n) upart[(size_t)rt * n + c0 + tid] = u;
+    sp = u * vc_s[tid];
+  }
+  for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+  if ((tid & 31) == 0) red[tid >> 5] = sp;
+  __syncthreads();
+  if (tid == 0) spart[(size_t)rt * gridDim.x + ct] = red[0] + red[1] + red[2] + red[3];
 }
 
-// Right application, pass 2: w_i = tau * sum over chunks (fixed order), then
-// a(i, c0 + j) -= w_i v_j for the CTA's column chunk.
-__global__ void __launch_bounds__(kRightRows) apply_right_update_kernel(
-    double* __restrict__ a, long long ld, int nr, int c0, int len, int nchunk,
-    const double* __restrict__ vsrc, const double* __restrict__ tau_p,
-    const double* __restrict__ part) {
-  double tau = *tau_p;
-  if (tau == 0.0) return;
-  int i = blockIdx.x * kRightRows + threadIdx.x;
-  int j0 = blockIdx.y * kRightCols, j1 = min(len, j0 + kRightCols);
-  __shared__ double vs[kRightCols];
-  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vs[j - j0] = j == 0 ? 1.0 : vsrc[j];
-  __syncthreads();
-  if (i >= nr) return;
-  double w = 0.0;
-  for (int c = 0; c < nchunk; ++c) w += part[(size_t)c * nr + i];
-  w *= tau;
-  double* row = a + i + (size_t)c0 * ld;
-  for (int j = j0; j < j1; ++j) row[(size_t)j * ld] = fma(-w, vs[j - j0], row[(size_t)j * ld]);
+constexpr size_t kFusedDotsSmem = sizeof(double) * (kFC * kFLD + kFC + kFR + 4 * kFR + 8);
+
+__global__ void __launch_bounds__(256) fused_finalize_kernel(
+    int n, int np, int cl, int nrt, int nct, const double* __restrict__ upart,
+    const double* __restrict__ wpart, const double* __restrict__ spart,
+    const double* __restrict__ tau_p, double* __restrict__ u, double* __restrict__ w,
+    double* __restrict__ s_out) {
+  if (*tau_p == 0.0) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= cl && idx < n) {
+    double a = 0.0;
+    for (int r = 0; r < nrt; ++r) a += upart[(size_t)r * n + idx];
+    u[idx] = a;
+  }
+  if (idx < np) {
+    double b = 0.0;
+    for (int c = 0; c < nct; ++c) b += wpart[(size_t)c * np + idx];
+    w[idx] = b;
+  }
+  if (blockIdx.x == 0) {
+    __shared__ double red[256];
+    double a = 0.0;
+    for (int k = threadIdx.x; k < nrt * nct; k += blockDim.x) a += spart[k];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *s_out = red[0];
+  }
 }
+
+// Pass 2: A -= tau v u^T (rows >= r0) + tau w' v^T; thread (row, quarter)
+// updates 32 columns with independent loads.
+__global__ void __launch_bounds__(256) fused_update_kernel(
+    double* __restrict__ A, int n, double* __restrict__ C, int ldc, int p, int r0, int cl,
+    const double* __restrict__ vsrc, const double* __restrict__ tau_p,
+    const double* __restrict__ u, const double* __restrict__ w, const double* __restrict__ s_p) {
+  const double tau = *tau_p;
+  if (tau == 0.0) return;
+  __shared__ double vc_s[kFC];
+  __shared__ double tu_s[kFC];
+  const int tid = threadIdx.x;
+  const int rt = blockIdx.y, ct = blockIdx.x;
+  const int c0 = cl + ct * kFC;
+  const int np = n + p;
+  if (tid < kFC) {
+    const int c = c0 + tid;
+    vc_s[tid] = (c < n) ? vrow(c, r0, n, vsrc) : 0.0;
+    tu_s[tid] = (c < n) ? tau * u[c] : 0.0;
+  }
+  __syncthreads();
+  const int r = tid % kFR, qtr = tid / kFR;
+  const int i = rt * kFR + r;
+  if (i >= np) return;
+  const double vi = vrow(i, r0, n, vsrc);
+  const double twp = tau * (w[i] - tau * (*s_p) * vi);   // tau * w'_i
+  const double lvi = (i >= r0 && i < n) ? vi : 0.0;       // left part only on rows >= r0
+  const int cb = c0 + qtr * 32;
+  const int cnt = min(32, n - cb);
+  if (cnt <= 0) return;
+  double* base = i < n ? A + i : C + (i - n);
+  const size_t ld = i < n ? (size_t)n : (size_t)ldc;
+  double a[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k)
+    if (k < cnt) a[k] = base[(size_t)(cb + k) * ld];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < cnt) {
+      const int cc = qtr * 32 + k;
+      double v = fma(-lvi, tu_s[cc], a[k]);
+      base[(size_t)(cb + k) * ld] = fma(-twp, vc_s[cc], v);
+    }
+  }
+}
+
+struct FusedWork {
+  double* upart;
+  double* wpart;
+  double* spart;
+  double* u;
+  double* w;
+  double* s;
+};
+
+inline cudaError_t launch_two_sided(double* A, int n, double* C, int ldc, int p, int r0, int cl,
+                                    const double* vsrc, const double* tau, const FusedWork& fw,
+                                    cudaStream_t st) {
+  if (n - r0 <= 1) return cudaSuccess;
+  const int np = n + p;
+  const int nrt = (np + kFR - 1) / kFR;
+  const int nct = (n - cl + kFC - 1) / kFC;
+  dim3 grid(nct, nrt);
+  fused_dots_kernel<<<grid, 256, kFusedDotsSmem, st>>>(A, n, C, ldc, p, r0, cl, vsrc, tau,
+                                                       fw.upart, fw.wpart, fw.spart);
+  count_launch();
+  fused_finalize_kernel<<<(std::max(n, np) + 255) / 256, 256, 0, st>>>(
+      n, np, cl, nrt, nct, fw.upart, fw.wpart, fw.spart, tau, fw.u, fw.w, fw.s);
+  count_launch();
+  fused_update_kernel<<<grid, 256, 0, st>>>(A, n, C, ldc, p, r0, cl, vsrc, tau, fw.u, fw.w, fw.s);
+  count_launch();
+  return cudaGetLastError();
+}
+
 
 // Frobenius norm^2 and trace of the structural part of H.
 __global__ void hnorm_kernel(const double* __restrict__ H, int n, int m, double* __restrict__ out) {
@@ -223,11 +371,6 @@ __global__ void split_h_kernel(const double* __restrict__ H, int n, int m, float
   }
 }
 
-struct RightWork {
-  double* part;
-  size_t cap;  // doubles
-};
-
 // One Householder reflector on the left of rows [r0, r0+len) of a's columns
 // [c0, c1), where v lives at vsrc (vsrc[0] ignored, treated as 1).
 inline cudaError_t launch_left(double* a, long long ld, int r0, int len, int c0, int c1,
@@ -236,20 +379,6 @@ inline cudaError_t launch_left(double* a, long long ld, int r0, int len, int c0,
   long long warps = c1 - c0;
   int blocks = (int)((warps * 32 + 255) / 256);
   apply_left_kernel<<<blocks, 256, 0, st>>>(a, ld, r0, len, c0, c1, vsrc, tau);
-  count_launch();
-  return cudaGetLastError();
-}
-
-inline cudaError_t launch_right(double* a, long long ld, int nr, int c0, int len,
-                                const double* vsrc, const double* tau, double* part,
-                                cudaStream_t st) {
-  if (nr <= 0 || len <= 1) return cudaSuccess;
-  int nchunk = (len + kRightCols - 1) / kRightCols;
-  dim3 grid((nr + kRightRows - 1) / kRightRows, nchunk);
-  apply_right_dot_kernel<<<grid, kRightRows, 0, st>>>(a, ld, nr, c0, len, vsrc, tau, part);
-  count_launch();
-  apply_right_update_kernel<<<grid, kRightRows, 0, st>>>(a, ld, nr, c0, len, nchunk, vsrc, tau,
-                                                         part);
   count_launch();
   return cudaGetLastError();
 }
@@ -267,10 +396,22 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
   if (p > 0)
     SSV_CUDA_TRY(cudaMemcpy2DAsync(h->Ct, sizeof(double) * ldct, C, sizeof(double) * ldc,
                                    sizeof(double) * p, n, cudaMemcpyDeviceToDevice, st));
-  int nchunk_max = (n + kRightCols - 1) / kRightCols;
-  double* part = nullptr;
-  SSV_CUDA_TRY(
-      cudaMallocAsync((void**)&part, sizeof(double) * (size_t)nchunk_max * std::max(n, p), st));
+  SSV_CUDA_TRY(cudaFuncSetAttribute(fused_dots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kFusedDotsSmem));
+  // workspace of the two-sided reflector application
+  const int np = n + p;
+  const size_t nrt_max = (size_t)(np + kFR - 1) / kFR;
+  const size_t nct_max = (size_t)(n + kFC - 1) / kFC;
+  const size_t wbytes = sizeof(double) * (nrt_max * n + nct_max * np + nrt_max * nct_max + n + np + 1);
+  double* wsp = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&wsp, wbytes, st));
+  FusedWork fw;
+  fw.upart = wsp;
+  fw.wpart = fw.upart + nrt_max * n;
+  fw.spart = fw.wpart + nct_max * np;
+  fw.u = fw.spart + nrt_max * nct_max;
+  fw.w = fw.u + n;
+  fw.s = fw.w + np;
 
   int rc = SSV_OK;
   auto chk = [&](cudaError_t e) {
@@ -279,7 +420,8 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
       rc = SSV_ECUDA;
     }
   };
-  // Steps 1-2: QR of B, similarity with Q_B, C <- C Q_B.
+  // Steps 1-2: QR of B; each reflector applied to the rest of B, and to A from
+  // both sides and to C from the right (left part: all columns).
   h->kb = std::min(m, n - 1);
   for (int i = 0; i < h->kb && rc == SSV_OK; ++i) {
     int len = n - i;
@@ -288,11 +430,10 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
     count_launch();
     chk(cudaGetLastError());
     chk(launch_left(h->R, n, i, len, i + 1, m, x, h->tauB + i, st));
-    chk(launch_left(h->H, n, i, len, 0, n, x, h->tauB + i, st));
-    chk(launch_right(h->H, n, n, i, len, x, h->tauB + i, part, st));
-    chk(launch_right(h->Ct, ldct, p, i, len, x, h->tauB + i, part, st));
+    chk(launch_two_sided(h->H, n, h->Ct, ldct, p, i, 0, x, h->tauB + i, fw, st));
   }
-  // Steps 3-4: m-Hessenberg reduction of A, C <- C Q_A.
+  // Steps 3-4: m-Hessenberg reduction of A, C <- C Q_A.  Reflector j acts on
+  // rows/columns j+m .. n-1; its left part touches columns j+1 .. n-1.
   h->ka = std::max(0, n - m - 1);
   for (int j = 0; j < h->ka && rc == SSV_OK; ++j) {
     int r0 = j + m, len = n - r0;
@@ -300,9 +441,7 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
     house_kernel<<<1, kHouseThreads, 0, st>>>(x, len, h->tauA + j);
     count_launch();
     chk(cudaGetLastError());
-    chk(launch_left(h->H, n, r0, len, j + 1, n, x, h->tauA + j, st));
-    chk(launch_right(h->H, n, n, r0, len, x, h->tauA + j, part, st));
-    chk(launch_right(h->Ct, ldct, p, r0, len, x, h->tauA + j, part, st));
+    chk(launch_two_sided(h->H, n, h->Ct, ldct, p, r0, j + 1, x, h->tauA + j, fw, st));
   }
   h->has_q = 1;
   if (rc == SSV_OK) {
@@ -312,7 +451,7 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
     count_launch();
     chk(cudaGetLastError());
   }
-  chk(cudaFreeAsync(part, st));
+  chk(cudaFreeAsync(wsp, st));
   return rc;
 }
 
