@@ -110,6 +110,53 @@ int ssv_solve(ssv_handle h, int s, const double* shifts, const ssv_opts* o, doub
               long long ldo, int* status, double* resid, void* stream);
 
 /*
+ * ssv_solve_many -- many reduced systems of uneven n, m and shift counts in
+ * one persistent launch (FP64: one kernel over a cost-ordered worklist of
+ * (system, shift) items, Sec. 3 applied to several systems at once; MIXED:
+ * the systems are solved one after another on the stream).
+ *   nsys systems; hs[k] handle, s[k] shifts at shifts[k] (device), results in
+ *   outs[k] (device, layout as ssv_solve with leading dimension ldos[k]),
+ *   statuses in status[k] (device, or status == NULL / status[k] == NULL).
+ *   hs, s, shifts, outs, ldos, status are host arrays.  Modes SSV_G, SSV_TF,
+ *   SSV_XHAT.  All handles must belong to the current device.
+ * The call returns after the work has completed (it frees its plan).
+ * Errors: SSV_EINVAL, SSV_ENOTSUP, SSV_ENOMEM, SSV_ECUDA.
+ */
+int ssv_solve_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
+                   const ssv_opts* o, double* const* outs, const long long* ldos,
+                   int* const* status, void* stream);
+
+/*
+ * Batch plans: the FP64 multi-system solve with everything fixed up front, so
+ * that ssv_batch_run is a single kernel launch with constant arguments that
+ * can be captured into a CUDA graph and replayed; between runs the caller may
+ * rewrite the contents (not the addresses) of the shift buffers.
+ *   ssv_batch_create: arguments as ssv_solve_many (precision must be SSV_FP64;
+ *   nb = 0 takes the autotuned or default block width per system); allocates
+ *   the plan (device descriptors, worklist, scratch) synchronously.
+ *   ssv_batch_run: enqueue the batch on `stream`.
+ *   ssv_batch_destroy: free the plan (after synchronising the device).
+ */
+typedef struct ssv_batch_s* ssv_batch;
+int ssv_batch_create(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
+                     const ssv_opts* o, double* const* outs, const long long* ldos,
+                     int* const* status, ssv_batch* out);
+int ssv_batch_run(ssv_batch b, void* stream);
+void ssv_batch_destroy(ssv_batch b);
+
+/*
+ * ssv_autotune -- choose the elimination block width n_b for this handle,
+ * precision and mode by timing each candidate (16, 24, 32, 48, 64) on the
+ * given s shifts (device) with CUDA events; writes the results to out
+ * (scratch for the caller, layout as ssv_solve).  The choice is cached for
+ * the process and used by every later call with o->nb == 0 on a system of the
+ * same (n, m, p).  Synchronises `stream`.  *best_nb receives the choice and
+ * *best_ms (may be NULL) its time.
+ */
+int ssv_autotune(ssv_handle h, int s, const double* shifts, const ssv_opts* o, double* out,
+                 long long ldo, void* stream, int* best_nb, float* best_ms);
+
+/*
  * ssv_solve_noalloc -- ssv_solve without any device allocation.  The paper has
  * no counterpart; this entry point exists for callers that cannot allocate
  * device memory when they solve (an external allocator or framework owns all

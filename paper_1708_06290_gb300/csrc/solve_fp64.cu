@@ -26,6 +26,11 @@
 // Givens rotations; each thread block owns one shift at a time for the whole
 // sweep (no grid-wide phases); the final m x m solve runs on the GPU.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <utility>
+#include <vector>
 
 #include "ssv_internal.cuh"
 
@@ -51,6 +56,341 @@ struct Layout {
       (cand_elems + coef_elems + 3 * MAXM * MAXM + 2 * MAXM + 4) * sizeof(cd) + 64;
 };
 
+// One system as the FP64 solve sees it.
+struct FpSys {
+  int n, m, p, nb, mode;
+  const double* H;
+  const double* Ct;
+  int ldct;
+  const double* R;
+  const cd* shifts;
+  cd* out;
+  long long ldo;
+  int* status;
+  cd* xhat_copy;
+  long long ldxc;
+  const double* hnorm;
+};
+
+// Solve shift sh of system d with the window state in Z2 (and ZT).
+template <int MAXM>
+__device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
+                           unsigned char* smem_raw, int* s_piv_p, int* s_sing_p) {
+  using L = Layout<MAXM>;
+  constexpr int S = L::kSlots;
+  cd* cand = reinterpret_cast<cd*>(smem_raw);
+  cd* coef = cand + L::cand_elems;
+  cd* Wm = coef + L::coef_elems;             // MAXM x (2 MAXM) augmented [Wm | R1]
+  cd* lmul = Wm + 2 * MAXM * MAXM;           // reflector v (MAXM + 2 slots) and tau
+  cd* Yb = lmul + (MAXM + 4);                // MAXM x MAXM solution
+  int& s_piv = *s_piv_p;
+  int& s_sing = *s_sing_p;
+  const int n = d.n, m = d.m, p = d.p, nb = d.nb, mode = d.mode, ldct = d.ldct;
+  const double* __restrict__ H = d.H;
+  const double* __restrict__ Ct = d.Ct;
+  const double* __restrict__ R = d.R;
+  const cd* __restrict__ shifts = d.shifts;
+  cd* __restrict__ out = d.out;
+  const long long ldo = d.ldo, ldxc = d.ldxc;
+  int* __restrict__ status = d.status;
+  cd* __restrict__ xhat_copy = d.xhat_copy;
+  const double* __restrict__ hnorm = d.hnorm;
+  const int tid = threadIdx.x;
+  const int ldz = p + n;
+  const bool track_t = (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
+  cd* ZT = Z2 + (size_t)ldz * m;  // n x m, valid when track_t
+  const cd sigma = shifts[sh];
+  // ||H - sigma I||_F from ||H||_F^2 and trace(H); a finalized diagonal entry
+  // of magnitude <= n eps ||H - sigma I||_F marks the shift singular.
+  const double mnorm2 = fmax(hnorm[0] - 2.0 * sigma.x * hnorm[1] +
+                                 (double)n * (sigma.x * sigma.x + sigma.y * sigma.y), 0.0);
+  const double sing_tol = (double)n * 2.220446049250313e-16 * sqrt(mnorm2);
+  // ---- shift setup: Z2 = last m columns of [Ct; H] - sigma on the diagonal
+  for (long long idx = tid; idx < (long long)ldz * m; idx += kThreads) {
+    int i = (int)(idx % ldz), q = (int)(idx / ldz);
+    int j = n - m + q;
+    double v = i < p ? Ct[i + (size_t)j * ldct] : H[(i - p) + (size_t)j * n];
+    cd z = mkcd(v, 0.0);
+    if (i - p == j) z = csub(z, sigma);
+    Z2[idx] = z;
+  }
+  if (track_t) {
+    for (long long idx = tid; idx < (long long)n * m; idx += kThreads) {
+      int i = (int)(idx % n), q = (int)(idx / n);
+      ZT[idx] = mkcd(i == n - m + q ? 1.0 : 0.0, 0.0);
+    }
+  }
+  if (tid == 0) s_sing = 0;
+  __syncthreads();
+
+  int k = n;
+  while (k > m) {
+    const int nbe = min(nb, k - m);
+    const int r = p + k - nbe;        // rows of [Ct; M] above the block
+    const int j0 = k - m - nbe;       // first fresh column
+    // stage the live rows of the block and reset coefficients
+    for (int idx = tid; idx < m * nbe; idx += kThreads) {
+      int t = idx % nbe, q = idx / nbe;
+      cand[q * kNB + t] = Z2[(r + t) + (size_t)q * ldz];
+    }
+    // coefficients: identity on the old live columns, e_{nbe-1} for the
+    // fresh column F_{nbe-1} that enters slot m (slots m, m+1 alternate)
+    for (int idx = tid; idx < L::kCoefRows * S; idx += kThreads) {
+      int c = idx / S, slot = idx % S;
+      cd v = mkcd(0.0, 0.0);
+      if ((slot < m && c == kNB + slot) || (slot == m && c == nbe - 1)) v = mkcd(1.0, 0.0);
+      coef[idx] = v;
+    }
+    {
+      const int c = nbe - 1, jc = j0 + c;
+      for (int t = tid; t <= c; t += kThreads) {
+        cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
+        if (t == c - m) z = csub(z, sigma);
+        cand[m * kNB + t] = z;
+      }
+    }
+    __syncthreads();
+    for (int c = nbe - 1; c >= 0; --c) {
+      const int fs = m + ((nbe - 1 - c) & 1);  // slot holding F_c
+      const int fn = (fs == m) ? m + 1 : m;    // slot for F_{c-1}
+      // ---- reflector U = I - tau v v^H on the m + 1 candidates of row c
+      //      (survivors 0..m-1, fresh fs): x U = conj(alpha) e_fs, x = row c.
+      if (tid < 32) {
+        double rest2 = 0.0;  // sum of |x_q|^2 over the m survivors
+        for (int q = tid; q < m; q += 32) {
+          const cd x = cand[q * kNB + c];
+          rest2 = fma(x.x, x.x, fma(x.y, x.y, rest2));
+        }
+        for (int o = 16; o > 0; o >>= 1) rest2 += __shfl_xor_sync(0xffffffffu, rest2, o);
+        const cd xf = cand[fs * kNB + c];
+        const double af2 = fma(xf.x, xf.x, xf.y * xf.y);
+        const double af = sqrt(af2);
+        const double nrm2 = rest2 + af2;
+        const double nrm = sqrt(nrm2);
+        // y = conj(x); alpha = -exp(i arg y_fs) ||y||; v = y - alpha e_fs
+        cd ph = af > 0.0 ? mkcd(xf.x / af, -xf.y / af) : mkcd(1.0, 0.0);
+        const cd alpha = mkcd(-ph.x * nrm, -ph.y * nrm);
+        const bool trivial = !(rest2 > 0.0);
+        for (int q = tid; q <= m; q += 32) {
+          const int slot = q < m ? q : fs;
+          const cd x = cand[slot * kNB + c];
+          cd v = mkcd(x.x, -x.y);
+          if (slot == fs) v = csub(v, alpha);
+          lmul[slot] = v;
+        }
+        if (tid == 0) {
+          // ||v||^2 = 2 ||y||^2 + 2 |y_fs| ||y||
+          const double vv = 2.0 * nrm2 + 2.0 * af * nrm;
+          lmul[MAXM + 2].x = trivial ? 0.0 : 2.0 / vv;
+          if (nrm <= sing_tol) s_sing = 1;  // |R(row, row)| = ||x|| at working precision
+        }
+      }
+      __syncthreads();
+      const double tau = lmul[MAXM + 2].x;
+      // ---- apply to window rows 0..c-1 and the nonzero coefficient rows;
+      //      load F_{c-1} into slot fn meanwhile.
+      if (tau != 0.0) {
+        const int nrow = c;
+        const int ncoef = (nbe - c) + m;
+        for (int e = tid; e < nrow + ncoef; e += kThreads) {
+          cd* base;
+          int stride;
+          if (e < nrow) {
+            base = cand + e;
+            stride = kNB;
+          } else {
+            const int ee = e - nrow;
+            const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
+            base = coef + crow * S;
+            stride = 1;
+          }
+          cd w = mkcd(0.0, 0.0);
+          for (int q = 0; q <= m; ++q) {
+            const int slot = q < m ? q : fs;
+            w = cfma(base[slot * stride], lmul[slot], w);
+          }
+          w = mkcd(w.x * tau, w.y * tau);
+          for (int q = 0; q <= m; ++q) {
+            const int slot = q < m ? q : fs;
+            const cd vc = mkcd(lmul[slot].x, -lmul[slot].y);
+            base[slot * stride] = cfms(w, vc, base[slot * stride]);
+          }
+        }
+      }
+      if (c > 0) {
+        const int cn = c - 1, jc = j0 + cn;
+        for (int t = tid; t <= cn; t += kThreads) {
+          cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
+          if (t == cn - m) z = csub(z, sigma);
+          cand[fn * kNB + t] = z;
+        }
+        for (int crow = tid; crow < L::kCoefRows; crow += kThreads)
+          coef[crow * S + fn] = mkcd(crow == cn ? 1.0 : 0.0, 0.0);
+      }
+      __syncthreads();
+    }
+
+    // ---- update the rows above the block (and the T rows)
+    for (int i = tid; i < r; i += kThreads) {
+      cd acc[MAXM];
+#pragma unroll
+      for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
+      for (int c = 0; c < nbe; ++c) {
+        const int jc = j0 + c;
+        const double z = i < p ? Ct[i + (size_t)jc * ldct] : H[(i - p) + (size_t)jc * n];
+        const cd* cr = coef + c * S;
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q) {
+          if (q < m) {
+            cd w = cr[q];
+            acc[q].x = fma(z, w.x, acc[q].x);
+            acc[q].y = fma(z, w.y, acc[q].y);
+          }
+        }
+      }
+      for (int qq = 0; qq < m; ++qq) {
+        const cd zz = Z2[i + (size_t)qq * ldz];
+        const cd* cr = coef + (kNB + qq) * S;
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
+      }
+      const int cd_ = i - (r - m);  // diagonal correction of fresh column cd_
+      if (cd_ >= 0 && cd_ < min(m, nbe)) {
+        const cd* cr = coef + cd_ * S;
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q < m) acc[q] = cfms(sigma, cr[q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < MAXM; ++q)
+        if (q < m) Z2[i + (size_t)q * ldz] = acc[q];
+    }
+    if (track_t) {
+      // rows k-m .. n-1: ZT <- ZT P2 ; rows j0 .. j0+nbe-1: ZT = P1
+      const int lo = k - m;
+      for (int i = j0 + tid; i < n; i += kThreads) {
+        cd acc[MAXM];
+        if (i < lo) {
+          const cd* cr = coef + (i - j0) * S;
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q) acc[q] = cr[q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
+          for (int qq = 0; qq < m; ++qq) {
+            const cd zz = ZT[i + (size_t)qq * n];
+            const cd* cr = coef + (kNB + qq) * S;
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q)
+              if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q < m) ZT[i + (size_t)q * n] = acc[q];
+      }
+    }
+    __syncthreads();
+    k -= nbe;
+  }
+
+  // ---- final m x m block: solve Wm Y = R(0:m, 0:m) by Gauss-Jordan with
+  // partial pivoting on the augmented [Wm | R1] (2m columns).
+  const int w2 = 2 * m;
+  for (int idx = tid; idx < m * w2; idx += kThreads) {
+    int i = idx % m, j = idx / m;
+    cd v;
+    if (j < m) v = Z2[(p + i) + (size_t)j * ldz];
+    else {
+      int jj = j - m;
+      v = mkcd(i <= jj ? R[i + (size_t)jj * n] : 0.0, 0.0);
+    }
+    Wm[i + j * MAXM] = v;
+  }
+  __syncthreads();
+  for (int kk = 0; kk < m; ++kk) {
+    if (tid < 32) {
+      double best = -1.0;
+      int brow = kk;
+      for (int i = kk + tid; i < m; i += 32) {
+        double v = cabs1(Wm[i + kk * MAXM]);
+        if (v > best) { best = v; brow = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+        if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
+      }
+      if (tid == 0) {
+        s_piv = brow;
+        const cd pv = Wm[brow + kk * MAXM];
+        if (best == 0.0 || sqrt(pv.x * pv.x + pv.y * pv.y) <= sing_tol) s_sing = 1;
+      }
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != kk) {
+      for (int j = tid; j < w2; j += kThreads) {
+        cd a = Wm[kk + j * MAXM];
+        Wm[kk + j * MAXM] = Wm[pr + j * MAXM];
+        Wm[pr + j * MAXM] = a;
+      }
+    }
+    __syncthreads();
+    const cd d = Wm[kk + kk * MAXM];
+    const bool dz = (d.x == 0.0 && d.y == 0.0);
+    if (tid < m) lmul[tid] = (tid == kk || dz) ? mkcd(0.0, 0.0) : cdiv(Wm[tid + kk * MAXM], d);
+    __syncthreads();
+    for (int idx = tid; idx < m * w2; idx += kThreads) {
+      int i = idx % m, j = idx / m;
+      if (i != kk && j > kk) Wm[i + j * MAXM] = cfms(lmul[i], Wm[kk + j * MAXM], Wm[i + j * MAXM]);
+    }
+    __syncthreads();
+  }
+  // Y(i, q) = Wm(i, m+q) / Wm(i, i)
+  for (int idx = tid; idx < m * m; idx += kThreads) {
+    int i = idx % m, q = idx / m;
+    cd d = Wm[i + i * MAXM];
+    Yb[i + q * MAXM] = (d.x == 0.0 && d.y == 0.0) ? mkcd(0.0, 0.0) : cdiv(Wm[i + (m + q) * MAXM], d);
+  }
+  __syncthreads();
+  const bool sing = s_sing != 0;
+  const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+  // ---- outputs
+  if (mode == SSV_G || mode == SSV_TF) {
+    const double sg = mode == SSV_TF ? -1.0 : 1.0;
+    cd* o = out + (size_t)sh * m * ldo;
+    for (int idx = tid; idx < p * m; idx += kThreads) {
+      int i = idx % p, q = idx / p;
+      cd acc = mkcd(0.0, 0.0);
+      for (int t = 0; t < m; ++t) acc = cfma(Z2[i + (size_t)t * ldz], Yb[t + q * MAXM], acc);
+      if (sing) acc = mkcd(nanv, nanv);
+      o[i + (size_t)q * ldo] = mkcd(sg * acc.x, sg * acc.y);
+    }
+  }
+  if (track_t) {
+    cd* o;
+    long long ld;
+    if (mode == SSV_XHAT || mode == SSV_X) {
+      o = out + (size_t)sh * m * ldo;
+      ld = ldo;
+    } else {
+      o = xhat_copy + (size_t)sh * m * ldxc;
+      ld = ldxc;
+    }
+    for (int idx = tid; idx < n * m; idx += kThreads) {
+      int i = idx % n, q = idx / n;
+      cd acc = mkcd(0.0, 0.0);
+      for (int t = 0; t < m; ++t) acc = cfma(ZT[i + (size_t)t * n], Yb[t + q * MAXM], acc);
+      if (sing) acc = mkcd(nanv, nanv);
+      o[i + (size_t)q * ld] = acc;
+    }
+  }
+  if (status != nullptr && tid == 0) status[sh] = sing ? SSV_SHIFT_SINGULAR : SSV_SHIFT_OK;
+  __syncthreads();
+}
+
 template <int MAXM>
 __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
     int n, int m, int p, int nb, const double* __restrict__ H, const double* __restrict__ Ct,
@@ -59,317 +399,36 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
     int* __restrict__ status, cd* __restrict__ xhat_copy, long long ldxc,
     const double* __restrict__ hnorm, const int* __restrict__ list,
     const int* __restrict__ count) {
-  using L = Layout<MAXM>;
-  constexpr int S = L::kSlots;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cd* cand = reinterpret_cast<cd*>(smem_raw);
-  cd* coef = cand + L::cand_elems;
-  cd* Wm = coef + L::coef_elems;             // MAXM x (2 MAXM) augmented [Wm | R1]
-  cd* lmul = Wm + 2 * MAXM * MAXM;           // reflector v (MAXM + 2 slots) and tau
-  cd* Yb = lmul + (MAXM + 4);                // MAXM x MAXM solution
   __shared__ int s_piv;
   __shared__ int s_sing;
-
-  const int tid = threadIdx.x;
-  const int ldz = p + n;
-  const bool track_t = (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
+  FpSys d;
+  d.n = n; d.m = m; d.p = p; d.nb = nb; d.mode = mode; d.H = H; d.Ct = Ct; d.ldct = ldct;
+  d.R = R; d.shifts = shifts; d.out = out; d.ldo = ldo; d.status = status;
+  d.xhat_copy = xhat_copy; d.ldxc = ldxc; d.hnorm = hnorm;
   cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
-  cd* ZT = Z2 + (size_t)ldz * m;  // n x m, valid when track_t
-
   // With a work list, the block takes list entries blockIdx.x, +gridDim.x, ...
   const int nwork = list != nullptr ? *count : s;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int sh = list != nullptr ? list[w] : w;
-    const cd sigma = shifts[sh];
-    // ||H - sigma I||_F from ||H||_F^2 and trace(H); a finalized diagonal entry
-    // of magnitude <= n eps ||H - sigma I||_F marks the shift singular.
-    const double mnorm2 = fmax(hnorm[0] - 2.0 * sigma.x * hnorm[1] +
-                                   (double)n * (sigma.x * sigma.x + sigma.y * sigma.y), 0.0);
-    const double sing_tol = (double)n * 2.220446049250313e-16 * sqrt(mnorm2);
-    // ---- shift setup: Z2 = last m columns of [Ct; H] - sigma on the diagonal
-    for (long long idx = tid; idx < (long long)ldz * m; idx += kThreads) {
-      int i = (int)(idx % ldz), q = (int)(idx / ldz);
-      int j = n - m + q;
-      double v = i < p ? Ct[i + (size_t)j * ldct] : H[(i - p) + (size_t)j * n];
-      cd z = mkcd(v, 0.0);
-      if (i - p == j) z = csub(z, sigma);
-      Z2[idx] = z;
-    }
-    if (track_t) {
-      for (long long idx = tid; idx < (long long)n * m; idx += kThreads) {
-        int i = (int)(idx % n), q = (int)(idx / n);
-        ZT[idx] = mkcd(i == n - m + q ? 1.0 : 0.0, 0.0);
-      }
-    }
-    if (tid == 0) s_sing = 0;
-    __syncthreads();
+    fp64_shift<MAXM>(d, sh, Z2, smem_raw, &s_piv, &s_sing);
+  }
+}
 
-    int k = n;
-    while (k > m) {
-      const int nbe = min(nb, k - m);
-      const int r = p + k - nbe;        // rows of [Ct; M] above the block
-      const int j0 = k - m - nbe;       // first fresh column
-      // stage the live rows of the block and reset coefficients
-      for (int idx = tid; idx < m * nbe; idx += kThreads) {
-        int t = idx % nbe, q = idx / nbe;
-        cand[q * kNB + t] = Z2[(r + t) + (size_t)q * ldz];
-      }
-      // coefficients: identity on the old live columns, e_{nbe-1} for the
-      // fresh column F_{nbe-1} that enters slot m (slots m, m+1 alternate)
-      for (int idx = tid; idx < L::kCoefRows * S; idx += kThreads) {
-        int c = idx / S, slot = idx % S;
-        cd v = mkcd(0.0, 0.0);
-        if ((slot < m && c == kNB + slot) || (slot == m && c == nbe - 1)) v = mkcd(1.0, 0.0);
-        coef[idx] = v;
-      }
-      {
-        const int c = nbe - 1, jc = j0 + c;
-        for (int t = tid; t <= c; t += kThreads) {
-          cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
-          if (t == c - m) z = csub(z, sigma);
-          cand[m * kNB + t] = z;
-        }
-      }
-      __syncthreads();
-      for (int c = nbe - 1; c >= 0; --c) {
-        const int fs = m + ((nbe - 1 - c) & 1);  // slot holding F_c
-        const int fn = (fs == m) ? m + 1 : m;    // slot for F_{c-1}
-        // ---- reflector U = I - tau v v^H on the m + 1 candidates of row c
-        //      (survivors 0..m-1, fresh fs): x U = conj(alpha) e_fs, x = row c.
-        if (tid < 32) {
-          double rest2 = 0.0;  // sum of |x_q|^2 over the m survivors
-          for (int q = tid; q < m; q += 32) {
-            const cd x = cand[q * kNB + c];
-            rest2 = fma(x.x, x.x, fma(x.y, x.y, rest2));
-          }
-          for (int o = 16; o > 0; o >>= 1) rest2 += __shfl_xor_sync(0xffffffffu, rest2, o);
-          const cd xf = cand[fs * kNB + c];
-          const double af2 = fma(xf.x, xf.x, xf.y * xf.y);
-          const double af = sqrt(af2);
-          const double nrm2 = rest2 + af2;
-          const double nrm = sqrt(nrm2);
-          // y = conj(x); alpha = -exp(i arg y_fs) ||y||; v = y - alpha e_fs
-          cd ph = af > 0.0 ? mkcd(xf.x / af, -xf.y / af) : mkcd(1.0, 0.0);
-          const cd alpha = mkcd(-ph.x * nrm, -ph.y * nrm);
-          const bool trivial = !(rest2 > 0.0);
-          for (int q = tid; q <= m; q += 32) {
-            const int slot = q < m ? q : fs;
-            const cd x = cand[slot * kNB + c];
-            cd v = mkcd(x.x, -x.y);
-            if (slot == fs) v = csub(v, alpha);
-            lmul[slot] = v;
-          }
-          if (tid == 0) {
-            // ||v||^2 = 2 ||y||^2 + 2 |y_fs| ||y||
-            const double vv = 2.0 * nrm2 + 2.0 * af * nrm;
-            lmul[MAXM + 2].x = trivial ? 0.0 : 2.0 / vv;
-            if (nrm <= sing_tol) s_sing = 1;  // |R(row, row)| = ||x|| at working precision
-          }
-        }
-        __syncthreads();
-        const double tau = lmul[MAXM + 2].x;
-        // ---- apply to window rows 0..c-1 and the nonzero coefficient rows;
-        //      load F_{c-1} into slot fn meanwhile.
-        if (tau != 0.0) {
-          const int nrow = c;
-          const int ncoef = (nbe - c) + m;
-          for (int e = tid; e < nrow + ncoef; e += kThreads) {
-            cd* base;
-            int stride;
-            if (e < nrow) {
-              base = cand + e;
-              stride = kNB;
-            } else {
-              const int ee = e - nrow;
-              const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
-              base = coef + crow * S;
-              stride = 1;
-            }
-            cd w = mkcd(0.0, 0.0);
-            for (int q = 0; q <= m; ++q) {
-              const int slot = q < m ? q : fs;
-              w = cfma(base[slot * stride], lmul[slot], w);
-            }
-            w = mkcd(w.x * tau, w.y * tau);
-            for (int q = 0; q <= m; ++q) {
-              const int slot = q < m ? q : fs;
-              const cd vc = mkcd(lmul[slot].x, -lmul[slot].y);
-              base[slot * stride] = cfms(w, vc, base[slot * stride]);
-            }
-          }
-        }
-        if (c > 0) {
-          const int cn = c - 1, jc = j0 + cn;
-          for (int t = tid; t <= cn; t += kThreads) {
-            cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
-            if (t == cn - m) z = csub(z, sigma);
-            cand[fn * kNB + t] = z;
-          }
-          for (int crow = tid; crow < L::kCoefRows; crow += kThreads)
-            coef[crow * S + fn] = mkcd(crow == cn ? 1.0 : 0.0, 0.0);
-        }
-        __syncthreads();
-      }
-
-      // ---- update the rows above the block (and the T rows)
-      for (int i = tid; i < r; i += kThreads) {
-        cd acc[MAXM];
-#pragma unroll
-        for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
-        for (int c = 0; c < nbe; ++c) {
-          const int jc = j0 + c;
-          const double z = i < p ? Ct[i + (size_t)jc * ldct] : H[(i - p) + (size_t)jc * n];
-          const cd* cr = coef + c * S;
-#pragma unroll
-          for (int q = 0; q < MAXM; ++q) {
-            if (q < m) {
-              cd w = cr[q];
-              acc[q].x = fma(z, w.x, acc[q].x);
-              acc[q].y = fma(z, w.y, acc[q].y);
-            }
-          }
-        }
-        for (int qq = 0; qq < m; ++qq) {
-          const cd zz = Z2[i + (size_t)qq * ldz];
-          const cd* cr = coef + (kNB + qq) * S;
-#pragma unroll
-          for (int q = 0; q < MAXM; ++q)
-            if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
-        }
-        const int cd_ = i - (r - m);  // diagonal correction of fresh column cd_
-        if (cd_ >= 0 && cd_ < min(m, nbe)) {
-          const cd* cr = coef + cd_ * S;
-#pragma unroll
-          for (int q = 0; q < MAXM; ++q)
-            if (q < m) acc[q] = cfms(sigma, cr[q], acc[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < MAXM; ++q)
-          if (q < m) Z2[i + (size_t)q * ldz] = acc[q];
-      }
-      if (track_t) {
-        // rows k-m .. n-1: ZT <- ZT P2 ; rows j0 .. j0+nbe-1: ZT = P1
-        const int lo = k - m;
-        for (int i = j0 + tid; i < n; i += kThreads) {
-          cd acc[MAXM];
-          if (i < lo) {
-            const cd* cr = coef + (i - j0) * S;
-#pragma unroll
-            for (int q = 0; q < MAXM; ++q) acc[q] = cr[q];
-          } else {
-#pragma unroll
-            for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
-            for (int qq = 0; qq < m; ++qq) {
-              const cd zz = ZT[i + (size_t)qq * n];
-              const cd* cr = coef + (kNB + qq) * S;
-#pragma unroll
-              for (int q = 0; q < MAXM; ++q)
-                if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < MAXM; ++q)
-            if (q < m) ZT[i + (size_t)q * n] = acc[q];
-        }
-      }
-      __syncthreads();
-      k -= nbe;
-    }
-
-    // ---- final m x m block: solve Wm Y = R(0:m, 0:m) by Gauss-Jordan with
-    // partial pivoting on the augmented [Wm | R1] (2m columns).
-    const int w2 = 2 * m;
-    for (int idx = tid; idx < m * w2; idx += kThreads) {
-      int i = idx % m, j = idx / m;
-      cd v;
-      if (j < m) v = Z2[(p + i) + (size_t)j * ldz];
-      else {
-        int jj = j - m;
-        v = mkcd(i <= jj ? R[i + (size_t)jj * n] : 0.0, 0.0);
-      }
-      Wm[i + j * MAXM] = v;
-    }
-    __syncthreads();
-    for (int kk = 0; kk < m; ++kk) {
-      if (tid < 32) {
-        double best = -1.0;
-        int brow = kk;
-        for (int i = kk + tid; i < m; i += 32) {
-          double v = cabs1(Wm[i + kk * MAXM]);
-          if (v > best) { best = v; brow = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          double ob = __shfl_xor_sync(0xffffffffu, best, o);
-          int orow = __shfl_xor_sync(0xffffffffu, brow, o);
-          if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
-        }
-        if (tid == 0) {
-          s_piv = brow;
-          const cd pv = Wm[brow + kk * MAXM];
-          if (best == 0.0 || sqrt(pv.x * pv.x + pv.y * pv.y) <= sing_tol) s_sing = 1;
-        }
-      }
-      __syncthreads();
-      const int pr = s_piv;
-      if (pr != kk) {
-        for (int j = tid; j < w2; j += kThreads) {
-          cd a = Wm[kk + j * MAXM];
-          Wm[kk + j * MAXM] = Wm[pr + j * MAXM];
-          Wm[pr + j * MAXM] = a;
-        }
-      }
-      __syncthreads();
-      const cd d = Wm[kk + kk * MAXM];
-      const bool dz = (d.x == 0.0 && d.y == 0.0);
-      if (tid < m) lmul[tid] = (tid == kk || dz) ? mkcd(0.0, 0.0) : cdiv(Wm[tid + kk * MAXM], d);
-      __syncthreads();
-      for (int idx = tid; idx < m * w2; idx += kThreads) {
-        int i = idx % m, j = idx / m;
-        if (i != kk && j > kk) Wm[i + j * MAXM] = cfms(lmul[i], Wm[kk + j * MAXM], Wm[i + j * MAXM]);
-      }
-      __syncthreads();
-    }
-    // Y(i, q) = Wm(i, m+q) / Wm(i, i)
-    for (int idx = tid; idx < m * m; idx += kThreads) {
-      int i = idx % m, q = idx / m;
-      cd d = Wm[i + i * MAXM];
-      Yb[i + q * MAXM] = (d.x == 0.0 && d.y == 0.0) ? mkcd(0.0, 0.0) : cdiv(Wm[i + (m + q) * MAXM], d);
-    }
-    __syncthreads();
-    const bool sing = s_sing != 0;
-    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-    // ---- outputs
-    if (mode == SSV_G || mode == SSV_TF) {
-      const double sg = mode == SSV_TF ? -1.0 : 1.0;
-      cd* o = out + (size_t)sh * m * ldo;
-      for (int idx = tid; idx < p * m; idx += kThreads) {
-        int i = idx % p, q = idx / p;
-        cd acc = mkcd(0.0, 0.0);
-        for (int t = 0; t < m; ++t) acc = cfma(Z2[i + (size_t)t * ldz], Yb[t + q * MAXM], acc);
-        if (sing) acc = mkcd(nanv, nanv);
-        o[i + (size_t)q * ldo] = mkcd(sg * acc.x, sg * acc.y);
-      }
-    }
-    if (track_t) {
-      cd* o;
-      long long ld;
-      if (mode == SSV_XHAT || mode == SSV_X) {
-        o = out + (size_t)sh * m * ldo;
-        ld = ldo;
-      } else {
-        o = xhat_copy + (size_t)sh * m * ldxc;
-        ld = ldxc;
-      }
-      for (int idx = tid; idx < n * m; idx += kThreads) {
-        int i = idx % n, q = idx / n;
-        cd acc = mkcd(0.0, 0.0);
-        for (int t = 0; t < m; ++t) acc = cfma(ZT[i + (size_t)t * n], Yb[t + q * MAXM], acc);
-        if (sing) acc = mkcd(nanv, nanv);
-        o[i + (size_t)q * ld] = acc;
-      }
-    }
-    if (status != nullptr && tid == 0) status[sh] = sing ? SSV_SHIFT_SINGULAR : SSV_SHIFT_OK;
-    __syncthreads();
+// Many systems in one launch: work item w = (system, shift) from `items`
+// (system in the high 32 bits), ordered by decreasing cost.
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) solve_fp64_batch_kernel(
+    const FpSys* __restrict__ systems, const unsigned long long* __restrict__ items, int nitems,
+    cd* __restrict__ scratch, size_t slot_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_piv;
+  __shared__ int s_sing;
+  cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const unsigned long long it = items[w];
+    const FpSys d = systems[(int)(it >> 32)];
+    fp64_shift<MAXM>(d, (int)(it & 0xffffffffu), Z2, smem_raw, &s_piv, &s_sing);
   }
 }
 
@@ -503,7 +562,7 @@ size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) {
 int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                long long ldo, int* status, double* resid, cudaStream_t st) {
   const int m = h->m;
-  int nb = o->nb > 0 ? o->nb : default_nb(h->n, m);
+  int nb = o->nb > 0 ? o->nb : tuned_nb(h->n, m, h->p, SSV_FP64, o->mode);
   if (nb > kNB) return SSV_ENOTSUP;
   if (s == 0) return SSV_OK;
   cd* xcopy = nullptr;
@@ -630,6 +689,204 @@ int solve_fp64_noalloc(const Handle* h, int s, const double* shifts, const ssv_o
   if (m <= 16) return launch_solve_noalloc<16>(h, s, shifts, nb, o->mode, out, ldo, status, st);
   if (m <= 32) return launch_solve_noalloc<32>(h, s, shifts, nb, o->mode, out, ldo, status, st);
   return SSV_ENOTSUP;
+}
+
+}  // namespace ssv
+
+// ---------------------------------------------------------------------------
+// Batched solve of many systems (uneven n, m, shift counts) in one persistent
+// launch.  A plan fixes the device-side system descriptors, the cost-ordered
+// (system, shift) worklist and the scratch, so that running it is one kernel
+// launch with fixed arguments (capturable in a CUDA graph and replayable after
+// the caller rewrites the shift buffers in place).
+// ---------------------------------------------------------------------------
+namespace ssv {
+
+struct BatchPlan {
+  int dev = 0;
+  int maxm = 1;
+  int nitems = 0;
+  int grid = 0;
+  size_t slot = 0;
+  size_t smem = 0;
+  FpSys* systems = nullptr;
+  unsigned long long* items = nullptr;
+  cd* scratch = nullptr;
+};
+
+namespace {
+
+template <int MAXM>
+int batch_config(BatchPlan* bp) {
+  using L = Layout<MAXM>;
+  auto kern = solve_fp64_batch_kernel<MAXM>;
+  SSV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+  int per_sm = 0;
+  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L::bytes));
+  per_sm = std::max(1, std::min(per_sm, 2));
+  bp->grid = std::max(1, std::min(bp->nitems, num_sms() * per_sm));
+  bp->smem = L::bytes;
+  return SSV_OK;
+}
+
+template <int MAXM>
+void batch_launch(const BatchPlan* bp, cudaStream_t st) {
+  solve_fp64_batch_kernel<MAXM><<<bp->grid, kThreads, bp->smem, st>>>(bp->systems, bp->items,
+                                                                     bp->nitems, bp->scratch,
+                                                                     bp->slot);
+  count_launch();
+}
+
+}  // namespace
+
+int batch_create(int nsys, const Handle* const* hs, const int* s, const double* const* shifts,
+                 const ssv_opts* o, double* const* outs, const long long* ldos, int* const* status,
+                 BatchPlan** out) {
+  *out = nullptr;
+  if (o->precision != SSV_FP64 || o->mode == SSV_X) return SSV_ENOTSUP;
+  BatchPlan* bp = new (std::nothrow) BatchPlan();
+  if (!bp) return SSV_ENOMEM;
+  cudaGetDevice(&bp->dev);
+  std::vector<FpSys> sys(nsys);
+  std::vector<std::pair<double, unsigned long long>> work;
+  const bool track_t = (o->mode == SSV_XHAT);
+  for (int k = 0; k < nsys; ++k) {
+    const Handle* h = hs[k];
+    FpSys& d = sys[k];
+    d.n = h->n; d.m = h->m; d.p = h->p;
+    d.nb = o->nb > 0 ? o->nb : tuned_nb(h->n, h->m, h->p, SSV_FP64, o->mode);
+    if (d.nb > kNB || h->m > 32) { delete bp; return SSV_ENOTSUP; }
+    d.mode = o->mode; d.H = h->H; d.Ct = h->Ct; d.ldct = h->p > 0 ? h->p : 1; d.R = h->R;
+    d.shifts = reinterpret_cast<const cd*>(shifts[k]);
+    d.out = reinterpret_cast<cd*>(outs[k]); d.ldo = ldos[k];
+    d.status = status ? status[k] : nullptr;
+    d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2;
+    bp->maxm = std::max(bp->maxm, h->m);
+    bp->slot = std::max(bp->slot, (size_t)(h->p + h->n) * h->m + (track_t ? (size_t)h->n * h->m : 0));
+    const double cost = (double)h->n * h->n * h->m * (1.0 + 2.0 * h->m / d.nb);
+    for (int j = 0; j < s[k]; ++j) work.push_back({cost, ((unsigned long long)k << 32) | (unsigned)j});
+  }
+  std::stable_sort(work.begin(), work.end(),
+                   [](const std::pair<double, unsigned long long>& a,
+                      const std::pair<double, unsigned long long>& b) { return a.first > b.first; });
+  bp->nitems = (int)work.size();
+  std::vector<unsigned long long> items(work.size());
+  for (size_t i = 0; i < work.size(); ++i) items[i] = work[i].second;
+  int rc = SSV_OK;
+  const int mm = bp->maxm;
+  if (bp->nitems > 0) {
+    if (mm <= 1) rc = batch_config<1>(bp);
+    else if (mm <= 2) rc = batch_config<2>(bp);
+    else if (mm <= 4) rc = batch_config<4>(bp);
+    else if (mm <= 8) rc = batch_config<8>(bp);
+    else if (mm <= 16) rc = batch_config<16>(bp);
+    else rc = batch_config<32>(bp);
+  }
+  cudaError_t e = cudaSuccess;
+  if (rc == SSV_OK && bp->nitems > 0) {
+    e = cudaMalloc((void**)&bp->systems, sizeof(FpSys) * nsys);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&bp->items, sizeof(unsigned long long) * items.size());
+    if (e == cudaSuccess) e = cudaMalloc((void**)&bp->scratch, sizeof(cd) * bp->slot * bp->grid);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(bp->systems, sys.data(), sizeof(FpSys) * nsys, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(bp->items, items.data(), sizeof(unsigned long long) * items.size(),
+                     cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      rc = e == cudaErrorMemoryAllocation ? SSV_ENOMEM : SSV_ECUDA;
+    }
+  }
+  if (rc != SSV_OK) {
+    batch_destroy(bp);
+    return rc;
+  }
+  *out = bp;
+  return SSV_OK;
+}
+
+int batch_run(const BatchPlan* bp, cudaStream_t st) {
+  if (bp->nitems == 0) return SSV_OK;
+  const int mm = bp->maxm;
+  if (mm <= 1) batch_launch<1>(bp, st);
+  else if (mm <= 2) batch_launch<2>(bp, st);
+  else if (mm <= 4) batch_launch<4>(bp, st);
+  else if (mm <= 8) batch_launch<8>(bp, st);
+  else if (mm <= 16) batch_launch<16>(bp, st);
+  else batch_launch<32>(bp, st);
+  SSV_CUDA_TRY(cudaGetLastError());
+  return SSV_OK;
+}
+
+void batch_destroy(BatchPlan* bp) {
+  if (!bp) return;
+  cudaFree(bp->systems);
+  cudaFree(bp->items);
+  cudaFree(bp->scratch);
+  delete bp;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner for the elimination block width n_b: times each candidate on the
+// caller's shifts with CUDA events and caches the fastest per
+// (n, m, p, precision, mode) for the life of the process.
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+  int n, m, p, prec, mode;
+  bool operator<(const TuneKey& o) const {
+    if (n != o.n) return n < o.n;
+    if (m != o.m) return m < o.m;
+    if (p != o.p) return p < o.p;
+    if (prec != o.prec) return prec < o.prec;
+    return mode < o.mode;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+}  // namespace
+
+int tuned_nb(int n, int m, int p, int prec, int mode) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(TuneKey{n, m, p, prec, mode});
+  return it == g_tune.end() ? default_nb(n, m) : it->second;
+}
+
+int autotune_nb(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
+                long long ldo, cudaStream_t st, int* best_nb, float* best_ms) {
+  static const int cand[] = {16, 24, 32, 48, 64};
+  cudaEvent_t e0, e1;
+  SSV_CUDA_TRY(cudaEventCreate(&e0));
+  SSV_CUDA_TRY(cudaEventCreate(&e1));
+  int best = default_nb(h->n, h->m);
+  float bms = 1e30f;
+  int rc = SSV_OK;
+  for (int c : cand) {
+    if (c > kNB) continue;
+    ssv_opts oo = *o;
+    oo.nb = c;
+    for (int rep = 0; rep < 2 && rc == SSV_OK; ++rep) {  // first run warms up
+      cudaEventRecord(e0, st);
+      rc = oo.precision == SSV_MIXED ? solve_mixed(h, s, shifts, &oo, out, ldo, nullptr, nullptr, st)
+                                     : solve_fp64(h, s, shifts, &oo, out, ldo, nullptr, nullptr, st);
+      cudaEventRecord(e1, st);
+      if (rc == SSV_OK && cudaEventSynchronize(e1) == cudaSuccess && rep == 1) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < bms) { bms = ms; best = c; }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SSV_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[TuneKey{h->n, h->m, h->p, o->precision, o->mode}] = best;
+  }
+  *best_nb = best;
+  if (best_ms) *best_ms = bms;
+  return SSV_OK;
 }
 
 }  // namespace ssv

@@ -171,6 +171,95 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
   return rc;
 }
 
+static int check_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
+                      const ssv_opts& o, double* const* outs, const long long* ldos) {
+  if (nsys < 0 || (nsys > 0 && (!hs || !s || !shifts || !outs || !ldos))) return SSV_EINVAL;
+  int rc = check_opts(&o);
+  if (rc != SSV_OK) return rc;
+  if (o.mode == SSV_X) return SSV_ENOTSUP;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int k = 0; k < nsys; ++k) {
+    const Handle* h = reinterpret_cast<const Handle*>(hs[k]);
+    if (!h || s[k] < 0) return SSV_EINVAL;
+    if (h->dev != dev) return SSV_EINVAL;
+    if (s[k] > 0 && (!shifts[k] || !outs[k])) return SSV_EINVAL;
+    const bool gmode = (o.mode == SSV_G || o.mode == SSV_TF);
+    if (gmode && ldos[k] < (h->p > 0 ? h->p : 1)) return SSV_EINVAL;
+    if (!gmode && ldos[k] < h->n) return SSV_EINVAL;
+  }
+  return SSV_OK;
+}
+
+int ssv_solve_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
+                   const ssv_opts* o_in, double* const* outs, const long long* ldos,
+                   int* const* status, void* stream) {
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_many(nsys, hs, s, shifts, o, outs, ldos);
+  if (rc != SSV_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (o.precision == SSV_MIXED) {
+    for (int k = 0; k < nsys && rc == SSV_OK; ++k)
+      rc = solve_mixed(reinterpret_cast<const Handle*>(hs[k]), s[k], shifts[k], &o, outs[k], ldos[k],
+                       status ? status[k] : nullptr, nullptr, st);
+    if (rc == SSV_OK) SSV_CUDA_TRY(cudaStreamSynchronize(st));
+    return rc;
+  }
+  BatchPlan* bp = nullptr;
+  rc = batch_create(nsys, reinterpret_cast<const Handle* const*>(hs), s, shifts, &o, outs, ldos,
+                    status, &bp);
+  if (rc != SSV_OK) return rc;
+  rc = batch_run(bp, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess && rc == SSV_OK) { set_cuda_error(e); rc = SSV_ECUDA; }
+  batch_destroy(bp);
+  return rc;
+}
+
+int ssv_batch_create(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
+                     const ssv_opts* o_in, double* const* outs, const long long* ldos,
+                     int* const* status, ssv_batch* out) {
+  if (!out) return SSV_EINVAL;
+  *out = nullptr;
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_many(nsys, hs, s, shifts, o, outs, ldos);
+  if (rc != SSV_OK) return rc;
+  if (o.precision != SSV_FP64) return SSV_ENOTSUP;
+  BatchPlan* bp = nullptr;
+  rc = batch_create(nsys, reinterpret_cast<const Handle* const*>(hs), s, shifts, &o, outs, ldos,
+                    status, &bp);
+  if (rc == SSV_OK) *out = reinterpret_cast<ssv_batch>(bp);
+  return rc;
+}
+
+int ssv_batch_run(ssv_batch b, void* stream) {
+  if (!b) return SSV_EINVAL;
+  return batch_run(reinterpret_cast<BatchPlan*>(b), (cudaStream_t)stream);
+}
+
+void ssv_batch_destroy(ssv_batch b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  batch_destroy(reinterpret_cast<BatchPlan*>(b));
+}
+
+int ssv_autotune(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, double* out,
+                 long long ldo, void* stream, int* best_nb, float* best_ms) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || s < 1 || !shifts || !out || !best_nb) return SSV_EINVAL;
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc != SSV_OK) return rc;
+  if (o.mode == SSV_X) return SSV_ENOTSUP;
+  const bool gmode = (o.mode == SSV_G || o.mode == SSV_TF);
+  if (gmode && ldo < (h->p > 0 ? h->p : 1)) return SSV_EINVAL;
+  if (!gmode && ldo < h->n) return SSV_EINVAL;
+  return autotune_nb(h, s, shifts, &o, out, ldo, (cudaStream_t)stream, best_nb, best_ms);
+}
+
 int ssv_solve_noalloc(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in,
                       double* out, long long ldo, int* status, void* stream) {
   Handle* h = reinterpret_cast<Handle*>(hh);

@@ -114,6 +114,18 @@ size_t noalloc_scratch_bytes();
 int default_nb(int n, int m);
 int num_sms();
 
+// batched multi-system FP64 solve (solve_fp64.cu)
+struct BatchPlan;
+int batch_create(int nsys, const Handle* const* hs, const int* s, const double* const* shifts,
+                 const ssv_opts* o, double* const* outs, const long long* ldos, int* const* status,
+                 BatchPlan** out);
+int batch_run(const BatchPlan* bp, cudaStream_t st);
+void batch_destroy(BatchPlan* bp);
+// n_b autotuner (solve_fp64.cu)
+int tuned_nb(int n, int m, int p, int prec, int mode);
+int autotune_nb(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
+                long long ldo, cudaStream_t st, int* best_nb, float* best_ms);
+
 // Kernel-launch counter (every launch site calls count_launch()).
 void count_launch(long long k = 1);
 // DFMA (kind 0) / FFMA (kind 1) throughput probe, TFLOP/s.

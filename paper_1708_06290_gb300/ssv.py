@@ -55,7 +55,8 @@ class Opts(ctypes.Structure):
 
 EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced",
            "ssv_dims", "ssv_footprint", "ssv_handle_bytes", "ssv_destroy", "ssv_strerror",
-           "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc")
+           "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc", "ssv_solve_many",
+           "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune")
 
 _lib = None
 
@@ -84,6 +85,16 @@ def load(build_if_missing=True):
     L.ssv_load_reduced.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
     L.ssv_solve.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P, P]
     L.ssv_solve_noalloc.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P]
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    L.ssv_solve_many.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
+                                 ctypes.POINTER(LL), PP, P]
+    L.ssv_batch_create.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
+                                   ctypes.POINTER(LL), PP, ctypes.POINTER(P)]
+    L.ssv_batch_run.argtypes = [P, P]
+    L.ssv_batch_destroy.argtypes = [P]
+    L.ssv_batch_destroy.restype = None
+    L.ssv_autotune.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, ctypes.POINTER(I),
+                               ctypes.POINTER(ctypes.c_float)]
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
     L.ssv_dims.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
@@ -97,7 +108,8 @@ def load(build_if_missing=True):
     L.ssv_kernel_launches.argtypes = []
     L.ssv_kernel_launches.restype = ctypes.c_longlong
     L.ssv_peak_probe.argtypes = [I, P, ctypes.POINTER(ctypes.c_double)]
-    for f in ("ssv_reduce", "ssv_load_reduced", "ssv_solve", "ssv_solve_noalloc", "ssv_apply_q", "ssv_get_reduced", "ssv_dims",
+    for f in ("ssv_reduce", "ssv_load_reduced", "ssv_solve", "ssv_solve_noalloc",
+              "ssv_solve_many", "ssv_batch_create", "ssv_batch_run", "ssv_autotune", "ssv_apply_q", "ssv_get_reduced", "ssv_dims",
               "ssv_footprint", "ssv_handle_bytes", "ssv_last_cuda_error", "ssv_peak_probe"):
         getattr(L, f).restype = I
     _lib = L
@@ -300,3 +312,88 @@ def peak_probe(kind="fp64", stream=None):
     _check(L.ssv_peak_probe({"fp64": 0, "fp32": 1}[kind], _stream_ptr(stream), ctypes.byref(v)),
            "ssv_peak_probe")
     return v.value
+
+
+def _many_args(handles, shifts, outs, statuses):
+    n = len(handles)
+    VP = ctypes.c_void_p * n
+    hs = VP(*[h.ptr for h in handles])
+    ss = (ctypes.c_int * n)(*[int(x.numel()) for x in shifts])
+    sp = VP(*[x.data_ptr() for x in shifts])
+    op = VP(*[o.data_ptr() for o in outs])
+    ld = (ctypes.c_longlong * n)(*[_ld(o, o.shape[0]) for o in outs])
+    st = VP(*[x.data_ptr() for x in statuses])
+    cast = lambda a: ctypes.cast(a, ctypes.POINTER(ctypes.c_void_p))  # noqa: E731
+    return n, cast(hs), ss, cast(sp), cast(op), ld, cast(st)
+
+
+def _alloc_outputs(handles, shifts, mode):
+    outs, sts = [], []
+    for h, x in zip(handles, shifts):
+        rows = h.out_rows(mode)
+        outs.append(torch.empty((x.numel() * h.m, max(rows, 1)), dtype=torch.complex128,
+                                device=x.device).t())
+        sts.append(torch.empty(x.numel(), dtype=torch.int32, device=x.device))
+    return outs, sts
+
+
+def solve_many(handles, shifts, mode="g", precision="fp64", nb=0, stream=None):
+    """Solve many systems (list of Handles, list of complex128 CUDA shift vectors) in one
+    batched launch.  Returns (outs, statuses), one entry per system."""
+    L = load()
+    for x in shifts:
+        _need_cuda(x, torch.complex128, "shifts")
+    outs, sts = _alloc_outputs(handles, shifts, mode)
+    o = opts(precision, mode, nb)
+    n, hs, ss, sp, op, ld, st = _many_args(handles, shifts, outs, sts)
+    _check(L.ssv_solve_many(n, hs, ss, sp, ctypes.byref(o), op, ld, st, _stream_ptr(stream)),
+           "ssv_solve_many")
+    return outs, sts
+
+
+class BatchPlan:
+    """A fixed FP64 multi-system solve: run() is one kernel launch with constant
+    arguments (capturable in a CUDA graph).  Rewrite the shift tensors in place
+    between runs; outputs land in .outs / .statuses."""
+
+    def __init__(self, handles, shifts, mode="g", nb=0):
+        L = load()
+        self.handles = list(handles)
+        self.shifts = list(shifts)
+        self.outs, self.statuses = _alloc_outputs(self.handles, self.shifts, mode)
+        o = opts("fp64", mode, nb)
+        n, hs, ss, sp, op, ld, st = _many_args(self.handles, self.shifts, self.outs, self.statuses)
+        b = ctypes.c_void_p()
+        _check(L.ssv_batch_create(n, hs, ss, sp, ctypes.byref(o), op, ld, st, ctypes.byref(b)),
+               "ssv_batch_create")
+        self._b = b
+
+    def run(self, stream=None):
+        _check(load().ssv_batch_run(self._b, _stream_ptr(stream)), "ssv_batch_run")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().ssv_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(handle, shifts, mode="g", precision="fp64", stream=None):
+    """Pick and cache the block width n_b for this system; returns (nb, ms)."""
+    L = load()
+    _need_cuda(shifts, torch.complex128, "shifts")
+    rows = handle.out_rows(mode)
+    out = torch.empty((shifts.numel() * handle.m, max(rows, 1)), dtype=torch.complex128,
+                      device=shifts.device).t()
+    o = opts(precision, mode)
+    nb = ctypes.c_int()
+    ms = ctypes.c_float()
+    _check(L.ssv_autotune(handle.ptr, shifts.numel(), ctypes.c_void_p(shifts.data_ptr()),
+                          ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), _ld(out, rows),
+                          _stream_ptr(stream), ctypes.byref(nb), ctypes.byref(ms)), "ssv_autotune")
+    return nb.value, ms.value
