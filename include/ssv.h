@@ -119,7 +119,9 @@ int ssv_solve(ssv_handle h, int s, const double* shifts, const ssv_opts* o, doub
  *   statuses in status[k] (device, or status == NULL / status[k] == NULL).
  *   hs, s, shifts, outs, ldos, status are host arrays.  Modes SSV_G, SSV_TF,
  *   SSV_XHAT.  All handles must belong to the current device.
- * The call returns after the work has completed (it frees its plan).
+ * Stream-ordered like ssv_solve: the per-call plan (descriptors, worklist,
+ * scratch) is allocated and freed on `stream` (on the legacy default stream,
+ * NULL, the call synchronises that stream before returning).
  * Errors: SSV_EINVAL, SSV_ENOTSUP, SSV_ENOMEM, SSV_ECUDA.
  */
 int ssv_solve_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,

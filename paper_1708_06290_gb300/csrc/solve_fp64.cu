@@ -704,6 +704,8 @@ namespace ssv {
 
 struct BatchPlan {
   int dev = 0;
+  bool stream_ordered = false;  // buffers from cudaMallocAsync on `stream`
+  cudaStream_t stream = nullptr;
   int maxm = 1;
   int nitems = 0;
   int grid = 0;
@@ -741,12 +743,14 @@ void batch_launch(const BatchPlan* bp, cudaStream_t st) {
 
 int batch_create(int nsys, const Handle* const* hs, const int* s, const double* const* shifts,
                  const ssv_opts* o, double* const* outs, const long long* ldos, int* const* status,
-                 BatchPlan** out) {
+                 BatchPlan** out, cudaStream_t stream_ordered) {
   *out = nullptr;
   if (o->precision != SSV_FP64 || o->mode == SSV_X) return SSV_ENOTSUP;
   BatchPlan* bp = new (std::nothrow) BatchPlan();
   if (!bp) return SSV_ENOMEM;
   cudaGetDevice(&bp->dev);
+  bp->stream_ordered = stream_ordered != nullptr;
+  bp->stream = stream_ordered;
   std::vector<FpSys> sys(nsys);
   std::vector<std::pair<double, unsigned long long>> work;
   const bool track_t = (o->mode == SSV_XHAT);
@@ -784,14 +788,30 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
   }
   cudaError_t e = cudaSuccess;
   if (rc == SSV_OK && bp->nitems > 0) {
-    e = cudaMalloc((void**)&bp->systems, sizeof(FpSys) * nsys);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&bp->items, sizeof(unsigned long long) * items.size());
-    if (e == cudaSuccess) e = cudaMalloc((void**)&bp->scratch, sizeof(cd) * bp->slot * bp->grid);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(bp->systems, sys.data(), sizeof(FpSys) * nsys, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(bp->items, items.data(), sizeof(unsigned long long) * items.size(),
-                     cudaMemcpyHostToDevice);
+    if (bp->stream_ordered) {
+      // stream-ordered: no device-wide synchronisation, so concurrent batches on
+      // other streams keep running; pageable sources are consumed before return
+      cudaStream_t st = bp->stream;
+      e = cudaMallocAsync((void**)&bp->systems, sizeof(FpSys) * nsys, st);
+      if (e == cudaSuccess)
+        e = cudaMallocAsync((void**)&bp->items, sizeof(unsigned long long) * items.size(), st);
+      if (e == cudaSuccess)
+        e = cudaMallocAsync((void**)&bp->scratch, sizeof(cd) * bp->slot * bp->grid, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bp->systems, sys.data(), sizeof(FpSys) * nsys, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bp->items, items.data(), sizeof(unsigned long long) * items.size(),
+                            cudaMemcpyHostToDevice, st);
+    } else {
+      e = cudaMalloc((void**)&bp->systems, sizeof(FpSys) * nsys);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&bp->items, sizeof(unsigned long long) * items.size());
+      if (e == cudaSuccess) e = cudaMalloc((void**)&bp->scratch, sizeof(cd) * bp->slot * bp->grid);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(bp->systems, sys.data(), sizeof(FpSys) * nsys, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(bp->items, items.data(), sizeof(unsigned long long) * items.size(),
+                       cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
       set_cuda_error(e);
       rc = e == cudaErrorMemoryAllocation ? SSV_ENOMEM : SSV_ECUDA;
@@ -820,9 +840,15 @@ int batch_run(const BatchPlan* bp, cudaStream_t st) {
 
 void batch_destroy(BatchPlan* bp) {
   if (!bp) return;
-  cudaFree(bp->systems);
-  cudaFree(bp->items);
-  cudaFree(bp->scratch);
+  if (bp->stream_ordered) {
+    if (bp->systems) cudaFreeAsync(bp->systems, bp->stream);
+    if (bp->items) cudaFreeAsync(bp->items, bp->stream);
+    if (bp->scratch) cudaFreeAsync(bp->scratch, bp->stream);
+  } else {
+    cudaFree(bp->systems);
+    cudaFree(bp->items);
+    cudaFree(bp->scratch);
+  }
   delete bp;
 }
 

@@ -203,16 +203,20 @@ int ssv_solve_many(int nsys, const ssv_handle* hs, const int* s, const double* c
     for (int k = 0; k < nsys && rc == SSV_OK; ++k)
       rc = solve_mixed(reinterpret_cast<const Handle*>(hs[k]), s[k], shifts[k], &o, outs[k], ldos[k],
                        status ? status[k] : nullptr, nullptr, st);
-    if (rc == SSV_OK) SSV_CUDA_TRY(cudaStreamSynchronize(st));
     return rc;
   }
+  // stream-ordered plan on a non-default stream (no device-wide synchronisation);
+  // on the legacy default stream the plan is ordinary and freed after a sync
   BatchPlan* bp = nullptr;
+  cudaStream_t so = st != nullptr ? st : nullptr;
   rc = batch_create(nsys, reinterpret_cast<const Handle* const*>(hs), s, shifts, &o, outs, ldos,
-                    status, &bp);
+                    status, &bp, so);
   if (rc != SSV_OK) return rc;
   rc = batch_run(bp, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess && rc == SSV_OK) { set_cuda_error(e); rc = SSV_ECUDA; }
+  if (so == nullptr) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && rc == SSV_OK) { set_cuda_error(e); rc = SSV_ECUDA; }
+  }
   batch_destroy(bp);
   return rc;
 }
@@ -229,7 +233,7 @@ int ssv_batch_create(int nsys, const ssv_handle* hs, const int* s, const double*
   if (o.precision != SSV_FP64) return SSV_ENOTSUP;
   BatchPlan* bp = nullptr;
   rc = batch_create(nsys, reinterpret_cast<const Handle* const*>(hs), s, shifts, &o, outs, ldos,
-                    status, &bp);
+                    status, &bp, nullptr);
   if (rc == SSV_OK) *out = reinterpret_cast<ssv_batch>(bp);
   return rc;
 }

@@ -116,9 +116,11 @@ int num_sms();
 
 // batched multi-system FP64 solve (solve_fp64.cu)
 struct BatchPlan;
+// stream_ordered != nullptr: stream-ordered buffers on that stream (freed by
+// batch_destroy on it, no device-wide synchronisation); else cudaMalloc.
 int batch_create(int nsys, const Handle* const* hs, const int* s, const double* const* shifts,
                  const ssv_opts* o, double* const* outs, const long long* ldos, int* const* status,
-                 BatchPlan** out);
+                 BatchPlan** out, cudaStream_t stream_ordered);
 int batch_run(const BatchPlan* bp, cudaStream_t st);
 void batch_destroy(BatchPlan* bp);
 // n_b autotuner (solve_fp64.cu)
