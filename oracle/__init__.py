@@ -32,19 +32,23 @@ STATUS_OK = 0
 STATUS_SINGULAR = 1
 
 
+def load_library(path):
+    """CDLL of an oracle build at `path` with its argument types declared."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    lib.ora_dense_solve.argtypes = [I, I, P, I, P, I, I, P, P, P]
+    lib.ora_reduce.argtypes = [I, I, I, P, I, P, I, P, I, P, P, P, P]
+    lib.ora_reduced_solve.argtypes = [I, I, I, P, I, P, I, P, I, I, P, I, P, P, P]
+    for f in (lib.ora_dense_solve, lib.ora_reduce, lib.ora_reduced_solve):
+        f.restype = I
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        path = _build.build()
-        lib = ctypes.CDLL(path)
-        P = ctypes.c_void_p
-        I = ctypes.c_int
-        lib.ora_dense_solve.argtypes = [I, I, P, I, P, I, I, P, P, P]
-        lib.ora_reduce.argtypes = [I, I, I, P, I, P, I, P, I, P, P, P, P]
-        lib.ora_reduced_solve.argtypes = [I, I, I, P, I, P, I, P, I, I, P, I, P, P, P]
-        for f in (lib.ora_dense_solve, lib.ora_reduce, lib.ora_reduced_solve):
-            f.restype = I
-        _lib = lib
+        _lib = load_library(_build.build())
     return _lib
 
 
