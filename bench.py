@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--cpu-shifts", type=int, default=16)
     ap.add_argument("--shifts", type=int, default=0,
                     help="solve only this many evenly spread grid shifts (profiling); 0 = all")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batching and serving measurements")
+    ap.add_argument("--serving-scale", type=float, default=1.0)
+    ap.add_argument("--serving-requests", type=int, default=40)
+    ap.add_argument("--serving-budget-gb", type=float, default=16.0)
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling case: one solve on a handle restored from an m-Hessenberg "
                          "stand-in (H = triu(A, -m), R = triu(B), Ct = C), no reduction")
@@ -181,33 +186,81 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# multi-rank aggregation (weak scaling: every rank solves its own copy)
+# ----------------------------------------------------------------------------
+def combine_ranks(world, shifts_per_rank, steps, local_ms, reduce_max):
+    """Whole-job throughput: shifts of all ranks over the slowest rank's time."""
+    total_ms = reduce_max(local_ms)
+    return world * shifts_per_rank * steps / (total_ms * 1e-3), total_ms
+
+
+# ----------------------------------------------------------------------------
 # the GPU arm
 # ----------------------------------------------------------------------------
-def profile_solve(args):
-    """One solve of the workload's shifts on a restored stand-in handle: the solve
-    kernel runs after only the handful of launches that restore the handle."""
+def serving_measurement(ssv, dev, args):
+    """The serving workload: 8 preloaded reduced systems (n = 1000 .. 10000,
+    m = (1, 4, 16)[i % 3], p = m), requests of 1..256 imaginary-axis shifts.
+    Saturated throughput first (all requests at t = 0), then Poisson arrivals at
+    0.5 / 0.8 / 0.95 of it; p50 / p99 latency per load."""
     import torch
 
-    from paper_1708_06290_gb300 import ssv
+    from paper_1708_06290_gb300.serve import Server, make_requests
 
-    sysr, sig = W.workload_precision()
-    if args.shifts:
-        sig = sig[np.unique(np.linspace(0, len(sig) - 1, args.shifts).astype(int))]
-    m = sysr.m
-    Hs = np.triu(sysr.A, -m)
-    Rs = np.triu(sysr.B)
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().cuda()  # noqa
-    h = ssv.load_reduced(dev(Hs), dev(Rs), dev(sysr.C))
-    sd = torch.from_numpy(sig.astype(np.complex128)).cuda()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    out, st, _ = h.solve(sd, mode="g", precision=args.precision, nb=args.nb)
-    e1.record()
+    systems = W.workload_serving_systems(scale=args.serving_scale)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().to(dev)  # noqa
+    t0 = time.perf_counter()
+    handles = [ssv.reduce(to(sy.A), to(sy.B), to(sy.C)) for sy in systems]
     torch.cuda.synchronize()
-    print(json.dumps({"profile": "solve", "n": sysr.n, "m": m, "shifts": int(len(sig)),
-                      "ms": e0.elapsed_time(e1), "nonzero_status": int((st != 0).sum())}))
-    h.close()
-    return 0
+    t_reduce = time.perf_counter() - t0
+    budget = int(args.serving_budget_gb * (1 << 30))
+    nreq = args.serving_requests
+    warm = make_requests(W.serving_requests(8, 100.0, seed=900))
+    Server(handles, slots=4, mem_budget=budget).run(warm, realtime=False)
+    sat = Server(handles, slots=4, mem_budget=budget).run(
+        make_requests(W.serving_requests(nreq, 1.0, seed=901)), realtime=False)
+    req_rate = sat["requests"] / sat["wall_s"]
+    loads = {}
+    for f in (0.5, 0.8, 0.95):
+        st = Server(handles, slots=4, mem_budget=budget).run(
+            make_requests(W.serving_requests(nreq, f * req_rate, seed=902 + int(100 * f))),
+            realtime=True)
+        loads["%.2f" % f] = {k: st[k] for k in ("p50_ms", "p99_ms", "shift_solves_per_s",
+                                                 "requests", "batches", "max_inflight_batches")}
+    for h in handles:
+        h.close()
+    return {"systems_n": [sy.n for sy in systems], "systems_m": [sy.m for sy in systems],
+            "reduce_s": t_reduce, "budget_bytes": budget,
+            "saturated": {"requests_per_s": req_rate,
+                          "shift_solves_per_s": sat["shift_solves_per_s"],
+                          "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"]},
+            "poisson": loads}
+
+
+def batching_measurement(ssv, dev, args):
+    """The batching workload: 64 systems, n ~ U{200..3000}, m in {1,2,4,8},
+    16..512 shifts each, one ssv_solve_many launch (FP64); reductions untimed."""
+    import torch
+
+    work = W.workload_batching()
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().to(dev)  # noqa
+    handles = [ssv.reduce(to(sy.A), to(sy.B), to(sy.C)) for sy, _ in work]
+    shifts = [torch.from_numpy(sig.astype(np.complex128)).to(dev) for _, sig in work]
+    total = sum(int(x.numel()) for x in shifts)
+    ssv.solve_many(handles, shifts, mode="g")
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ssv.solve_many(handles, shifts, mode="g")
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    for h in handles:
+        h.close()
+    ms = float(np.median(ts))
+    return {"systems": len(work), "shifts": total, "ms": ms,
+            "shift_solves_per_s": total / (ms * 1e-3), "launches_per_batch": 1}
 
 
 def main():
@@ -234,6 +287,13 @@ def main():
         if world > 1:
             dist.barrier()
 
+    def max_over_ranks(x):
+        if world > 1:
+            tt = torch.tensor([x], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            return float(tt.item())
+        return x
+
     ssv.load()
     sysr, sig = W.workload_precision()
     if args.shifts:
@@ -252,67 +312,56 @@ def main():
     status = torch.empty(s, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    ev = {}
-
-    def step(record=None):
-        if record is not None:
-            record[0].record(stream)
+    def step(precision):
         h = ssv.reduce(A_d, B_d, C_d)
-        if record is not None:
-            record[1].record(stream)
-        h.solve(sig_d, mode="g", precision=args.precision, nb=args.nb, out=out, status=status)
-        if record is not None:
-            record[2].record(stream)
+        h.solve(sig_d, mode="g", precision=precision, nb=args.nb, out=out, status=status)
         return h
 
-    # correctness gate outside the timed region: statuses and backward errors
-    h = step()
-    _, st_chk, resid = h.solve(sig_d, mode="g", precision=args.precision, nb=args.nb,
-                               want_resid=True)
-    torch.cuda.synchronize()
-    max_bwd = float(resid.max())
-    n_bad = int((st_chk != 0).sum())
-    h.close()
-
-    for _ in range(args.warmup):
-        step().close()
-    torch.cuda.synchronize()
-    barrier()
+    def timed(precision):
+        """W warm-up steps, then K steps bracketed by barrier + sync; phase spans
+        from the library tracer (CUDA events on this stream)."""
+        h = step(precision)
+        _, st_chk, resid = h.solve(sig_d, mode="g", precision=precision, nb=args.nb,
+                                   want_resid=True)
+        torch.cuda.synchronize()
+        gate = {"max_backward_error": float(resid.max()), "nonzero_status": int((st_chk != 0).sum())}
+        h.close()
+        for _ in range(args.warmup):
+            step(precision).close()
+        torch.cuda.synchronize()
+        ssv.trace(True)
+        launches0 = ssv.kernel_launches()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        handles = []
+        for _ in range(args.steps):
+            handles.append(step(precision))
+            if len(handles) > 1:
+                handles.pop(0).close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        for hh in handles:
+            hh.close()
+        launches = ssv.kernel_launches() - launches0
+        phases = ssv.trace_read()
+        ssv.trace(False)
+        value, total_ms = combine_ranks(world, s, args.steps, e0.elapsed_time(e1), max_over_ranks)
+        phase_ms = {k: v[0] / args.steps for k, v in phases.items()}
+        return {"value": value, "ms_per_step": total_ms / args.steps,
+                "phase_ms_per_step": phase_ms, "gpu_launches": int(launches), **gate}
 
     fp64_peak = ssv.peak_probe("fp64")
+    fp32_peak = ssv.peak_probe("fp32")
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
-    recs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    launches0 = ssv.kernel_launches()
-    barrier()
-    torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    handles = []
-    for k in range(args.steps):
-        handles.append(step(recs[k]))
-        if len(handles) > 1:
-            handles.pop(0).close()
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    for hh in handles:
-        hh.close()
-    launches = ssv.kernel_launches() - launches0
+    res = {"fp64": timed("fp64"), "mixed": timed("mixed")}
     clocks = clk.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    red_ms = float(np.mean([r[0].elapsed_time(r[1]) for r in recs]))
-    solve_ms = float(np.mean([r[1].elapsed_time(r[2]) for r in recs]))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = world * s * args.steps / (total_ms * 1e-3)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers (FP64 path)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     A_h = pin(sysr.A.T.copy())
     B_h = pin(sysr.B.T.copy())
@@ -333,7 +382,7 @@ def main():
         C_e.copy_(C_h, non_blocking=True)
         sig_e.copy_(sig_h, non_blocking=True)
         hh = ssv.reduce(A_e.t(), B_e.t(), C_e.t())
-        o, st2, _ = hh.solve(sig_e, mode="g", precision=args.precision, nb=args.nb)
+        o, st2, _ = hh.solve(sig_e, mode="g", precision="fp64", nb=args.nb)
         G_h.copy_(o.t(), non_blocking=True)
         st_h.copy_(st2, non_blocking=True)
         torch.cuda.synchronize()
@@ -348,14 +397,12 @@ def main():
         for _ in range(args.e2e_steps):
             e2e_step()
         barrier()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
         e2e_value = world * s * args.e2e_steps / e2e_s
 
-    # ---- roofline of the dominant kernel (the shift-batched solve)
+    # ---- roofline of the dominant kernel of the reported (FP64) path
+    head = res["fp64"]
+    solve_ms = head["phase_ms_per_step"].get("solve_fp64", float("nan"))
     flops_floor = s * (2.0 * n * n * m + 4.0 * n * m * p)   # n_b-independent algorithmic floor
     achieved = flops_floor / (solve_ms * 1e-3) / 1e12
     roofline = {
@@ -363,31 +410,39 @@ def main():
         "achieved": achieved, "peak": fp64_peak, "frac": achieved / fp64_peak,
         "peak_source": "FP64 DFMA probe measured in this run (nominal GB300 FP64 1.25 TFLOP/s)",
         "flops_per_launch": flops_floor, "launch_ms": solve_ms,
+        "flops_definition": "2 n^2 m + 4 n m p per shift (trailing update Z1 P1 + Ct rows)",
         "traffic": None,
     }
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "c64+f64",
-        "data": "synthetic",
-        "config": workload_config(sysr, sig, args.nb, args.precision),
-        "phase_ms": {"reduce": red_ms, "solve": solve_ms},
-        "solve_only_shift_solves_per_s": s / (solve_ms * 1e-3),
-        "max_backward_error": max_bwd, "nonzero_status": n_bad,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(sysr, sig, args.nb, "fp64"),
+        "phase_ms": head["phase_ms_per_step"],
+        "max_backward_error": head["max_backward_error"], "nonzero_status": head["nonzero_status"],
+        "mixed_vs_fp64": {
+            "fp64": {k: res["fp64"][k] for k in ("value", "ms_per_step", "phase_ms_per_step",
+                                                 "max_backward_error")},
+            "mixed": {k: res["mixed"][k] for k in ("value", "ms_per_step", "phase_ms_per_step",
+                                                   "max_backward_error")},
+            "fp32_ffma_peak_tflops": fp32_peak,
+        },
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
+        "gpu_launches": head["gpu_launches"],
         "roofline": roofline,
     }
+    if not args.no_extras and world == 1:
+        line["batching"] = batching_measurement(ssv, dev, args)
+        line["serving"] = serving_measurement(ssv, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, t_red, per_shift, cnt, _ = time_oracle(sysr, sig, args.cpu_shifts)
         line["cpu_baseline"] = {
             "value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": "oracle reduction of the full n=5000 system (%.1f s) + tier-2 reduced GEPP "
-                      "on %d evenly spread shifts (%.3f s/shift), extrapolated to 2000 shifts"
-                      % (t_red, cnt, per_shift)}
+                      "on %d evenly spread shifts (%.3f s/shift), extrapolated to %d shifts"
+                      % (t_red, cnt, per_shift, s)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

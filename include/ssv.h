@@ -148,7 +148,8 @@ void ssv_batch_destroy(ssv_batch b);
 
 /*
  * ssv_autotune -- choose the elimination block width n_b for this handle,
- * precision and mode by timing each candidate (16, 24, 32, 48, 64) on the
+ * precision and mode by timing each candidate (FP64: 32, 48, 64, 96, 128;
+ * MIXED: 16, 24, 32, 48, 64) on the
  * given s shifts (device) with CUDA events; writes the results to out
  * (scratch for the caller, layout as ssv_solve).  The choice is cached for
  * the process and used by every later call with o->nb == 0 on a system of the
@@ -242,6 +243,18 @@ int ssv_last_cuda_error(void);
  * threads); differences of two reads count the launches of the calls between
  * them.  Measurement aid; the paper has no counterpart. */
 long long ssv_kernel_launches(void);
+
+/* Phase tracer (measurement aid; the paper has no counterpart).  When
+ * enabled, the library records CUDA events on the launching stream around its
+ * internal phases ("reduce", "solve_fp64", "mixed_sweep0", "mixed_residual",
+ * "mixed_correction", "mixed_fallback", "batch").  ssv_trace_read
+ * synchronises the recorded events and returns up to `max` phases: names
+ * (NUL-terminated, `name_len` bytes each), total milliseconds and call
+ * counts; *count receives the number of distinct phases.  Keep the tracer off
+ * while a stream is captured into a CUDA graph. */
+int ssv_trace_enable(int on);
+int ssv_trace_reset(void);
+int ssv_trace_read(int max, char* names, int name_len, float* total_ms, int* calls, int* count);
 
 /* Arithmetic peak probe (measurement aid; the paper has no counterpart):
  * runs independent fused multiply-add chains on every SM of the current

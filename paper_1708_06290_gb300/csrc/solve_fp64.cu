@@ -39,7 +39,7 @@ namespace ssv {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kNB = 64;  // maximum rows per block (runtime nb <= kNB)
+constexpr int kNB = 128;  // maximum rows per block (runtime nb <= kNB)
 
 // Shared memory per thread block:
 //   cand[slot * kNB + t]       rows t of the window block, slot in [0, m]
@@ -496,7 +496,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
 int default_nb(int n, int m) {
   (void)n;
   (void)m;
-  return kNB;
+  return 64;
 }
 
 // Work list of the shifts with mask[j] != 0 (single block, order preserved).
@@ -880,15 +880,17 @@ int tuned_nb(int n, int m, int p, int prec, int mode) {
 
 int autotune_nb(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                 long long ldo, cudaStream_t st, int* best_nb, float* best_ms) {
-  static const int cand[] = {16, 24, 32, 48, 64};
+  static const int cand_fp64[] = {32, 48, 64, 96, 128};
+  static const int cand_mixed[] = {16, 24, 32, 48, 64};
+  const int* cand = o->precision == SSV_MIXED ? cand_mixed : cand_fp64;
   cudaEvent_t e0, e1;
   SSV_CUDA_TRY(cudaEventCreate(&e0));
   SSV_CUDA_TRY(cudaEventCreate(&e1));
   int best = default_nb(h->n, h->m);
   float bms = 1e30f;
   int rc = SSV_OK;
-  for (int c : cand) {
-    if (c > kNB) continue;
+  for (int ci = 0; ci < 5; ++ci) {
+    const int c = cand[ci];
     ssv_opts oo = *o;
     oo.nb = c;
     for (int rep = 0; rep < 2 && rc == SSV_OK; ++rep) {  // first run warms up

@@ -914,23 +914,29 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
   mixed_init_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(s, ms.flags, ms.eta, ms.acc,
                                                                      ms.list, ms.count);
   count_launch();
+  void* tr = trace_begin("mixed_sweep0", st);
   k0<<<grid, kThreads, L::bytes, st>>>(n, m, nb, h->Hhi, h->R, sd, ms.list, ms.count, ms.slots,
                                       slot_bytes, ms.X, ms.E, ms.flags, h->hnorm2);
   count_launch();
+  trace_end(tr, st);
   const int rgrid = num_sms() * kResidBlocksPerSm;
   for (int it = 0; it <= max_refine; ++it) {
+    tr = trace_begin("mixed_residual", st);
     mixed_residual_kernel<MAXM><<<rgrid, kRT, 0, st>>>(n, m, h->Hhi, h->Hlo, h->R, sd, ms.list,
                                                       ms.count, ms.X, ms.E, ms.acc);
     count_launch();
+    trace_end(tr, st);
     mixed_check_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(
         n, m, h->R, sd, ms.list, ms.count, ms.acc, ms.eta, ms.flags, h->hnorm2, it, max_refine, tol);
     count_launch();
     mixed_compact_kernel<<<1, 1024, 0, st>>>(s, ms.flags, ms.list, ms.count);
     count_launch();
     if (it == max_refine) break;
+    tr = trace_begin("mixed_correction", st);
     k1<<<grid, kThreads, L::bytes, st>>>(n, m, nb, h->Hhi, h->R, sd, ms.list, ms.count, ms.slots,
                                         slot_bytes, ms.X, ms.E, ms.flags, h->hnorm2);
     count_launch();
+    trace_end(tr, st);
   }
   mixed_output_kernel<<<std::min(s, num_sms() * 8), 256, 0, st>>>(
       n, m, p, s, mode, h->Ct, p > 0 ? p : 1, ms.X, ms.flags, ms.eta,
@@ -971,8 +977,11 @@ int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o,
   else rc = SSV_ENOTSUP;
   // shifts that did not converge: FP64 sweep (status and output overwritten);
   // their backward errors come from the FP64 solution
-  if (rc == SSV_OK && resid == nullptr)
+  if (rc == SSV_OK && resid == nullptr) {
+    void* tr = trace_begin("mixed_fallback", st);
     rc = solve_fp64_masked(h, s, shifts, mode, 0, out, ldo, status, fallback, nullptr, 0, st);
+    trace_end(tr, st);
+  }
   if (rc == SSV_OK && resid != nullptr) {
     cd* xcopy = nullptr;
     const bool gm = (mode == SSV_G || mode == SSV_TF);

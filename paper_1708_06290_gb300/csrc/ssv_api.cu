@@ -114,8 +114,10 @@ int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double
   Handle* h = nullptr;
   int rc = make_handle(n, m, p, st, &h);
   if (rc != SSV_OK) return rc;
+  void* tr = trace_begin("reduce", st);
   rc = reduce_fp64(h, A, lda, B, ldb, C, ldc, st);
   if (rc == SSV_OK) rc = split_h(h, st);
+  trace_end(tr, st);
   if (rc != SSV_OK) {
     cudaStreamSynchronize(st);
     free_handle_buffers(h);
@@ -165,8 +167,13 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
   if (!gmode && ldo < h->n) return SSV_EINVAL;
   if (o.mode == SSV_X && !h->has_q) return SSV_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
-  if (o.precision == SSV_MIXED) rc = solve_mixed(h, s, shifts, &o, out, ldo, status, resid, st);
-  else rc = solve_fp64(h, s, shifts, &o, out, ldo, status, resid, st);
+  if (o.precision == SSV_MIXED) {
+    rc = solve_mixed(h, s, shifts, &o, out, ldo, status, resid, st);
+  } else {
+    void* tr = trace_begin("solve_fp64", st);
+    rc = solve_fp64(h, s, shifts, &o, out, ldo, status, resid, st);
+    trace_end(tr, st);
+  }
   if (rc == SSV_OK && o.mode == SSV_X) rc = apply_q_fp64(h, s * h->m, out, ldo, out, ldo, st);
   return rc;
 }
@@ -212,7 +219,9 @@ int ssv_solve_many(int nsys, const ssv_handle* hs, const int* s, const double* c
   rc = batch_create(nsys, reinterpret_cast<const Handle* const*>(hs), s, shifts, &o, outs, ldos,
                     status, &bp, so);
   if (rc != SSV_OK) return rc;
+  void* tr = trace_begin("batch", st);
   rc = batch_run(bp, st);
+  trace_end(tr, st);
   if (so == nullptr) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess && rc == SSV_OK) { set_cuda_error(e); rc = SSV_ECUDA; }

@@ -128,6 +128,11 @@ int tuned_nb(int n, int m, int p, int prec, int mode);
 int autotune_nb(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                 long long ldo, cudaStream_t st, int* best_nb, float* best_ms);
 
+// Phase tracer (trace.cu): no-ops unless enabled with ssv_trace_enable.
+bool trace_on();
+void* trace_begin(const char* name, cudaStream_t st);
+void trace_end(void* tok, cudaStream_t st);
+
 // Kernel-launch counter (every launch site calls count_launch()).
 void count_launch(long long k = 1);
 // DFMA (kind 0) / FFMA (kind 1) throughput probe, TFLOP/s.

@@ -56,7 +56,8 @@ class Opts(ctypes.Structure):
 EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced",
            "ssv_dims", "ssv_footprint", "ssv_handle_bytes", "ssv_destroy", "ssv_strerror",
            "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc", "ssv_solve_many",
-           "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune")
+           "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
+           "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read")
 
 _lib = None
 
@@ -95,6 +96,12 @@ def load(build_if_missing=True):
     L.ssv_batch_destroy.restype = None
     L.ssv_autotune.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_float)]
+    L.ssv_trace_enable.argtypes = [I]
+    L.ssv_trace_reset.argtypes = []
+    L.ssv_trace_read.argtypes = [I, ctypes.c_char_p, I, ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(I), ctypes.POINTER(I)]
+    for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read"):
+        getattr(L, f).restype = I
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
     L.ssv_dims.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
@@ -397,3 +404,27 @@ def autotune(handle, shifts, mode="g", precision="fp64", stream=None):
                           ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), _ld(out, rows),
                           _stream_ptr(stream), ctypes.byref(nb), ctypes.byref(ms)), "ssv_autotune")
     return nb.value, ms.value
+
+
+def trace(on=True):
+    """Enable / disable the library's phase tracer (CUDA events per internal phase)."""
+    L = load()
+    if on:
+        L.ssv_trace_reset()
+    L.ssv_trace_enable(1 if on else 0)
+
+
+def trace_read():
+    """{phase: (total_ms, calls)} for the spans recorded since trace(True)."""
+    L = load()
+    mx, ln = 32, 48
+    names = ctypes.create_string_buffer(mx * ln)
+    tot = (ctypes.c_float * mx)()
+    calls = (ctypes.c_int * mx)()
+    cnt = ctypes.c_int()
+    _check(L.ssv_trace_read(mx, names, ln, tot, calls, ctypes.byref(cnt)), "ssv_trace_read")
+    out = {}
+    for k in range(min(cnt.value, mx)):
+        nm = names.raw[k * ln:(k + 1) * ln].split(b"\0", 1)[0].decode()
+        out[nm] = (tot[k], calls[k])
+    return out
