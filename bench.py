@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--serving-scale", type=float, default=1.0)
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
+    ap.add_argument("--profile-reduce", type=int, default=0,
+                    help="profiling case: one reduction of an n x n system (m = p = 8)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling case: one solve on a handle restored from an m-Hessenberg "
                          "stand-in (H = triu(A, -m), R = triu(B), Ct = C), no reduction")
@@ -263,10 +265,59 @@ def batching_measurement(ssv, dev, args):
             "shift_solves_per_s": total / (ms * 1e-3), "launches_per_batch": 1}
 
 
+def profile_solve(args):
+    """One solve of the workload's shifts on a restored stand-in handle: the solve
+    kernels run after only the handful of launches that restore the handle."""
+    import torch
+
+    from paper_1708_06290_gb300 import ssv
+
+    sysr, sig = W.workload_precision()
+    if args.shifts:
+        sig = sig[np.unique(np.linspace(0, len(sig) - 1, args.shifts).astype(int))]
+    m = sysr.m
+    Hs = np.triu(sysr.A, -m)
+    Rs = np.triu(sysr.B)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().cuda()  # noqa
+    h = ssv.load_reduced(dev(Hs), dev(Rs), dev(sysr.C))
+    sd = torch.from_numpy(sig.astype(np.complex128)).cuda()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out, st, _ = h.solve(sd, mode="g", precision=args.precision, nb=args.nb)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "solve", "precision": args.precision, "n": sysr.n, "m": m,
+                      "shifts": int(len(sig)), "ms": e0.elapsed_time(e1),
+                      "nonzero_status": int((st != 0).sum())}))
+    h.close()
+    return 0
+
+
+def profile_reduce(args):
+    """One controller-Hessenberg reduction (a single persistent kernel launch)."""
+    import torch
+
+    from paper_1708_06290_gb300 import ssv
+
+    n = args.profile_reduce
+    sysr = W.random_system(n, 8, 8, seed=77)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().cuda()  # noqa
+    A, B, C = dev(sysr.A), dev(sysr.B), dev(sysr.C)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = ssv.reduce(A, B, C)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "reduce", "n": n, "m": 8, "s": time.perf_counter() - t0}))
+    h.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_reduce:
+        return profile_reduce(args)
     if args.profile_solve:
         return profile_solve(args)
 

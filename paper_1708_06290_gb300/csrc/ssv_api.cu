@@ -360,6 +360,11 @@ int ssv_last_cuda_error(void) { return g_last_cuda; }
 
 long long ssv_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int ssv_selftest_barrier(long long spin_limit, void* stream) {
+  if (spin_limit < 1) return SSV_EINVAL;
+  return barrier_selftest(spin_limit, (cudaStream_t)stream);
+}
+
 int ssv_peak_probe(int kind, void* stream, double* tflops) {
   if (!tflops || (kind != 0 && kind != 1)) return SSV_EINVAL;
   return peak_probe(kind, (cudaStream_t)stream, tflops);

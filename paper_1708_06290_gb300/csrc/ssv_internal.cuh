@@ -72,6 +72,11 @@ void set_cuda_error(cudaError_t e);
     }                                              \
   } while (0)
 
+// the reduction proper: one persistent cooperative kernel (reduce_persistent.cu);
+// H, R, Ct hold copies of A, B, C on entry.  Synchronises `st`.
+int reduce_persistent(Handle* h, cudaStream_t st);
+// self-test of the bounded grid barrier (expects SSV_ETIMEOUT)
+int barrier_selftest(long long limit, cudaStream_t st);
 // reduction (reduce_fp64.cu)
 int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long long ldb,
                 const double* C, long long ldc, cudaStream_t st);

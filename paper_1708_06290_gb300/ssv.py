@@ -57,7 +57,7 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_dims", "ssv_footprint", "ssv_handle_bytes", "ssv_destroy", "ssv_strerror",
            "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc", "ssv_solve_many",
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
-           "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read")
+           "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier")
 
 _lib = None
 
@@ -96,11 +96,13 @@ def load(build_if_missing=True):
     L.ssv_batch_destroy.restype = None
     L.ssv_autotune.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_float)]
+    L.ssv_selftest_barrier.argtypes = [LL, P]
+    L.ssv_selftest_barrier.restype = I
     L.ssv_trace_enable.argtypes = [I]
     L.ssv_trace_reset.argtypes = []
     L.ssv_trace_read.argtypes = [I, ctypes.c_char_p, I, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(I), ctypes.POINTER(I)]
-    for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read"):
+    for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier"):
         getattr(L, f).restype = I
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
@@ -428,3 +430,9 @@ def trace_read():
         nm = names.raw[k * ln:(k + 1) * ln].split(b"\0", 1)[0].decode()
         out[nm] = (tot[k], calls[k])
     return out
+
+
+def selftest_barrier(spin_limit=100000, stream=None):
+    """Run the bounded-barrier timeout self-test; returns the library's return code
+    (SSV_ETIMEOUT when the timeout path works)."""
+    return load().ssv_selftest_barrier(int(spin_limit), _stream_ptr(stream))

@@ -245,3 +245,14 @@ def test_mixed_precision_workload_sampled():
             assert relerr(G[j], Go[k]) < REL_TOL, (j, cond[k])
             checked += 1
     assert checked >= 8
+
+
+def test_bounded_barrier_times_out_and_device_stays_usable():
+    """A grid barrier that one block never reaches gives up after its spin limit:
+    the library returns SSV_ETIMEOUT and later work on the device still runs."""
+    assert ssv.selftest_barrier(100000) == ssv.SSV_ETIMEOUT
+    sysr = W.random_system(60, 2, 2, seed=3)
+    h = gpu_system(sysr)
+    out, st, _ = h.solve(shifts_dev([0.5j]), mode="g")
+    X, _ = oracle.dense_solve(sysr.A, sysr.B, [0.5j])
+    assert relerr(blocks(out, 2)[0], oracle.transfer(sysr.C, X)[0]) < REL_TOL
