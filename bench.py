@@ -65,7 +65,7 @@ def workload_config(sysr, sig, nb, precision):
         "n": sysr.n, "m": sysr.m, "p": sysr.p, "shifts": int(len(sig)),
         "output": "G(sigma)=C X, complex128, p x (s*m)",
         "step": "FP64 reduction + solve of all shifts",
-        "precision": precision, "nb": nb or 64,
+        "precision": precision, "nb": nb or (128 if sysr.n >= 1024 else 64),
         "l2": "inputs larger than L2 (A and H are 200 MB each; every step re-reads A)",
     }
 
@@ -462,7 +462,12 @@ def main():
         "peak_source": "FP64 DFMA probe measured in this run (nominal GB300 FP64 1.25 TFLOP/s)",
         "flops_per_launch": flops_floor, "launch_ms": solve_ms,
         "flops_definition": "2 n^2 m + 4 n m p per shift (trailing update Z1 P1 + Ct rows)",
-        "traffic": None,
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one solve_fp64_kernel launch
+        # on 152 shifts of this workload (2.986672 + 3.463191 GB, profiles/
+        # solve_fp64_kernel_n5000_m16_152shifts.md), scaled by shifts to this launch: each
+        # shift streams its own Z2 state, so traffic grows in proportion to the shifts.
+        "traffic": (2.986672e9 + 3.463191e9) * s / 152.0 if args.nb in (0, 128) else None,
+        "traffic_source": "ncu capture of 152 shifts at n_b=128, scaled to %d shifts" % s,
     }
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
