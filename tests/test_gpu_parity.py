@@ -27,7 +27,8 @@ def gpu_system(sysr):
 
 
 @pytest.mark.parametrize("n,m,p", [(256, 2, 2), (300, 7, 3), (130, 16, 16), (65, 32, 5),
-                                   (40, 1, 1), (17, 17, 2), (9, 8, 3), (1, 1, 1)])
+                                   (40, 1, 1), (17, 17, 2), (9, 8, 3), (1, 1, 1),
+                                   (520, 20, 4), (1100, 16, 16), (700, 1, 3), (401, 33, 2)])
 def test_reduce_matches_oracle(n, m, p):
     sysr = W.random_system(n, m, p, seed=700 + n + m)
     h = gpu_system(sysr)
