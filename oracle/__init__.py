@@ -9,6 +9,8 @@ All arithmetic is IEEE double (complex128), done in ``csrc/ssv_oracle.c``:
 
 * :func:`dense_solve` -- X = (A - sigma I)^{-1} B by LU with partial pivoting
   on the full matrix (the plain definition of the shifted solve, Sec. 1).
+* :func:`dense_solve_vec` -- one right-hand side per shift, x = (A - sigma I)^{-1} b
+  or x = (A - sigma I)^{-T} c (Sec. 3.5), same LU.
 * :func:`reduce` -- controller-Hessenberg form (H, R, Ct[, Q]) of (A, B, C) by
   unblocked Householder reflectors in the order of Algorithm 1 (Sec. 2).
 * :func:`reduced_solve` -- Xhat = (H - sigma I)^{-1} R (or G = Ct Xhat) by
@@ -38,9 +40,10 @@ def load_library(path):
     P = ctypes.c_void_p
     I = ctypes.c_int
     lib.ora_dense_solve.argtypes = [I, I, P, I, P, I, I, P, P, P]
+    lib.ora_dense_solve_vec.argtypes = [I, P, I, I, P, I, P, I, P, P]
     lib.ora_reduce.argtypes = [I, I, I, P, I, P, I, P, I, P, P, P, P]
     lib.ora_reduced_solve.argtypes = [I, I, I, P, I, P, I, P, I, I, P, I, P, P, P]
-    for f in (lib.ora_dense_solve, lib.ora_reduce, lib.ora_reduced_solve):
+    for f in (lib.ora_dense_solve, lib.ora_dense_solve_vec, lib.ora_reduce, lib.ora_reduced_solve):
         f.restype = I
     return lib
 
@@ -79,6 +82,25 @@ def dense_solve(A, B, sigmas):
     if rc != 0:
         raise MemoryError("oracle dense_solve failed")
     return np.transpose(X, (0, 2, 1)).copy(), st
+
+
+def dense_solve_vec(A, rhs, sigmas, trans=False):
+    """Return (X, status) with X[j] = (A - sigmas[j] I)^{-1} rhs[j] (trans=False) or
+    (A - sigmas[j] I)^{-T} rhs[j] (trans=True, plain transpose); rhs and X (s, n)
+    complex128.  status[j] = 1 where LU met an exactly zero pivot (X[j] NaN)."""
+    lib = _load()
+    A = _f64(A)
+    n = A.shape[0]
+    sig = np.ascontiguousarray(np.asarray(sigmas, dtype=np.complex128).reshape(-1))
+    ns = sig.size
+    R = np.ascontiguousarray(np.asarray(rhs, dtype=np.complex128).reshape(ns, n))
+    X = np.zeros((ns, n), dtype=np.complex128)
+    st = np.zeros(ns, dtype=np.int32)
+    rc = lib.ora_dense_solve_vec(n, _ptr(A), n, ns, _ptr(sig), 1 if trans else 0, _ptr(R), n,
+                                 _ptr(X), _ptr(st))
+    if rc != 0:
+        raise MemoryError("oracle dense_solve_vec failed")
+    return X, st
 
 
 def reduce(A, B, C, want_q=False):

@@ -15,6 +15,11 @@
  *   ora_dense_solve   : X = (A - sigma I)^{-1} B by LU with partial pivoting on
  *                       the full matrix A - sigma I (the plain definition of the
  *                       solve of Sec. 1, eq. for (A - sigma I)X = B).
+ *   ora_dense_solve_vec: one right-hand side per shift, x = (A - sigma I)^{-1} b
+ *                       or, transposed, x = (A - sigma I)^{-T} c (plain
+ *                       transpose, not conjugate): the systems with different
+ *                       right-hand sides for different shifts of Sec. 3.5,
+ *                       b = B bhat, c = C^T chat.  Same LU as ora_dense_solve.
  *   ora_reduce        : controller-Hessenberg form of (A, B, C) by unblocked
  *                       Householder reflectors, following Algorithm 1 (Sec. 2):
  *                       QR of B, similarity with Q_B, m-Hessenberg reduction,
@@ -115,6 +120,35 @@ int ora_dense_solve(int n, int m, const double* A, int lda, const double* B, int
       continue;
     }
     zgetrs_plain(n, M, piv, m, Xs);
+    status[s] = ORA_OK;
+  }
+  free(M);
+  free(piv);
+  return 0;
+}
+
+/* One complex right-hand side per shift: column s of rhs (ld ldr) solved with
+ * M = A - sigma_s I (trans = 0) or M = (A - sigma_s I)^T (trans = 1) into
+ * column s of X (ld n).  status[s] = ORA_SINGULAR on an exactly zero pivot. */
+int ora_dense_solve_vec(int n, const double* A, int lda, int ns, const zc* sigma, int trans,
+                        const zc* rhs, int ldr, zc* X, int* status) {
+  zc* M = (zc*)malloc(sizeof(zc) * (size_t)n * n);
+  int* piv = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!M || !piv) { free(M); free(piv); return -1; }
+  for (int s = 0; s < ns; ++s) {
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i)
+        M[i + (size_t)j * n] = trans ? A[j + (size_t)i * lda] : A[i + (size_t)j * lda];
+    for (int i = 0; i < n; ++i) M[i + (size_t)i * n] -= sigma[s];
+    zc* xs = X + (size_t)s * n;
+    for (int i = 0; i < n; ++i) xs[i] = rhs[i + (size_t)s * ldr];
+    int info = zgetrf_plain(n, M, piv);
+    if (info) {
+      status[s] = ORA_SINGULAR;
+      for (int i = 0; i < n; ++i) xs[i] = NAN;
+      continue;
+    }
+    zgetrs_plain(n, M, piv, 1, xs);
     status[s] = ORA_OK;
   }
   free(M);

@@ -28,6 +28,10 @@ MUTANTS = {
                            "for (int i = 0; i < n; ++i) U[(size_t)i * n + i] += sigma[s];"),
     "reduced_band_short": ("      int last = k + m < n - 1 ? k + m : n - 1;\n      int pr = k;",
                            "      int last = k + m - 1 < n - 1 ? k + m - 1 : n - 1;\n      int pr = k;"),
+    "vec_transpose_ignored": ("M[i + (size_t)j * n] = trans ? A[j + (size_t)i * lda] : A[i + (size_t)j * lda];",
+                              "M[i + (size_t)j * n] = A[i + (size_t)j * lda];"),
+    "vec_rhs_column": ("for (int i = 0; i < n; ++i) xs[i] = rhs[i + (size_t)s * ldr];",
+                       "for (int i = 0; i < n; ++i) xs[i] = rhs[i];"),
     "transfer_index": ("acc += Ct[i + (size_t)k * ldc] * X[k + (size_t)j * n];",
                        "acc += Ct[k + (size_t)i * ldc] * X[k + (size_t)j * n];"),
 }
@@ -77,6 +81,18 @@ def _checks(lib):
         Gd = oracle.transfer(sysr.C, Xd)
         if not all(np.linalg.norm(G[k] - Gd[k]) <= 1e-11 * np.linalg.norm(Gd[k]) for k in range(2)):
             fails.append("coordinate invariance")
+        # per-shift right-hand sides, both sides, exact rational
+        from fractions import Fraction as Fr
+        An, Bn, sig, den = W.small_rational_system(5, 2, 8)
+        rre, rim = Bn @ np.array([2, -1]), Bn @ np.array([1, 3])
+        for trans in (False, True):
+            xe = exact.solve(exact.shifted(An.T if trans else An, den, sig),
+                             [[(Fr(int(rre[i]), den), Fr(int(rim[i]), den))] for i in range(5)])
+            xe = np.array([exact.to_complex(row[0]) for row in xe])
+            rhs = np.stack([(rre + 1j * rim) / den, np.zeros(5)])
+            Xv, _ = oracle.dense_solve_vec(An / den, rhs, [complex(*sig) / den, 0.5j], trans=trans)
+            if not np.linalg.norm(Xv[0] - xe) <= 1e-12 * np.linalg.norm(xe) or np.abs(Xv[1]).max() != 0:
+                fails.append("vec exact trans=%d" % trans)
     except Exception as e:  # a mutant may also crash a check
         fails.append("exception: %r" % (e,))
     finally:

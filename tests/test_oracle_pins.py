@@ -233,3 +233,90 @@ def test_hager_condition_estimate_is_tight_lower_bound(ora):
         k1 = np.linalg.norm(M, 1) * np.linalg.norm(np.linalg.inv(M), 1)
         assert c1[j] <= k1 * (1 + 1e-10)
         assert c1[j] >= k1 / 10
+
+
+# --------------------------------------------------------------------------
+# dense_solve_vec: a different right-hand side for every shift (Sec. 3.5),
+# x = (A - sigma I)^{-1} b and the transposed x = (A - sigma I)^{-T} c
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("n,seed", [(1, 21), (4, 22), (7, 23)])
+def test_dense_solve_vec_matches_exact_rational(ora, n, trans, seed):
+    from fractions import Fraction as Fr
+    An, Bn, sig, den = W.small_rational_system(n, 2, seed)
+    rng = np.random.default_rng(seed + 100)
+    wr, wi = rng.integers(-5, 6, 2), rng.integers(-5, 6, 2)
+    # rhs = B (wr + i wi) / den, exactly representable
+    rre = Bn @ wr
+    rim = Bn @ wi
+    rhs = (rre + 1j * rim) / den
+    M = exact.shifted(An.T if trans else An, den, sig)
+    b = [[(Fr(int(rre[i]), den), Fr(int(rim[i]), den))] for i in range(n)]
+    xe = exact.solve(M, b)
+    assert xe is not None
+    xe = np.array([exact.to_complex(row[0]) for row in xe])
+    X, st = ora.dense_solve_vec(An / den, rhs[None, :], [complex(sig[0], sig[1]) / den], trans=trans)
+    assert st[0] == 0
+    assert relerr(X[0], xe) < 1e-12
+
+
+@pytest.mark.parametrize("trans", [False, True])
+def test_dense_solve_vec_diagonal_closed_form(ora, trans):
+    a, sysd = W.diagonal_system(20, 1, 1, seed=24)
+    sig = W.imag_axis_logspace(-1, 1, 5)
+    rng = np.random.default_rng(25)
+    rhs = rng.standard_normal((5, 20)) + 1j * rng.standard_normal((5, 20))
+    X, st = ora.dense_solve_vec(sysd.A, rhs, sig, trans=trans)
+    assert (st == 0).all()
+    for j, s in enumerate(sig):
+        assert relerr(X[j], rhs[j] / (a - s)) < 1e-14
+
+
+def test_dense_solve_vec_transposed_block_diagonal_closed_form(ora):
+    """c-side of the transfer function: x = (A - sigma I)^{-T} C^T chat gives
+    x^T B = chat^T C (A - sigma I)^{-1} B = -chat^T G(sigma), with G(s) = C (sI - A)^{-1} B
+    in closed form for 2 x 2 blocks [[alpha, beta], [-beta, alpha]]."""
+    alpha, beta, sysb = W.block_diagonal_system(6, 2, 3, seed=26)
+    sig = np.array([0.4j, -1.1 + 0.7j, 2.5j])
+    chat = np.array([1.0 - 0.5j, 0.25j, -2.0])
+    rhs = np.tile(sysb.C.T @ chat, (len(sig), 1))
+    X, st = ora.dense_solve_vec(sysb.A, rhs, sig, trans=True)
+    assert (st == 0).all()
+    for j, s in enumerate(sig):
+        G = np.zeros((3, 2), dtype=complex)
+        for k in range(len(alpha)):
+            Ak = np.array([[alpha[k], beta[k]], [-beta[k], alpha[k]]])
+            # (sI - Ak)^{-1} = [[s - a, b], [-b, s - a]] / ((s - a)^2 + b^2)
+            d = (s - alpha[k]) ** 2 + beta[k] ** 2
+            inv = np.array([[s - alpha[k], beta[k]], [-beta[k], s - alpha[k]]]) / d
+            sl = slice(2 * k, 2 * k + 2)
+            G += sysb.C[:, sl] @ inv @ sysb.B[sl, :]
+            assert np.allclose(inv @ (s * np.eye(2) - Ak), np.eye(2))
+        assert relerr(X[j] @ sysb.B, -(chat @ G)) < 1e-13
+
+
+def test_dense_solve_vec_duality_of_the_two_sides(ora):
+    """For nonsymmetric A: chat^T C x_b = x_c^T B bhat with x_b = (A - sigma I)^{-1} B bhat
+    and x_c = (A - sigma I)^{-T} C^T chat (both are chat^T C (A - sigma I)^{-1} B bhat)."""
+    sysr = W.random_system(40, 3, 2, seed=27)
+    sig = np.array([0.3j, -2.2 + 0.4j])
+    rng = np.random.default_rng(28)
+    bhat = rng.standard_normal((2, 3)) + 1j * rng.standard_normal((2, 3))
+    chat = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    xb, _ = ora.dense_solve_vec(sysr.A, bhat @ sysr.B.T, sig)
+    xc, _ = ora.dense_solve_vec(sysr.A, chat @ sysr.C, sig, trans=True)
+    for j in range(2):
+        lhs = chat[j] @ (sysr.C @ xb[j])
+        rhs = xc[j] @ (sysr.B @ bhat[j])
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # and the two sides differ (A is not symmetric): the transpose matters
+    xwrong, _ = ora.dense_solve_vec(sysr.A, chat @ sysr.C, sig, trans=False)
+    assert abs(xwrong[0] @ (sysr.B @ bhat[0]) - chat[0] @ (sysr.C @ xb[0])) > 1e-6
+
+
+def test_dense_solve_vec_exact_singular_shift(ora):
+    a, sysd = W.diagonal_system(6, 1, 1, seed=29)
+    X, st = ora.dense_solve_vec(sysd.A, np.ones((2, 6), dtype=complex), [a[2] + 0j, 0.5j], trans=True)
+    assert st[0] == ora.STATUS_SINGULAR and np.isnan(X[0]).all()
+    assert st[1] == ora.STATUS_OK
