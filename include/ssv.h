@@ -112,6 +112,25 @@ int ssv_solve(ssv_handle h, int s, const double* shifts, const ssv_opts* o, doub
               long long ldo, int* status, double* resid, void* stream);
 
 /*
+ * ssv_solve_rhs -- one right-hand side per shift (Sec. 3.3, the systems
+ * (A - sigma_l I) x_l = B bhat_l that interpolatory model reduction needs):
+ * the same sweep as ssv_solve, whose final m x m step solves for the single
+ * column R(1:m, 1:m) bhat_l (the reduced right-hand side has at most m
+ * nonzero entries) instead of the m columns of R.
+ *   bhat (device): complex m x s, column l = bhat_l, ld ldb >= m.
+ *   o: precision SSV_FP64 only (SSV_MIXED -> SSV_ENOTSUP); mode
+ *     SSV_X     out column l = x_l = (A - sigma_l I)^{-1} B bhat_l (n rows),
+ *     SSV_XHAT  out column l = Q^T x_l (reduced coordinates, n rows),
+ *     SSV_G     out column l = C x_l = G(sigma_l) bhat_l (p rows),
+ *     SSV_TF    out column l = -C x_l = C (sigma_l I - A)^{-1} B bhat_l.
+ *   out (device): complex, (n or p) x s, ld ldo >= n (or max(1, p)).
+ *   status (device, may be NULL): s ints, SSV_SHIFT_*.
+ * Errors: SSV_EINVAL, SSV_ENOTSUP, SSV_ENOMEM, SSV_ECUDA.
+ */
+int ssv_solve_rhs(ssv_handle h, int s, const double* shifts, const double* bhat, long long ldb,
+                  const ssv_opts* o, double* out, long long ldo, int* status, void* stream);
+
+/*
  * ssv_solve_many -- many reduced systems of uneven n, m and shift counts in
  * one persistent launch (FP64: one kernel over a cost-ordered worklist of
  * (system, shift) items, Sec. 3 applied to several systems at once; MIXED:

@@ -10,7 +10,7 @@ All arithmetic is IEEE double (complex128), done in ``csrc/ssv_oracle.c``:
 * :func:`dense_solve` -- X = (A - sigma I)^{-1} B by LU with partial pivoting
   on the full matrix (the plain definition of the shifted solve, Sec. 1).
 * :func:`dense_solve_vec` -- one right-hand side per shift, x = (A - sigma I)^{-1} b
-  or x = (A - sigma I)^{-T} c (Sec. 3.5), same LU.
+  or x = (A - sigma I)^{-T} c (Sec. 3.3), same LU.
 * :func:`reduce` -- controller-Hessenberg form (H, R, Ct[, Q]) of (A, B, C) by
   unblocked Householder reflectors in the order of Algorithm 1 (Sec. 2).
 * :func:`reduced_solve` -- Xhat = (H - sigma I)^{-1} R (or G = Ct Xhat) by

@@ -18,7 +18,7 @@
  *   ora_dense_solve_vec: one right-hand side per shift, x = (A - sigma I)^{-1} b
  *                       or, transposed, x = (A - sigma I)^{-T} c (plain
  *                       transpose, not conjugate): the systems with different
- *                       right-hand sides for different shifts of Sec. 3.5,
+ *                       right-hand sides for different shifts of Sec. 3.3,
  *                       b = B bhat, c = C^T chat.  Same LU as ora_dense_solve.
  *   ora_reduce        : controller-Hessenberg form of (A, B, C) by unblocked
  *                       Householder reflectors, following Algorithm 1 (Sec. 2):

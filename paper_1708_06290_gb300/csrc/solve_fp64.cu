@@ -6,25 +6,30 @@
 // is combined with n_b fresh columns Z1 of the original [Ct; H] (shared by all
 // shifts) on each block of n_b rows:
 //   1. the n_b x (n_b + m) window block is triangularised from its bottom row
-//      up; in each row the pivot is the candidate column (m live + 1 fresh)
-//      of largest |re| + |im|, and the other m candidates are reduced by a
-//      multiple of it (Gauss transformations from the right).  Only the
-//      coefficients P (n_b + m) x m expressing the m surviving columns in terms
-//      of [Z1 | Z2] are kept (Sec. 3.1: "only the first m columns of P* are
-//      needed");
+//      up.  Row c has m + 1 candidate entries (m live columns and the fresh
+//      column that enters at this row); one complex Householder reflector
+//      acting on those m + 1 columns from the right maps the row onto the
+//      fresh column's slot (an RQ step, as in Sec. 3.1).  The reflector is
+//      applied to the rows of the block above c and accumulated into the
+//      coefficients P ((n_b + m) x m) that express the m surviving columns in
+//      terms of [Z1 | Z2]; the rest of the block transform is never formed,
+//      the economy of Sec. 3.1;
 //   2. the rows above the block are updated once:
 //      Z2 <- Z1 P(1:n_b, :) + Z2 P(n_b+1:, :) - sigma E P(1:min(m,n_b), :),
 //      the last term being the shifted diagonal of the fresh columns that
 //      lies above the block (Algorithm 8, diagonal correction);
 //   3. the window slides up by n_b rows.
 // When m rows remain, the live block W = [Wc; Wm] (p + m rows) gives
-// Y = Wm^{-1} R(1:m, 1:m) and G = Wc Y (Algorithm 8, final loop; here on the
-// GPU).  For Xhat the window also carries the rows of the accumulated column
-// transformation T (the "Q*" rows of Sec. 3.4), Xhat = T(:, live) Y.
+// Y = Wm^{-1} R(1:m, 1:m) (Gauss-Jordan with partial pivoting) and G = Wc Y
+// (Algorithm 8, final loop; here on the GPU).  For Xhat the window also
+// carries the rows of the accumulated column transformation T (the "Q*" rows
+// of Sec. 3.3), Xhat = T(:, live) Y.  With one right-hand side R bhat_l per
+// shift (Sec. 3.3) Y is the m-vector Wm^{-1} R(1:m, 1:m) bhat_l.
 //
-// Differences from the paper: Gauss transformations with pivoting instead of
-// Givens rotations; each thread block owns one shift at a time for the whole
-// sweep (no grid-wide phases); the final m x m solve runs on the GPU.
+// Differences from the paper: one Householder reflector per row instead of
+// the Givens schedule (unitary either way, so the one-shot update of the rows
+// above stays stable); each thread block owns one shift at a time for the
+// whole sweep (no grid-wide phases); the final m x m solve runs on the GPU.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -70,6 +75,8 @@ struct FpSys {
   cd* xhat_copy;
   long long ldxc;
   const double* hnorm;
+  const cd* bhat;    // per-shift right-hand side coefficients (m x s, ld ldb), or null
+  long long ldb;
 };
 
 // Solve shift sh of system d with the window state in Z2 (and ZT).
@@ -296,13 +303,23 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   }
 
   // ---- final m x m block: solve Wm Y = R(0:m, 0:m) by Gauss-Jordan with
-  // partial pivoting on the augmented [Wm | R1] (2m columns).
-  const int w2 = 2 * m;
+  // partial pivoting on the augmented [Wm | R1] (2m columns).  With a
+  // right-hand side per shift (Sec. 3.3) the augmented part is the single
+  // column R1 bhat, and Y is m x 1.
+  const cd* __restrict__ bh = d.bhat != nullptr ? d.bhat + (size_t)sh * d.ldb : nullptr;
+  const int nr = bh != nullptr ? 1 : m;
+  const int w2 = m + nr;
   for (int idx = tid; idx < m * w2; idx += kThreads) {
     int i = idx % m, j = idx / m;
     cd v;
     if (j < m) v = Z2[(p + i) + (size_t)j * ldz];
-    else {
+    else if (bh != nullptr) {
+      v = mkcd(0.0, 0.0);
+      for (int t = i; t < m; ++t) {
+        const double rv = R[i + (size_t)t * n];
+        v = mkcd(fma(rv, bh[t].x, v.x), fma(rv, bh[t].y, v.y));
+      }
+    } else {
       int jj = j - m;
       v = mkcd(i <= jj ? R[i + (size_t)jj * n] : 0.0, 0.0);
     }
@@ -349,7 +366,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     __syncthreads();
   }
   // Y(i, q) = Wm(i, m+q) / Wm(i, i)
-  for (int idx = tid; idx < m * m; idx += kThreads) {
+  for (int idx = tid; idx < m * nr; idx += kThreads) {
     int i = idx % m, q = idx / m;
     cd d = Wm[i + i * MAXM];
     Yb[i + q * MAXM] = (d.x == 0.0 && d.y == 0.0) ? mkcd(0.0, 0.0) : cdiv(Wm[i + (m + q) * MAXM], d);
@@ -360,8 +377,8 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   // ---- outputs
   if (mode == SSV_G || mode == SSV_TF) {
     const double sg = mode == SSV_TF ? -1.0 : 1.0;
-    cd* o = out + (size_t)sh * m * ldo;
-    for (int idx = tid; idx < p * m; idx += kThreads) {
+    cd* o = out + (size_t)sh * nr * ldo;
+    for (int idx = tid; idx < p * nr; idx += kThreads) {
       int i = idx % p, q = idx / p;
       cd acc = mkcd(0.0, 0.0);
       for (int t = 0; t < m; ++t) acc = cfma(Z2[i + (size_t)t * ldz], Yb[t + q * MAXM], acc);
@@ -373,13 +390,13 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     cd* o;
     long long ld;
     if (mode == SSV_XHAT || mode == SSV_X) {
-      o = out + (size_t)sh * m * ldo;
+      o = out + (size_t)sh * nr * ldo;
       ld = ldo;
     } else {
-      o = xhat_copy + (size_t)sh * m * ldxc;
+      o = xhat_copy + (size_t)sh * nr * ldxc;
       ld = ldxc;
     }
-    for (int idx = tid; idx < n * m; idx += kThreads) {
+    for (int idx = tid; idx < n * nr; idx += kThreads) {
       int i = idx % n, q = idx / n;
       cd acc = mkcd(0.0, 0.0);
       for (int t = 0; t < m; ++t) acc = cfma(ZT[i + (size_t)t * n], Yb[t + q * MAXM], acc);
@@ -398,14 +415,14 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
     cd* __restrict__ scratch, size_t slot_stride, cd* __restrict__ out, long long ldo,
     int* __restrict__ status, cd* __restrict__ xhat_copy, long long ldxc,
     const double* __restrict__ hnorm, const int* __restrict__ list,
-    const int* __restrict__ count) {
+    const int* __restrict__ count, const cd* __restrict__ bhat, long long ldb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_piv;
   __shared__ int s_sing;
   FpSys d;
   d.n = n; d.m = m; d.p = p; d.nb = nb; d.mode = mode; d.H = H; d.Ct = Ct; d.ldct = ldct;
   d.R = R; d.shifts = shifts; d.out = out; d.ldo = ldo; d.status = status;
-  d.xhat_copy = xhat_copy; d.ldxc = ldxc; d.hnorm = hnorm;
+  d.xhat_copy = xhat_copy; d.ldxc = ldxc; d.hnorm = hnorm; d.bhat = bhat; d.ldb = ldb;
   cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
   // With a work list, the block takes list entries blockIdx.x, +gridDim.x, ...
   const int nwork = list != nullptr ? *count : s;
@@ -453,7 +470,8 @@ __global__ void nonfinite_kernel(const cd* __restrict__ out, long long ldo, int 
 template <int MAXM>
 int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode, double* out,
                  long long ldo, int* status, cd* xhat_copy, long long ldxc, cudaStream_t st,
-                 const int* list = nullptr, const int* count = nullptr) {
+                 const int* list = nullptr, const int* count = nullptr,
+                 const cd* bhat = nullptr, long long ldb = 0) {
   using L = Layout<MAXM>;
   const int n = h->n, m = h->m, p = h->p;
   const bool track_t = (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
@@ -471,7 +489,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
   kern<<<grid, kThreads, L::bytes, st>>>(n, m, p, nb, h->H, h->Ct, p > 0 ? p : 1, h->R, s,
                                          reinterpret_cast<const cd*>(shifts), mode, scratch, slot,
                                          reinterpret_cast<cd*>(out), ldo, status, xhat_copy, ldxc,
-                                         h->hnorm2, list, count);
+                                         h->hnorm2, list, count, bhat, ldb);
   count_launch();
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaFreeAsync(scratch, st);
@@ -483,7 +501,8 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
   if (status != nullptr && list == nullptr) {
     int rows = (mode == SSV_G || mode == SSV_TF) ? p : n;
     if (rows > 0) {
-      nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows, m, s, status);
+      nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows,
+                                          bhat != nullptr ? 1 : m, s, status);
       count_launch();
       SSV_CUDA_TRY(cudaGetLastError());
     }
@@ -596,6 +615,26 @@ int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, 
   return rc;
 }
 
+// One right-hand side B bhat_l per shift (Sec. 3.3): out column l holds
+// Xhat_l bhat_l (SSV_XHAT / SSV_X before the back-transform) or
+// +-Ct Xhat_l bhat_l (SSV_G / SSV_TF).
+int solve_fp64_rhs(const Handle* h, int s, const double* shifts, const double* bhat,
+                   long long ldb, const ssv_opts* o, double* out, long long ldo, int* status,
+                   cudaStream_t st) {
+  const int m = h->m;
+  const int nb = o->nb > 0 ? o->nb : tuned_nb(h->n, m, h->p, SSV_FP64, o->mode);
+  if (nb > kNB) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  const int mode = o->mode == SSV_X ? SSV_XHAT : o->mode;
+  const cd* b = reinterpret_cast<const cd*>(bhat);
+  if (m <= 1) return launch_solve<1>(h, s, shifts, nb, mode, out, ldo, status, nullptr, 0, st, nullptr, nullptr, b, ldb);
+  if (m <= 2) return launch_solve<2>(h, s, shifts, nb, mode, out, ldo, status, nullptr, 0, st, nullptr, nullptr, b, ldb);
+  if (m <= 4) return launch_solve<4>(h, s, shifts, nb, mode, out, ldo, status, nullptr, 0, st, nullptr, nullptr, b, ldb);
+  if (m <= 8) return launch_solve<8>(h, s, shifts, nb, mode, out, ldo, status, nullptr, 0, st, nullptr, nullptr, b, ldb);
+  if (m <= 16) return launch_solve<16>(h, s, shifts, nb, mode, out, ldo, status, nullptr, 0, st, nullptr, nullptr, b, ldb);
+  if (m <= 32) return launch_solve<32>(h, s, shifts, nb, mode, out, ldo, status, nullptr, 0, st, nullptr, nullptr, b, ldb);
+  return SSV_ENOTSUP;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the FP64 solve (ssv_solve_noalloc).
@@ -661,13 +700,14 @@ int launch_solve_noalloc(const Handle* h, int s, const double* shifts, int nb, i
                                          reinterpret_cast<const cd*>(shifts), mode,
                                          reinterpret_cast<cd*>(base), slot,
                                          reinterpret_cast<cd*>(out), ldo, status, nullptr, 0,
-                                         h->hnorm2, nullptr, nullptr);
+                                         h->hnorm2, nullptr, nullptr, nullptr, 0);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   if (status != nullptr) {
     const int rows = (mode == SSV_G || mode == SSV_TF) ? p : n;
     if (rows > 0) {
-      nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows, m, s, status);
+      nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows,
+                                          m, s, status);
       count_launch();
       SSV_CUDA_TRY(cudaGetLastError());
     }
@@ -766,7 +806,7 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
     d.shifts = reinterpret_cast<const cd*>(shifts[k]);
     d.out = reinterpret_cast<cd*>(outs[k]); d.ldo = ldos[k];
     d.status = status ? status[k] : nullptr;
-    d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2;
+    d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2; d.bhat = nullptr; d.ldb = 0;
     bp->maxm = std::max(bp->maxm, h->m);
     bp->slot = std::max(bp->slot, (size_t)(h->p + h->n) * h->m + (track_t ? (size_t)h->n * h->m : 0));
     const double cost = (double)h->n * h->n * h->m * (1.0 + 2.0 * h->m / d.nb);

@@ -5,7 +5,7 @@
 //   1. sweep 0: the blocked bottom-up window elimination of Sec. 3.1 /
 //      Algorithm 8 in complex64 (one Householder reflector per row over the m
 //      live + 1 fresh candidate columns), carrying the rows of the accumulated
-//      column transformation T (the "Q*" rows of Sec. 3.4), so that
+//      column transformation T (the "Q*" rows of Sec. 3.3), so that
 //      Xhat0 = T(:, live) Wm^{-1} R(1:m, 1:m) is formed (stored in complex128);
 //   2. refinement: E = R - (H - sigma I) Xhat with H = Hhi + Hlo (two FP32
 //      words) and Xhat split the same way, each product formed exactly by an
@@ -14,7 +14,7 @@
 //      this GPU); the normwise backward error decides convergence;
 //   3. a correction sweep solves (H - sigma I) D = E for the dense right-hand
 //      side E by carrying E as extra window columns that are back-substituted
-//      on the fly with each finalised column (the technique of Sec. 3.4 for
+//      on the fly with each finalised column (the technique of Sec. 3.3 for
 //      unreduced right-hand sides, here in the bottom-up RQ direction), and
 //      Xhat += D.
 // Shifts that do not reach the tolerance are flagged; the host re-solves them

@@ -178,6 +178,29 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
   return rc;
 }
 
+int ssv_solve_rhs(ssv_handle hh, int s, const double* shifts, const double* bhat, long long ldb,
+                  const ssv_opts* o_in, double* out, long long ldo, int* status, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || s < 0) return SSV_EINVAL;
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc != SSV_OK) return rc;
+  if (o.precision != SSV_FP64) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  if (!shifts || !out || !bhat || ldb < h->m) return SSV_EINVAL;
+  const bool gmode = (o.mode == SSV_G || o.mode == SSV_TF);
+  if (gmode && ldo < (h->p > 0 ? h->p : 1)) return SSV_EINVAL;
+  if (!gmode && ldo < h->n) return SSV_EINVAL;
+  if (o.mode == SSV_X && !h->has_q) return SSV_ENOTSUP;
+  cudaStream_t st = (cudaStream_t)stream;
+  void* tr = trace_begin("solve_rhs", st);
+  rc = solve_fp64_rhs(h, s, shifts, bhat, ldb, &o, out, ldo, status, st);
+  trace_end(tr, st);
+  if (rc == SSV_OK && o.mode == SSV_X) rc = apply_q_fp64(h, s, out, ldo, out, ldo, st);
+  return rc;
+}
+
 static int check_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
                       const ssv_opts& o, double* const* outs, const long long* ldos) {
   if (nsys < 0 || (nsys > 0 && (!hs || !s || !shifts || !outs || !ldos))) return SSV_EINVAL;

@@ -93,6 +93,11 @@ int get_reduced(const Handle* h, double* H, long long ldh, double* R, long long 
 // solver (solve_fp64.cu)
 int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                long long ldo, int* status, double* resid, cudaStream_t st);
+// one right-hand side B bhat_l per shift (Sec. 3.3); mode G / TF / XHAT (X = XHAT
+// here, the caller applies Q)
+int solve_fp64_rhs(const Handle* h, int s, const double* shifts, const double* bhat,
+                   long long ldb, const ssv_opts* o, double* out, long long ldo, int* status,
+                   cudaStream_t st);
 // FP64 solve restricted to the shifts with mask[j] != 0 (others untouched)
 int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, int nb,
                       double* out, long long ldo, int* status, const int* mask, void* xhat_copy,

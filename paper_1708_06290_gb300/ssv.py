@@ -57,7 +57,8 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_dims", "ssv_footprint", "ssv_handle_bytes", "ssv_destroy", "ssv_strerror",
            "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc", "ssv_solve_many",
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
-           "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier")
+           "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
+           "ssv_solve_rhs")
 
 _lib = None
 
@@ -86,6 +87,7 @@ def load(build_if_missing=True):
     L.ssv_load_reduced.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
     L.ssv_solve.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P, P]
     L.ssv_solve_noalloc.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P]
+    L.ssv_solve_rhs.argtypes = [P, I, P, P, LL, ctypes.POINTER(Opts), P, LL, P, P]
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.ssv_solve_many.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
                                  ctypes.POINTER(LL), PP, P]
@@ -102,7 +104,8 @@ def load(build_if_missing=True):
     L.ssv_trace_reset.argtypes = []
     L.ssv_trace_read.argtypes = [I, ctypes.c_char_p, I, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(I), ctypes.POINTER(I)]
-    for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier"):
+    for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
+           "ssv_solve_rhs"):
         getattr(L, f).restype = I
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
@@ -234,6 +237,31 @@ class Handle:
                          _stream_ptr(stream))
         _check(rc, "ssv_solve")
         return out, status, resid
+
+    def solve_rhs(self, shifts, bhat, mode="x", nb=0, out=None, status=None, stream=None):
+        """One right-hand side B bhat[:, l] per shift (Sec. 3.3).  bhat: complex128
+        (m, s) CUDA tensor (column-major or contiguous columns).  Returns (out, status)
+        with out (rows, s): rows = n for x / xhat, p for g / tf."""
+        L = load()
+        _need_cuda(shifts, torch.complex128, "shifts")
+        _need_cuda(bhat, torch.complex128, "bhat")
+        s = shifts.numel()
+        if tuple(bhat.shape) != (self.m, s):
+            raise ValueError("bhat must be (m, s) = (%d, %d)" % (self.m, s))
+        o = opts("fp64", mode, nb, 0, 0, 0.0)
+        rows = self.out_rows(o.mode)
+        dev = shifts.device
+        if out is None:
+            out = torch.empty((s, max(rows, 1)), dtype=torch.complex128, device=dev).t()
+        _need_cuda(out, torch.complex128, "out")
+        if status is None:
+            status = torch.empty(s, dtype=torch.int32, device=dev)
+        rc = L.ssv_solve_rhs(self.ptr, s, ctypes.c_void_p(shifts.data_ptr()),
+                             ctypes.c_void_p(bhat.data_ptr()), _ld(bhat, self.m), ctypes.byref(o),
+                             ctypes.c_void_p(out.data_ptr()), _ld(out, rows),
+                             ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream))
+        _check(rc, "ssv_solve_rhs")
+        return out, status
 
     def apply_q(self, xhat, out=None, stream=None):
         L = load()

@@ -1,0 +1,119 @@
+"""One right-hand side per shift (Sec. 3.3): ssv_solve_rhs against the oracle.
+
+x_l = (A - sigma_l I)^{-1} B bhat_l is checked against the plain dense solve
+with the same right-hand side (oracle.dense_solve_vec), in every output mode;
+with bhat_l = e_j the result must equal column j of the multi-column solve
+bit for bit (the same arithmetic runs).  Tolerances as in test_gpu_parity:
+relative error 1e-10 (well-conditioned shifts; kappa gate 1e6 where sampled).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from paper_1708_06290_gb300 import ssv
+from tests.gpu_util import blocks, dev, relerr, shifts_dev
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-10
+KAPPA_GATE = 1e6
+
+
+def _bhat(m, s, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((m, s)) + 1j * rng.standard_normal((m, s))
+
+
+def _bhat_dev(b):
+    return torch.from_numpy(np.asfortranarray(b)).t().contiguous().t().cuda()
+
+
+@pytest.mark.parametrize("n,m,p,nb", [(300, 4, 3, 0), (97, 3, 2, 5), (130, 16, 16, 0), (64, 1, 1, 0),
+                                      (40, 8, 2, 16)])
+def test_solve_rhs_matches_dense_oracle_all_modes(n, m, p, nb):
+    sysr = W.random_system(n, m, p, seed=1200 + n + m)
+    sig = np.concatenate([W.imag_axis_logspace(-2, 2, 7), [-2.4 + 0.3j, 0.2 - 0.1j]])
+    bh = _bhat(m, len(sig), seed=n)
+    h = ssv.reduce(dev(sysr.A), dev(sysr.B), dev(sysr.C))
+    xo, st = oracle.dense_solve_vec(sysr.A, (sysr.B @ bh).T, sig)
+    assert (st == 0).all()
+    sd, bd = shifts_dev(sig), _bhat_dev(bh)
+    x, status = h.solve_rhs(sd, bd, mode="x", nb=nb)
+    xh, _ = h.solve_rhs(sd, bd, mode="xhat", nb=nb)
+    g, _ = h.solve_rhs(sd, bd, mode="g", nb=nb)
+    tf, _ = h.solve_rhs(sd, bd, mode="tf", nb=nb)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    x, g, tf = x.cpu().numpy(), g.cpu().numpy(), tf.cpu().numpy()
+    qx = h.apply_q(xh).cpu().numpy()
+    for j in range(len(sig)):
+        assert relerr(x[:, j], xo[j]) < REL_TOL, j
+        assert relerr(qx[:, j], xo[j]) < REL_TOL, j
+        assert relerr(g[:, j], sysr.C @ xo[j]) < REL_TOL, j
+        assert relerr(tf[:, j], -(sysr.C @ xo[j])) < REL_TOL, j
+
+
+def test_unit_coefficients_reproduce_the_multi_column_solve_exactly():
+    sysr = W.random_system(210, 5, 3, seed=1301)
+    sig = W.imag_axis_logspace(-1, 1, 6)
+    h = ssv.reduce(dev(sysr.A), dev(sysr.B), dev(sysr.C))
+    sd = shifts_dev(sig)
+    full, _, _ = h.solve(sd, mode="xhat")
+    gfull, _, _ = h.solve(sd, mode="g")
+    for j in (0, 3, 4):
+        e = np.zeros((5, len(sig)), dtype=complex)
+        e[j, :] = 1.0
+        xv, _ = h.solve_rhs(sd, _bhat_dev(e), mode="xhat")
+        gv, _ = h.solve_rhs(sd, _bhat_dev(e), mode="g")
+        for l in range(len(sig)):
+            assert torch.equal(xv[:, l], full[:, l * 5 + j])
+            assert torch.equal(gv[:, l], gfull[:, l * 5 + j])
+
+
+def test_exact_singular_shift_is_reported():
+    n, m, p = 30, 2, 2
+    rng = np.random.default_rng(9)
+    A = np.triu(rng.standard_normal((n, n))) - 2 * np.eye(n)
+    B = np.eye(n)[:, :m]
+    C = rng.standard_normal((p, n))
+    h = ssv.reduce(dev(A), dev(B), dev(C))
+    sig = np.array([A[n - 1, n - 1] + 0j, 0.4j])
+    _, st = h.solve_rhs(shifts_dev(sig), _bhat_dev(_bhat(m, 2, 1)), mode="g")
+    st = st.cpu().numpy()
+    assert st[0] == ssv.SHIFT_SINGULAR and st[1] == ssv.SHIFT_OK
+
+
+def test_precision_workload_sampled_tangential_values():
+    """n = 5000, m = p = 16, the 2000 grid shifts with random bhat_l; sampled
+    G(sigma_l) bhat_l against the tier-2 oracle (kappa gate 1e6)."""
+    sysr, sig = W.workload_precision()
+    bh = _bhat(sysr.m, len(sig), seed=77)
+    h = ssv.reduce(dev(sysr.A), dev(sysr.B), dev(sysr.C))
+    g, st = h.solve_rhs(shifts_dev(sig), _bhat_dev(bh), mode="g")
+    g = g.cpu().numpy()
+    assert (st.cpu().numpy() == 0).all()
+    idx = np.linspace(0, len(sig) - 1, 10).astype(int)
+    Ho, Ro, Co, _ = oracle.reduce(sysr.A, sysr.B, sysr.C)
+    Go, sto, cond = oracle.reduced_solve(Ho, Ro, Co, sig[idx], want="g", cond=True)
+    checked = 0
+    for k, j in enumerate(idx):
+        if cond[k] <= KAPPA_GATE:
+            assert relerr(g[:, j], Go[k] @ bh[:, j]) < REL_TOL, (j, cond[k])
+            checked += 1
+    assert checked >= 5
+
+
+def test_mixed_precision_is_refused():
+    sysr = W.random_system(20, 2, 1, seed=3)
+    h = ssv.reduce(dev(sysr.A), dev(sysr.B), dev(sysr.C))
+    L = ssv.load()
+    o = ssv.opts("mixed", "x", 0, 0, 8, 1e-14)
+    sd = shifts_dev([0.5j])
+    b = _bhat_dev(np.ones((2, 1), dtype=complex))
+    out = torch.empty((1, 20), dtype=torch.complex128, device="cuda").t()
+    import ctypes
+    rc = L.ssv_solve_rhs(h.ptr, 1, ctypes.c_void_p(sd.data_ptr()), ctypes.c_void_p(b.data_ptr()), 2,
+                         ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), 20, None, None)
+    assert rc == ssv.SSV_ENOTSUP

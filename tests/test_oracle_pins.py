@@ -236,7 +236,7 @@ def test_hager_condition_estimate_is_tight_lower_bound(ora):
 
 
 # --------------------------------------------------------------------------
-# dense_solve_vec: a different right-hand side for every shift (Sec. 3.5),
+# dense_solve_vec: a different right-hand side for every shift (Sec. 3.3),
 # x = (A - sigma I)^{-1} b and the transposed x = (A - sigma I)^{-T} c
 # --------------------------------------------------------------------------
 
