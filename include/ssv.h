@@ -131,6 +131,26 @@ int ssv_solve_rhs(ssv_handle h, int s, const double* shifts, const double* bhat,
                   const ssv_opts* o, double* out, long long ldo, int* status, void* stream);
 
 /*
+ * ssv_solve_trans -- the transposed systems (A - sigma_l I)^T x_l = C^T chat_l
+ * (Sec. 3.3; plain transpose, not conjugate), one right-hand side per shift.
+ * In reduced coordinates (H - sigma I)^T xt = C~^T chat with x = Q xt.  With J
+ * the reversal permutation, J (H - sigma I)^T J is upper m-Hessenberg again,
+ * so the bottom-up sweep of ssv_solve solves it for the dense right-hand side
+ * J C~^T chat, back-substituting against each finalised column as it appears.
+ *   chat (device): complex p x s, column l = chat_l, ld ldc >= max(1, p);
+ *     the handle must have p >= 1.
+ *   o: precision SSV_FP64 only; mode SSV_X (out column l = x_l) or SSV_XHAT
+ *     (out column l = Q^T x_l); other modes -> SSV_ENOTSUP.
+ *   out (device): complex n x s, ld ldo >= n.
+ *   status (device, may be NULL): s ints, SSV_SHIFT_*.
+ * Each call allocates (stream-ordered) an n x n flipped copy of H, n x s
+ * right-hand sides and the per-block window state; the handle is not changed.
+ * Errors: SSV_EINVAL, SSV_ENOTSUP, SSV_ENOMEM, SSV_ECUDA.
+ */
+int ssv_solve_trans(ssv_handle h, int s, const double* shifts, const double* chat, long long ldc,
+                    const ssv_opts* o, double* out, long long ldo, int* status, void* stream);
+
+/*
  * ssv_solve_many -- many reduced systems of uneven n, m and shift counts in
  * one persistent launch (FP64: one kernel over a cost-ordered worklist of
  * (system, shift) items, Sec. 3 applied to several systems at once; MIXED:

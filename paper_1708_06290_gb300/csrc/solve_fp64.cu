@@ -57,8 +57,9 @@ struct Layout {
   static constexpr int kCoefRows = kNB + MAXM;
   static constexpr size_t cand_elems = (size_t)kSlots * kNB;
   static constexpr size_t coef_elems = (size_t)kCoefRows * kSlots;
+  // + the dense right-hand side's block rows and coefficients (RHS sweeps)
   static constexpr size_t bytes =
-      (cand_elems + coef_elems + 3 * MAXM * MAXM + 2 * MAXM + 4) * sizeof(cd) + 64;
+      (cand_elems + coef_elems + 3 * MAXM * MAXM + 2 * MAXM + 4 + kNB + kCoefRows) * sizeof(cd) + 64;
 };
 
 // One system as the FP64 solve sees it.
@@ -77,10 +78,19 @@ struct FpSys {
   const double* hnorm;
   const cd* bhat;    // per-shift right-hand side coefficients (m x s, ld ldb), or null
   long long ldb;
+  const cd* rhs;     // dense right-hand sides (n x s, ld ldr) of an RHS sweep (p == 0)
+  long long ldr;
+  int flip_out;      // write output row i to row n-1-i (transposed systems)
 };
 
-// Solve shift sh of system d with the window state in Z2 (and ZT).
-template <int MAXM>
+// Solve shift sh of system d with the window state in Z2 (and ZT).  With RHS,
+// the dense right-hand side d.rhs(:, sh) is carried through the sweep: each
+// finalised column F_c (diagonal beta_c) removes f_c = rhs_c / beta_c times
+// itself from the rows above (back substitution against the triangular factor
+// as it is produced, bottom-up), the rows above the block through the
+// accumulated coefficients `coefr`; the solution is T(:, live) y - Tr with Tr
+// the T rows of sum_c (-f_c) F_c and y from the final m x m block.
+template <int MAXM, bool RHS = false>
 __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
                            unsigned char* smem_raw, int* s_piv_p, int* s_sing_p) {
   using L = Layout<MAXM>;
@@ -90,6 +100,8 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   cd* Wm = coef + L::coef_elems;             // MAXM x (2 MAXM) augmented [Wm | R1]
   cd* lmul = Wm + 2 * MAXM * MAXM;           // reflector v (MAXM + 2 slots) and tau
   cd* Yb = lmul + (MAXM + 4);                // MAXM x MAXM solution
+  cd* rhs_s = Yb + MAXM * MAXM;              // RHS rows of the block (kNB)
+  cd* coefr = rhs_s + kNB;                   // RHS coefficients (kCoefRows)
   int& s_piv = *s_piv_p;
   int& s_sing = *s_sing_p;
   const int n = d.n, m = d.m, p = d.p, nb = d.nb, mode = d.mode, ldct = d.ldct;
@@ -104,8 +116,10 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   const double* __restrict__ hnorm = d.hnorm;
   const int tid = threadIdx.x;
   const int ldz = p + n;
-  const bool track_t = (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
+  const bool track_t = RHS || (mode == SSV_XHAT || mode == SSV_X || xhat_copy != nullptr);
   cd* ZT = Z2 + (size_t)ldz * m;  // n x m, valid when track_t
+  cd* Zr = ZT + (size_t)n * m;    // RHS rows in progress (n), when RHS
+  cd* Tr = Zr + n;                // T rows of the removed finalised columns (n), when RHS
   const cd sigma = shifts[sh];
   // ||H - sigma I||_F from ||H||_F^2 and trace(H); a finalized diagonal entry
   // of magnitude <= n eps ||H - sigma I||_F marks the shift singular.
@@ -127,6 +141,13 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
       ZT[idx] = mkcd(i == n - m + q ? 1.0 : 0.0, 0.0);
     }
   }
+  if (RHS) {
+    const cd* rin = d.rhs + (size_t)sh * d.ldr;
+    for (int i = tid; i < n; i += kThreads) {
+      Zr[i] = rin[i];
+      Tr[i] = mkcd(0.0, 0.0);
+    }
+  }
   if (tid == 0) s_sing = 0;
   __syncthreads();
 
@@ -139,6 +160,10 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     for (int idx = tid; idx < m * nbe; idx += kThreads) {
       int t = idx % nbe, q = idx / nbe;
       cand[q * kNB + t] = Z2[(r + t) + (size_t)q * ldz];
+    }
+    if (RHS) {
+      for (int t = tid; t < nbe; t += kThreads) rhs_s[t] = Zr[r + t];
+      for (int crow = tid; crow < L::kCoefRows; crow += kThreads) coefr[crow] = mkcd(0.0, 0.0);
     }
     // coefficients: identity on the old live columns, e_{nbe-1} for the
     // fresh column F_{nbe-1} that enters slot m (slots m, m+1 alternate)
@@ -189,6 +214,8 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
           // ||v||^2 = 2 ||y||^2 + 2 |y_fs| ||y||
           const double vv = 2.0 * nrm2 + 2.0 * af * nrm;
           lmul[MAXM + 2].x = trivial ? 0.0 : 2.0 / vv;
+          // finalised diagonal entry of row c: conj(alpha) (x_fs when no reflection)
+          lmul[MAXM + 3] = trivial ? xf : mkcd(alpha.x, -alpha.y);
           if (nrm <= sing_tol) s_sing = 1;  // |R(row, row)| = ||x|| at working precision
         }
       }
@@ -224,6 +251,23 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
           }
         }
       }
+      if (RHS) {
+        // back substitution with the finalised column F_c (slot fs)
+        __syncthreads();
+        const cd beta = lmul[MAXM + 3];
+        const cd f = (beta.x == 0.0 && beta.y == 0.0) ? mkcd(0.0, 0.0) : cdiv(rhs_s[c], beta);
+        const int nrow = c;
+        const int ncoef = (nbe - c) + m;
+        for (int e = tid; e < nrow + ncoef; e += kThreads) {
+          if (e < nrow) {
+            rhs_s[e] = cfms(f, cand[fs * kNB + e], rhs_s[e]);
+          } else {
+            const int ee = e - nrow;
+            const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
+            coefr[crow] = cfms(f, coef[crow * S + fs], coefr[crow]);
+          }
+        }
+      }
       if (c > 0) {
         const int cn = c - 1, jc = j0 + cn;
         for (int t = tid; t <= cn; t += kThreads) {
@@ -240,6 +284,8 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     // ---- update the rows above the block (and the T rows)
     for (int i = tid; i < r; i += kThreads) {
       cd acc[MAXM];
+      cd racc = mkcd(0.0, 0.0);
+      if (RHS) racc = Zr[i];
 #pragma unroll
       for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
       for (int c = 0; c < nbe; ++c) {
@@ -254,6 +300,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
             acc[q].y = fma(z, w.y, acc[q].y);
           }
         }
+        if (RHS) racc = mkcd(fma(z, coefr[c].x, racc.x), fma(z, coefr[c].y, racc.y));
       }
       for (int qq = 0; qq < m; ++qq) {
         const cd zz = Z2[i + (size_t)qq * ldz];
@@ -261,6 +308,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
 #pragma unroll
         for (int q = 0; q < MAXM; ++q)
           if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
+        if (RHS) racc = cfma(zz, coefr[kNB + qq], racc);
       }
       const int cd_ = i - (r - m);  // diagonal correction of fresh column cd_
       if (cd_ >= 0 && cd_ < min(m, nbe)) {
@@ -268,7 +316,9 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
 #pragma unroll
         for (int q = 0; q < MAXM; ++q)
           if (q < m) acc[q] = cfms(sigma, cr[q], acc[q]);
+        if (RHS) racc = cfms(sigma, coefr[cd_], racc);
       }
+      if (RHS) Zr[i] = racc;
 #pragma unroll
       for (int q = 0; q < MAXM; ++q)
         if (q < m) Z2[i + (size_t)q * ldz] = acc[q];
@@ -278,6 +328,16 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
       const int lo = k - m;
       for (int i = j0 + tid; i < n; i += kThreads) {
         cd acc[MAXM];
+        if (RHS) {
+          cd tr;
+          if (i < lo) {
+            tr = coefr[i - j0];
+          } else {
+            tr = Tr[i];
+            for (int qq = 0; qq < m; ++qq) tr = cfma(ZT[i + (size_t)qq * n], coefr[kNB + qq], tr);
+          }
+          Tr[i] = tr;
+        }
         if (i < lo) {
           const cd* cr = coef + (i - j0) * S;
 #pragma unroll
@@ -307,13 +367,15 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   // right-hand side per shift (Sec. 3.3) the augmented part is the single
   // column R1 bhat, and Y is m x 1.
   const cd* __restrict__ bh = d.bhat != nullptr ? d.bhat + (size_t)sh * d.ldb : nullptr;
-  const int nr = bh != nullptr ? 1 : m;
+  const int nr = (RHS || bh != nullptr) ? 1 : m;
   const int w2 = m + nr;
   for (int idx = tid; idx < m * w2; idx += kThreads) {
     int i = idx % m, j = idx / m;
     cd v;
     if (j < m) v = Z2[(p + i) + (size_t)j * ldz];
-    else if (bh != nullptr) {
+    else if (RHS) {
+      v = Zr[i];
+    } else if (bh != nullptr) {
       v = mkcd(0.0, 0.0);
       for (int t = i; t < m; ++t) {
         const double rv = R[i + (size_t)t * n];
@@ -399,9 +461,10 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     for (int idx = tid; idx < n * nr; idx += kThreads) {
       int i = idx % n, q = idx / n;
       cd acc = mkcd(0.0, 0.0);
+      if (RHS) acc = mkcd(-Tr[i].x, -Tr[i].y);
       for (int t = 0; t < m; ++t) acc = cfma(ZT[i + (size_t)t * n], Yb[t + q * MAXM], acc);
       if (sing) acc = mkcd(nanv, nanv);
-      o[i + (size_t)q * ld] = acc;
+      o[(d.flip_out ? n - 1 - i : i) + (size_t)q * ld] = acc;
     }
   }
   if (status != nullptr && tid == 0) status[sh] = sing ? SSV_SHIFT_SINGULAR : SSV_SHIFT_OK;
@@ -423,12 +486,68 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
   d.n = n; d.m = m; d.p = p; d.nb = nb; d.mode = mode; d.H = H; d.Ct = Ct; d.ldct = ldct;
   d.R = R; d.shifts = shifts; d.out = out; d.ldo = ldo; d.status = status;
   d.xhat_copy = xhat_copy; d.ldxc = ldxc; d.hnorm = hnorm; d.bhat = bhat; d.ldb = ldb;
+  d.rhs = nullptr; d.ldr = 0; d.flip_out = 0;
   cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
   // With a work list, the block takes list entries blockIdx.x, +gridDim.x, ...
   const int nwork = list != nullptr ? *count : s;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int sh = list != nullptr ? list[w] : w;
     fp64_shift<MAXM>(d, sh, Z2, smem_raw, &s_piv, &s_sing);
+  }
+}
+
+// Dense right-hand side per shift (the transposed systems of Sec. 3.3, in the
+// flipped form built by solve_fp64_trans); d.p == 0.
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) solve_fp64_rhs_kernel(FpSys d, int s,
+                                                                  cd* __restrict__ scratch,
+                                                                  size_t slot_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_piv;
+  __shared__ int s_sing;
+  cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
+  for (int w = blockIdx.x; w < s; w += gridDim.x)
+    fp64_shift<MAXM, true>(d, w, Z2, smem_raw, &s_piv, &s_sing);
+}
+
+// Ht(i, j) = H(n-1-j, n-1-i) on the structural part i <= j + m, zero below:
+// J (H - sigma I)^T J = Ht - sigma I is upper m-Hessenberg again.  32 x 32
+// tiles through shared memory, coalesced on both sides.
+__global__ void flip_transpose_kernel(const double* __restrict__ H, int n, int m,
+                                      double* __restrict__ Ht) {
+  __shared__ double tile[32][33];
+  const int a0 = blockIdx.x * 32, b0 = blockIdx.y * 32;  // rows / columns of H
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int k = 0; k < 32; k += 8) {
+    const int a = a0 + tx, b = b0 + ty + k;
+    tile[ty + k][tx] = (a < n && b < n) ? H[a + (size_t)b * n] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < 32; k += 8) {
+    const int b = b0 + tx, a = a0 + ty + k;
+    if (a < n && b < n) {
+      const int i = n - 1 - b, j = n - 1 - a;
+      Ht[i + (size_t)j * n] = (i <= j + m) ? tile[tx][ty + k] : 0.0;
+    }
+  }
+}
+
+// d(i, l) = (Ct^T chat_l)(n-1-i): the flipped reduced right-hand side C~^T chat_l.
+__global__ void flipped_rhs_kernel(const double* __restrict__ Ct, int ldct, int p, int n,
+                                   const cd* __restrict__ chat, long long ldc, int s,
+                                   cd* __restrict__ dvec) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * s;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n), l = (int)(idx / n);
+    const int col = n - 1 - i;
+    const cd* c = chat + (size_t)l * ldc;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < p; ++k) {
+      const double v = Ct[k + (size_t)col * ldct];
+      re = fma(v, c[k].x, re);
+      im = fma(v, c[k].y, im);
+    }
+    dvec[idx] = mkcd(re, im);
   }
 }
 
@@ -635,6 +754,91 @@ int solve_fp64_rhs(const Handle* h, int s, const double* shifts, const double* b
   if (m <= 32) return launch_solve<32>(h, s, shifts, nb, mode, out, ldo, status, nullptr, 0, st, nullptr, nullptr, b, ldb);
   return SSV_ENOTSUP;
 }
+namespace {
+template <int MAXM>
+int launch_rhs(const FpSys& d, int s, cudaStream_t st) {
+  using L = Layout<MAXM>;
+  const size_t slot = (size_t)d.n * d.m * 2 + 2 * (size_t)d.n;
+  auto kern = solve_fp64_rhs_kernel<MAXM>;
+  SSV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+  int per_sm = 0;
+  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L::bytes));
+  per_sm = std::max(1, std::min(per_sm, 2));
+  const int grid = std::min(s, num_sms() * per_sm);
+  cd* scratch = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(cd) * slot * grid, st));
+  kern<<<grid, kThreads, L::bytes, st>>>(d, s, scratch, slot);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return SSV_ECUDA;
+  }
+  return SSV_OK;
+}
+}  // namespace
+
+// Transposed systems (A - sigma_l I)^T x_l = C^T chat_l (Sec. 3.3) in reduced
+// coordinates: (H - sigma I)^T xt = C~^T chat with x = Q xt.  With J the
+// reversal, J (H - sigma I)^T J = Ht - sigma I is upper m-Hessenberg, so the
+// same bottom-up sweep solves it for the dense right-hand side J C~^T chat;
+// the solution is flipped back on output (out = Q^T x_l).
+int solve_fp64_trans(const Handle* h, int s, const double* shifts, const double* chat,
+                     long long ldc, const ssv_opts* o, double* out, long long ldo, int* status,
+                     cudaStream_t st) {
+  const int n = h->n, m = h->m, p = h->p;
+  const int nb = o->nb > 0 ? o->nb : tuned_nb(n, m, 0, SSV_FP64, SSV_XHAT);
+  if (nb > kNB) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  double* Ht = nullptr;
+  cd* dvec = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&Ht, sizeof(double) * (size_t)n * n, st));
+  cudaError_t e = cudaMallocAsync((void**)&dvec, sizeof(cd) * (size_t)n * s, st);
+  int rc = SSV_OK;
+  if (e == cudaSuccess) {
+    const dim3 tg((n + 31) / 32, (n + 31) / 32);
+    flip_transpose_kernel<<<tg, dim3(32, 8), 0, st>>>(h->H, n, m, Ht);
+    count_launch();
+    const long long tot = (long long)n * s;
+    flipped_rhs_kernel<<<(int)std::min<long long>(4096, (tot + 255) / 256), 256, 0, st>>>(
+        h->Ct, p > 0 ? p : 1, p, n, reinterpret_cast<const cd*>(chat), ldc, s, dvec);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    rc = e == cudaErrorMemoryAllocation ? SSV_ENOMEM : SSV_ECUDA;
+  }
+  if (rc == SSV_OK) {
+    FpSys d;
+    d.n = n; d.m = m; d.p = 0; d.nb = nb; d.mode = SSV_XHAT; d.H = Ht; d.Ct = nullptr; d.ldct = 1;
+    d.R = h->R; d.shifts = reinterpret_cast<const cd*>(shifts);
+    d.out = reinterpret_cast<cd*>(out); d.ldo = ldo; d.status = status;
+    d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2; d.bhat = nullptr; d.ldb = 0;
+    d.rhs = dvec; d.ldr = n; d.flip_out = 1;
+    if (m <= 1) rc = launch_rhs<1>(d, s, st);
+    else if (m <= 2) rc = launch_rhs<2>(d, s, st);
+    else if (m <= 4) rc = launch_rhs<4>(d, s, st);
+    else if (m <= 8) rc = launch_rhs<8>(d, s, st);
+    else if (m <= 16) rc = launch_rhs<16>(d, s, st);
+    else if (m <= 32) rc = launch_rhs<32>(d, s, st);
+    else rc = SSV_ENOTSUP;
+  }
+  if (rc == SSV_OK && status != nullptr) {
+    nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, n, 1, s, status);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      rc = SSV_ECUDA;
+    }
+  }
+  if (dvec) cudaFreeAsync(dvec, st);
+  if (Ht) cudaFreeAsync(Ht, st);
+  return rc;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the FP64 solve (ssv_solve_noalloc).
@@ -807,6 +1011,7 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
     d.out = reinterpret_cast<cd*>(outs[k]); d.ldo = ldos[k];
     d.status = status ? status[k] : nullptr;
     d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2; d.bhat = nullptr; d.ldb = 0;
+    d.rhs = nullptr; d.ldr = 0; d.flip_out = 0;
     bp->maxm = std::max(bp->maxm, h->m);
     bp->slot = std::max(bp->slot, (size_t)(h->p + h->n) * h->m + (track_t ? (size_t)h->n * h->m : 0));
     const double cost = (double)h->n * h->n * h->m * (1.0 + 2.0 * h->m / d.nb);

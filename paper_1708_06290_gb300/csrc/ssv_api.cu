@@ -201,6 +201,28 @@ int ssv_solve_rhs(ssv_handle hh, int s, const double* shifts, const double* bhat
   return rc;
 }
 
+int ssv_solve_trans(ssv_handle hh, int s, const double* shifts, const double* chat, long long ldc,
+                    const ssv_opts* o_in, double* out, long long ldo, int* status, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || s < 0) return SSV_EINVAL;
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc != SSV_OK) return rc;
+  if (o.precision != SSV_FP64) return SSV_ENOTSUP;
+  if (o.mode != SSV_X && o.mode != SSV_XHAT) return SSV_ENOTSUP;
+  if (h->p < 1) return SSV_EINVAL;
+  if (s == 0) return SSV_OK;
+  if (!shifts || !out || !chat || ldc < h->p || ldo < h->n) return SSV_EINVAL;
+  if (o.mode == SSV_X && !h->has_q) return SSV_ENOTSUP;
+  cudaStream_t st = (cudaStream_t)stream;
+  void* tr = trace_begin("solve_trans", st);
+  rc = solve_fp64_trans(h, s, shifts, chat, ldc, &o, out, ldo, status, st);
+  trace_end(tr, st);
+  if (rc == SSV_OK && o.mode == SSV_X) rc = apply_q_fp64(h, s, out, ldo, out, ldo, st);
+  return rc;
+}
+
 static int check_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
                       const ssv_opts& o, double* const* outs, const long long* ldos) {
   if (nsys < 0 || (nsys > 0 && (!hs || !s || !shifts || !outs || !ldos))) return SSV_EINVAL;

@@ -98,6 +98,10 @@ int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, 
 int solve_fp64_rhs(const Handle* h, int s, const double* shifts, const double* bhat,
                    long long ldb, const ssv_opts* o, double* out, long long ldo, int* status,
                    cudaStream_t st);
+// transposed systems (A - sigma_l I)^T x_l = C^T chat_l (Sec. 3.3); out = Q^T x_l (n x s)
+int solve_fp64_trans(const Handle* h, int s, const double* shifts, const double* chat,
+                     long long ldc, const ssv_opts* o, double* out, long long ldo, int* status,
+                     cudaStream_t st);
 // FP64 solve restricted to the shifts with mask[j] != 0 (others untouched)
 int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, int nb,
                       double* out, long long ldo, int* status, const int* mask, void* xhat_copy,

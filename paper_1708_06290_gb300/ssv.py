@@ -58,7 +58,7 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc", "ssv_solve_many",
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
            "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
-           "ssv_solve_rhs")
+           "ssv_solve_rhs", "ssv_solve_trans")
 
 _lib = None
 
@@ -88,6 +88,7 @@ def load(build_if_missing=True):
     L.ssv_solve.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P, P]
     L.ssv_solve_noalloc.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P]
     L.ssv_solve_rhs.argtypes = [P, I, P, P, LL, ctypes.POINTER(Opts), P, LL, P, P]
+    L.ssv_solve_trans.argtypes = [P, I, P, P, LL, ctypes.POINTER(Opts), P, LL, P, P]
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.ssv_solve_many.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
                                  ctypes.POINTER(LL), PP, P]
@@ -105,7 +106,7 @@ def load(build_if_missing=True):
     L.ssv_trace_read.argtypes = [I, ctypes.c_char_p, I, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(I), ctypes.POINTER(I)]
     for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
-           "ssv_solve_rhs"):
+           "ssv_solve_rhs", "ssv_solve_trans"):
         getattr(L, f).restype = I
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
@@ -261,6 +262,30 @@ class Handle:
                              ctypes.c_void_p(out.data_ptr()), _ld(out, rows),
                              ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream))
         _check(rc, "ssv_solve_rhs")
+        return out, status
+
+    def solve_trans(self, shifts, chat, mode="x", nb=0, out=None, status=None, stream=None):
+        """Transposed systems (A - sigma_l I)^T x_l = C^T chat[:, l] (Sec. 3.3).
+        chat: complex128 (p, s) CUDA tensor.  Returns (out, status), out (n, s):
+        x_l (mode x) or Q^T x_l (mode xhat)."""
+        L = load()
+        _need_cuda(shifts, torch.complex128, "shifts")
+        _need_cuda(chat, torch.complex128, "chat")
+        s = shifts.numel()
+        if tuple(chat.shape) != (self.p, s):
+            raise ValueError("chat must be (p, s) = (%d, %d)" % (self.p, s))
+        o = opts("fp64", mode, nb, 0, 0, 0.0)
+        dev = shifts.device
+        if out is None:
+            out = torch.empty((s, self.n), dtype=torch.complex128, device=dev).t()
+        _need_cuda(out, torch.complex128, "out")
+        if status is None:
+            status = torch.empty(s, dtype=torch.int32, device=dev)
+        rc = L.ssv_solve_trans(self.ptr, s, ctypes.c_void_p(shifts.data_ptr()),
+                               ctypes.c_void_p(chat.data_ptr()), _ld(chat, self.p), ctypes.byref(o),
+                               ctypes.c_void_p(out.data_ptr()), _ld(out, self.n),
+                               ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream))
+        _check(rc, "ssv_solve_trans")
         return out, status
 
     def apply_q(self, xhat, out=None, stream=None):
