@@ -17,6 +17,10 @@ All arithmetic is IEEE double (complex128), done in ``csrc/ssv_oracle.c``:
   band-limited Gaussian elimination with row pivoting in reduced coordinates,
   plus an optional Hager/Higham estimate of kappa_1(H - sigma I).
 
+:mod:`oracle.givens` holds the greedy Givens annihilation schedule of
+Algorithm 9 (plain Python), pinned by the paper's worked example in
+``tests/golden/greedy_givens_m6_nb8.txt``.
+
 Conventions (Sec. 2, Sec. 3): G(sigma) = C X = Ct Xhat with
 X = (A - sigma I)^{-1} B; the paper's transfer function is
 C (sigma I - A)^{-1} B = -G(sigma).

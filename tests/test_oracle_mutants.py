@@ -121,3 +121,31 @@ def test_mutant_is_caught(tmp_path, name):
     old, new = MUTANTS[name]
     lib = _build_mutant(tmp_path, name, old, new)
     assert _checks(lib) != [], "mutant %s survived every pin" % name
+
+
+GIVENS_MUTANTS = {
+    "partner_smallest_first": ("for c2 in range(r + delta, c1, -1):", "for c2 in range(c1 + 1, r + delta + 1):"),
+    "opens_the_row_below": ("                available.add((r - 1, c))", "                available.add((r + 1, c))"),
+    "partners_never_return": ("        ready |= busy\n", "\n"),
+    "rows_from_the_top": ("for r in range(n_rows, 0, -1):", "for r in range(1, n_rows + 1):"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GIVENS_MUTANTS))
+def test_givens_schedule_mutant_is_caught(name):
+    import types
+
+    import oracle.givens as og
+    from tests.test_oracle_pins import _golden_schedule
+    src = open(og.__file__).read()
+    old, new = GIVENS_MUTANTS[name]
+    assert src.count(old) == 1, name
+    mod = types.ModuleType("givens_mutant")
+    exec(compile(src.replace(old, new), "givens_mutant", "exec"), mod.__dict__)
+    gold = [rots for _, rots in _golden_schedule()]
+    assert og.greedy_schedule(8, 14) == gold
+    try:
+        got = mod.greedy_schedule(8, 14)
+    except Exception:
+        return
+    assert got != gold, "mutant %s reproduces the figure" % name

@@ -320,3 +320,82 @@ def test_dense_solve_vec_exact_singular_shift(ora):
     X, st = ora.dense_solve_vec(sysd.A, np.ones((2, 6), dtype=complex), [a[2] + 0j, 0.5j], trans=True)
     assert st[0] == ora.STATUS_SINGULAR and np.isnan(X[0]).all()
     assert st[1] == ora.STATUS_OK
+
+
+# --------------------------------------------------------------------------
+# greedy Givens schedule (Algorithm 9): the paper's worked example and the
+# properties any valid schedule must have
+# --------------------------------------------------------------------------
+
+def _golden_schedule():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "greedy_givens_m6_nb8.txt")
+    steps = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        steps.append((int(parts[0]), [tuple(int(v) for v in t.split(",")) for t in parts[1:]]))
+    return steps
+
+
+def test_greedy_schedule_reproduces_the_papers_figure():
+    from oracle.givens import greedy_schedule
+    gold = _golden_schedule()
+    assert [k for k, _ in gold] == list(range(1, 14))
+    assert greedy_schedule(8, 14) == [rots for _, rots in gold]
+
+
+def test_literal_bottom_only_initialisation_does_not_finish():
+    """Reading R6: with only the bottom row available at the start, the diagonal
+    entries never open up and the schedule stops early (21 of 48 rotations)."""
+    from oracle.givens import greedy_schedule
+    lit = greedy_schedule(8, 14, initial="bottom_only")
+    assert sum(map(len, lit)) < 48
+
+
+@pytest.mark.parametrize("n_rows,n_cols", [(8, 14), (1, 2), (5, 6), (16, 32), (64, 80), (12, 13), (3, 40)])
+def test_greedy_schedule_is_a_valid_rq_order(n_rows, n_cols):
+    from oracle.givens import greedy_schedule
+    steps = greedy_schedule(n_rows, n_cols)
+    d = n_cols - n_rows
+    zeroed = {}
+    for k, step in enumerate(steps):
+        cols = [c for (_, c1, c2) in step for c in (c1, c2)]
+        assert len(cols) == len(set(cols)), "rotations of a step share a column"
+        for (r, c1, c2) in step:
+            assert r <= c1 < c2 <= r + d
+            assert (r, c1) not in zeroed and (r, c2) not in zeroed
+            if r < n_rows and c1 > r:
+                # the entry below must already be zero (it was updated by that rotation)
+                assert zeroed.get((r + 1, c1), k) < k
+            zeroed[(r, c1)] = k
+    assert set(zeroed) == {(r, c) for r in range(1, n_rows + 1) for c in range(r, r + d)}
+
+
+def test_greedy_schedule_applied_as_givens_rotations_gives_an_rq_factor():
+    """Applying the rotations to a random complex trapezoidal block (rows 1..8,
+    nonzeros in columns r..14) leaves the first delta columns zero and one
+    entry (r, r + delta) on the 'diagonal' of R; the column transform is unitary."""
+    from oracle.givens import greedy_schedule
+    rng = np.random.default_rng(30)
+    nr, ncol = 8, 14
+    Z = rng.standard_normal((nr, ncol)) + 1j * rng.standard_normal((nr, ncol))
+    Z[np.tril_indices(nr, -1, ncol)] = 0.0
+    Z0 = Z.copy()
+    Q = np.eye(ncol, dtype=complex)
+    for step in greedy_schedule(nr, ncol):
+        for (r, c1, c2) in step:
+            a, b = Z[r - 1, c1 - 1], Z[r - 1, c2 - 1]
+            rho = np.hypot(abs(a), abs(b))
+            # [a, b] G = [0, rho] with the unitary G = [[b, conj a], [-a, conj b]] / rho
+            G = np.array([[b, np.conj(a)], [-a, np.conj(b)]]) / rho
+            Z[:, [c1 - 1, c2 - 1]] = Z[:, [c1 - 1, c2 - 1]] @ G
+            Q[:, [c1 - 1, c2 - 1]] = Q[:, [c1 - 1, c2 - 1]] @ G
+    d = ncol - nr
+    assert np.abs(Z[:, :d]).max() < 1e-12 * np.abs(Z0).max()
+    for r in range(nr):
+        assert np.abs(Z[r, d:d + r]).max(initial=0.0) < 1e-12 * np.abs(Z0).max()
+        assert abs(Z[r, r + d]) > 1e-3
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(ncol)) < 1e-13
+    assert np.linalg.norm(Z0 @ Q - Z) < 1e-12 * np.linalg.norm(Z0)
