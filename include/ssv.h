@@ -61,6 +61,11 @@ extern "C" {
 #define SSV_XHAT 2 /* out(n x m) = Xhat = (H - sigma I)^{-1} R                */
 #define SSV_X 3    /* out(n x m) = X = Q Xhat = (A - sigma I)^{-1} B          */
 
+/* panel factorisation of each window block (FP64 sweeps) */
+#define SSV_PANEL_HOUSEHOLDER 0 /* one complex reflector per row (default) */
+#define SSV_PANEL_GIVENS 1      /* Givens rotations in the greedy parallel order of
+                                   Algorithm 9 (Sec. 3.2); n_b <= 32, m <= 32 */
+
 typedef struct ssv_opts {
   int precision;           /* SSV_FP64 or SSV_MIXED */
   int mode;                /* SSV_G, SSV_TF, SSV_XHAT, SSV_X */
@@ -68,12 +73,13 @@ typedef struct ssv_opts {
   int tile;                /* shifts per thread block; 0 = default */
   int max_refine;          /* SSV_MIXED: maximum refinement sweeps */
   double tol;              /* SSV_MIXED: target normwise backward error */
+  int panel;               /* SSV_PANEL_HOUSEHOLDER or SSV_PANEL_GIVENS (ssv_solve, FP64) */
 } ssv_opts;
 
 typedef struct ssv_handle_s* ssv_handle;
 
 /* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 8,
- * tol = 1e-14. */
+ * tol = 1e-14, panel = SSV_PANEL_HOUSEHOLDER. */
 void ssv_default_opts(ssv_opts* o);
 
 /*
@@ -149,6 +155,20 @@ int ssv_solve_rhs(ssv_handle h, int s, const double* shifts, const double* bhat,
  */
 int ssv_solve_trans(ssv_handle h, int s, const double* shifts, const double* chat, long long ldc,
                     const ssv_opts* o, double* out, long long ldo, int* status, void* stream);
+
+/*
+ * ssv_givens_schedule -- the greedy parallel annihilation schedule that
+ * SSV_PANEL_GIVENS uses (Algorithm 9, Sec. 3.2), for a window block of `rows`
+ * rows and rows + m columns.  Host-only (no device work).
+ *   rot (host, capacity max_rot): triples r, c1, c2 (1-based, as in the
+ *     paper's worked example): the zero at (r, c1) is introduced with (r, c2);
+ *   off (host, capacity max_steps + 1): step t holds rotations off[t] ..
+ *     off[t+1]-1;  *nsteps: the number of steps.
+ * Returns the number of rotations (rows * m), or SSV_EINVAL (bad sizes,
+ * NULL pointers, or capacities too small).
+ */
+int ssv_givens_schedule(int rows, int m, int* rot, int max_rot, int* off, int max_steps,
+                        int* nsteps);
 
 /*
  * ssv_solve_many -- many reduced systems of uneven n, m and shift counts in

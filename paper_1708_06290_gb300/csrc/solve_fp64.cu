@@ -32,6 +32,7 @@
 // whole sweep (no grid-wide phases); the final m x m solve runs on the GPU.
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -62,6 +63,33 @@ struct Layout {
       (cand_elems + coef_elems + 3 * MAXM * MAXM + 2 * MAXM + 4 + kNB + kCoefRows) * sizeof(cd) + 64;
 };
 
+// Givens-panel variant (Sec. 3.2, Algorithms 9/10): the whole window block
+// Zb (n_b x (n_b + m), column-major, ld kNBG) and its column transform P
+// ((n_b + m) x (n_b + m), ld kNBG + MAXM) live in shared memory, so
+// n_b <= kNBG; coefficient rows: fresh c < kNBG, old live kNBG + q.
+constexpr int kNBG = 32;
+template <int MAXM>
+struct GivensLayout {
+  static constexpr int kSlots = MAXM + 2;
+  static constexpr int kCols = kNBG + MAXM;
+  static constexpr int kCoefRows = kNBG + MAXM;
+  static constexpr size_t zb_elems = (size_t)kNBG * kCols;
+  static constexpr size_t p_elems = (size_t)kCols * kCols;
+  static constexpr size_t coef_elems = (size_t)kCoefRows * kSlots;
+  static constexpr size_t bytes =
+      (zb_elems + p_elems + coef_elems + 3 * MAXM * MAXM + 2 * MAXM + 4 + 2 * kNBG) * sizeof(cd) +
+      kNBG * sizeof(int) + 64;
+};
+
+// Greedy annihilation schedule of one block shape (n_b rows, n_b + m columns):
+// rotation j zeroes (r, c1) of the block with (r, c2), packed r | c1 << 8 |
+// c2 << 16 (0-based); step t holds rotations off[t] .. off[t+1]-1.
+struct GivensSched {
+  const int* rot;
+  const int* off;
+  int nsteps;
+};
+
 // One system as the FP64 solve sees it.
 struct FpSys {
   int n, m, p, nb, mode;
@@ -81,6 +109,8 @@ struct FpSys {
   const cd* rhs;     // dense right-hand sides (n x s, ld ldr) of an RHS sweep (p == 0)
   long long ldr;
   int flip_out;      // write output row i to row n-1-i (transposed systems)
+  GivensSched gfull;  // Givens panel: schedule of full blocks (n_b rows)
+  GivensSched gtail;  // and of the last, shorter block
 };
 
 // Solve shift sh of system d with the window state in Z2 (and ZT).  With RHS,
@@ -90,18 +120,25 @@ struct FpSys {
 // as it is produced, bottom-up), the rows above the block through the
 // accumulated coefficients `coefr`; the solution is T(:, live) y - Tr with Tr
 // the T rows of sum_c (-f_c) F_c and y from the final m x m block.
-template <int MAXM, bool RHS = false>
+template <int MAXM, bool RHS = false, bool GIVENS = false>
 __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
                            unsigned char* smem_raw, int* s_piv_p, int* s_sing_p) {
   using L = Layout<MAXM>;
+  using GL = GivensLayout<MAXM>;
   constexpr int S = L::kSlots;
+  constexpr int LB = GIVENS ? kNBG : kNB;   // coefficient row of old live column 0
+  constexpr int CR = GIVENS ? GL::kCoefRows : L::kCoefRows;
   cd* cand = reinterpret_cast<cd*>(smem_raw);
-  cd* coef = cand + L::cand_elems;
-  cd* Wm = coef + L::coef_elems;             // MAXM x (2 MAXM) augmented [Wm | R1]
+  cd* Zb = cand;                             // Givens: window block
+  cd* Pg = Zb + GL::zb_elems;                // Givens: column transform
+  cd* coef = GIVENS ? Pg + GL::p_elems : cand + L::cand_elems;
+  cd* Wm = coef + (GIVENS ? GL::coef_elems : L::coef_elems);  // MAXM x (2 MAXM) augmented [Wm | R1]
   cd* lmul = Wm + 2 * MAXM * MAXM;           // reflector v (MAXM + 2 slots) and tau
   cd* Yb = lmul + (MAXM + 4);                // MAXM x MAXM solution
   cd* rhs_s = Yb + MAXM * MAXM;              // RHS rows of the block (kNB)
   cd* coefr = rhs_s + kNB;                   // RHS coefficients (kCoefRows)
+  cd* grot = Yb + MAXM * MAXM;               // Givens: (g0, g1) of the step's rotations
+  int* grc = reinterpret_cast<int*>(grot + 2 * kNBG);  // Givens: packed (r, c1, c2)
   int& s_piv = *s_piv_p;
   int& s_sing = *s_sing_p;
   const int n = d.n, m = d.m, p = d.p, nb = d.nb, mode = d.mode, ldct = d.ldct;
@@ -156,129 +193,213 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     const int nbe = min(nb, k - m);
     const int r = p + k - nbe;        // rows of [Ct; M] above the block
     const int j0 = k - m - nbe;       // first fresh column
-    // stage the live rows of the block and reset coefficients
-    for (int idx = tid; idx < m * nbe; idx += kThreads) {
-      int t = idx % nbe, q = idx / nbe;
-      cand[q * kNB + t] = Z2[(r + t) + (size_t)q * ldz];
-    }
-    if (RHS) {
-      for (int t = tid; t < nbe; t += kThreads) rhs_s[t] = Zr[r + t];
-      for (int crow = tid; crow < L::kCoefRows; crow += kThreads) coefr[crow] = mkcd(0.0, 0.0);
-    }
-    // coefficients: identity on the old live columns, e_{nbe-1} for the
-    // fresh column F_{nbe-1} that enters slot m (slots m, m+1 alternate)
-    for (int idx = tid; idx < L::kCoefRows * S; idx += kThreads) {
-      int c = idx / S, slot = idx % S;
-      cd v = mkcd(0.0, 0.0);
-      if ((slot < m && c == kNB + slot) || (slot == m && c == nbe - 1)) v = mkcd(1.0, 0.0);
-      coef[idx] = v;
-    }
-    {
-      const int c = nbe - 1, jc = j0 + c;
-      for (int t = tid; t <= c; t += kThreads) {
-        cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
-        if (t == c - m) z = csub(z, sigma);
-        cand[m * kNB + t] = z;
+    if constexpr (GIVENS) {
+      // ---- RQ of the window block with the greedy Givens schedule
+      const int nc = nbe + m;
+      constexpr int ldp = GL::kCols;
+      for (int idx = tid; idx < nc * nbe; idx += kThreads) {
+        const int t = idx % nbe, col = idx / nbe;
+        cd z;
+        if (col < nbe) {  // fresh column j0 + col: nonzero in block rows t <= col
+          z = mkcd(t <= col ? H[(k - nbe + t) + (size_t)(j0 + col) * n] : 0.0, 0.0);
+          if (t == col - m) z = csub(z, sigma);
+        } else {
+          z = Z2[(r + t) + (size_t)(col - nbe) * ldz];
+        }
+        Zb[col * kNBG + t] = z;
       }
-    }
-    __syncthreads();
-    for (int c = nbe - 1; c >= 0; --c) {
-      const int fs = m + ((nbe - 1 - c) & 1);  // slot holding F_c
-      const int fn = (fs == m) ? m + 1 : m;    // slot for F_{c-1}
-      // ---- reflector U = I - tau v v^H on the m + 1 candidates of row c
-      //      (survivors 0..m-1, fresh fs): x U = conj(alpha) e_fs, x = row c.
-      if (tid < 32) {
-        double rest2 = 0.0;  // sum of |x_q|^2 over the m survivors
-        for (int q = tid; q < m; q += 32) {
-          const cd x = cand[q * kNB + c];
-          rest2 = fma(x.x, x.x, fma(x.y, x.y, rest2));
-        }
-        for (int o = 16; o > 0; o >>= 1) rest2 += __shfl_xor_sync(0xffffffffu, rest2, o);
-        const cd xf = cand[fs * kNB + c];
-        const double af2 = fma(xf.x, xf.x, xf.y * xf.y);
-        const double af = sqrt(af2);
-        const double nrm2 = rest2 + af2;
-        const double nrm = sqrt(nrm2);
-        // y = conj(x); alpha = -exp(i arg y_fs) ||y||; v = y - alpha e_fs
-        cd ph = af > 0.0 ? mkcd(xf.x / af, -xf.y / af) : mkcd(1.0, 0.0);
-        const cd alpha = mkcd(-ph.x * nrm, -ph.y * nrm);
-        const bool trivial = !(rest2 > 0.0);
-        for (int q = tid; q <= m; q += 32) {
-          const int slot = q < m ? q : fs;
-          const cd x = cand[slot * kNB + c];
-          cd v = mkcd(x.x, -x.y);
-          if (slot == fs) v = csub(v, alpha);
-          lmul[slot] = v;
-        }
-        if (tid == 0) {
-          // ||v||^2 = 2 ||y||^2 + 2 |y_fs| ||y||
-          const double vv = 2.0 * nrm2 + 2.0 * af * nrm;
-          lmul[MAXM + 2].x = trivial ? 0.0 : 2.0 / vv;
-          // finalised diagonal entry of row c: conj(alpha) (x_fs when no reflection)
-          lmul[MAXM + 3] = trivial ? xf : mkcd(alpha.x, -alpha.y);
-          if (nrm <= sing_tol) s_sing = 1;  // |R(row, row)| = ||x|| at working precision
-        }
+      for (int idx = tid; idx < nc * nc; idx += kThreads) {
+        const int row = idx % nc, col = idx / nc;
+        Pg[col * ldp + row] = mkcd(row == col ? 1.0 : 0.0, 0.0);
       }
       __syncthreads();
-      const double tau = lmul[MAXM + 2].x;
-      // ---- apply to window rows 0..c-1 and the nonzero coefficient rows;
-      //      load F_{c-1} into slot fn meanwhile.
-      if (tau != 0.0) {
-        const int nrow = c;
-        const int ncoef = (nbe - c) + m;
-        for (int e = tid; e < nrow + ncoef; e += kThreads) {
-          cd* base;
-          int stride;
-          if (e < nrow) {
-            base = cand + e;
-            stride = kNB;
-          } else {
-            const int ee = e - nrow;
-            const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
-            base = coef + crow * S;
-            stride = 1;
+      const GivensSched& gs = (nbe == nb) ? d.gfull : d.gtail;
+      for (int step = 0; step < gs.nsteps; ++step) {
+        const int j0r = gs.off[step], cnt = gs.off[step + 1] - j0r;
+        // rotation j maps [a, b] = Zb(r, (c1, c2)) to [0, rho]:
+        // G = [[g0, conj(g1)], [-g1, conj(g0)]], g0 = b / rho, g1 = a / rho
+        for (int j = tid; j < cnt; j += kThreads) {
+          const int pk = gs.rot[j0r + j];
+          const int rr = pk & 255, c1 = (pk >> 8) & 255, c2 = (pk >> 16) & 255;
+          const cd a = Zb[c1 * kNBG + rr], b = Zb[c2 * kNBG + rr];
+          const double rho = hypot(hypot(a.x, a.y), hypot(b.x, b.y));
+          cd g0 = mkcd(1.0, 0.0), g1 = mkcd(0.0, 0.0);
+          if (rho > 0.0) {
+            g0 = mkcd(b.x / rho, b.y / rho);
+            g1 = mkcd(a.x / rho, a.y / rho);
           }
-          cd w = mkcd(0.0, 0.0);
-          for (int q = 0; q <= m; ++q) {
-            const int slot = q < m ? q : fs;
-            w = cfma(base[slot * stride], lmul[slot], w);
-          }
-          w = mkcd(w.x * tau, w.y * tau);
-          for (int q = 0; q <= m; ++q) {
-            const int slot = q < m ? q : fs;
-            const cd vc = mkcd(lmul[slot].x, -lmul[slot].y);
-            base[slot * stride] = cfms(w, vc, base[slot * stride]);
-          }
+          grot[2 * j] = g0;
+          grot[2 * j + 1] = g1;
+          grc[j] = pk;
         }
+        __syncthreads();
+        // [x1, x2] <- [x1 g0 - x2 g1, x1 conj(g1) + x2 conj(g0)] on the block rows
+        // 0 .. r and on every row of P
+        const int span = nbe + nc;
+        for (int e = tid; e < cnt * span; e += kThreads) {
+          const int j = e / span, w = e % span;
+          const int pk = grc[j];
+          const int rr = pk & 255, c1 = (pk >> 8) & 255, c2 = (pk >> 16) & 255;
+          cd *x1, *x2;
+          if (w < nbe) {
+            if (w > rr) continue;
+            x1 = Zb + c1 * kNBG + w;
+            x2 = Zb + c2 * kNBG + w;
+          } else {
+            x1 = Pg + c1 * ldp + (w - nbe);
+            x2 = Pg + c2 * ldp + (w - nbe);
+          }
+          const cd g0 = grot[2 * j], g1 = grot[2 * j + 1];
+          const cd u = *x1, v = *x2;
+          const cd nu = csub(cmul(u, g0), cmul(v, g1));
+          const cd nv = cfma(u, mkcd(g1.x, -g1.y), cmul(v, mkcd(g0.x, -g0.y)));
+          *x1 = (w == rr) ? mkcd(0.0, 0.0) : nu;
+          *x2 = nv;
+        }
+        __syncthreads();
+      }
+      // R(t, t + m) is the finalised diagonal of block row t
+      for (int t = tid; t < nbe; t += kThreads) {
+        const cd dgl = Zb[(t + m) * kNBG + t];
+        if (sqrt(dgl.x * dgl.x + dgl.y * dgl.y) <= sing_tol) s_sing = 1;
+      }
+      // the first m columns of P express the surviving (new live) columns:
+      // coefficient rows fresh c -> P(c, q), old live qq -> P(nbe + qq, q)
+      for (int idx = tid; idx < CR * S; idx += kThreads) {
+        const int crow = idx / S, q = idx % S;
+        cd v = mkcd(0.0, 0.0);
+        if (q < m) {
+          if (crow < nbe) v = Pg[q * ldp + crow];
+          else if (crow >= LB && crow - LB < m) v = Pg[q * ldp + nbe + (crow - LB)];
+        }
+        coef[idx] = v;
+      }
+      __syncthreads();
+    } else {
+      // stage the live rows of the block and reset coefficients
+      for (int idx = tid; idx < m * nbe; idx += kThreads) {
+        int t = idx % nbe, q = idx / nbe;
+        cand[q * kNB + t] = Z2[(r + t) + (size_t)q * ldz];
       }
       if (RHS) {
-        // back substitution with the finalised column F_c (slot fs)
-        __syncthreads();
-        const cd beta = lmul[MAXM + 3];
-        const cd f = (beta.x == 0.0 && beta.y == 0.0) ? mkcd(0.0, 0.0) : cdiv(rhs_s[c], beta);
-        const int nrow = c;
-        const int ncoef = (nbe - c) + m;
-        for (int e = tid; e < nrow + ncoef; e += kThreads) {
-          if (e < nrow) {
-            rhs_s[e] = cfms(f, cand[fs * kNB + e], rhs_s[e]);
-          } else {
-            const int ee = e - nrow;
-            const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
-            coefr[crow] = cfms(f, coef[crow * S + fs], coefr[crow]);
-          }
-        }
+        for (int t = tid; t < nbe; t += kThreads) rhs_s[t] = Zr[r + t];
+        for (int crow = tid; crow < L::kCoefRows; crow += kThreads) coefr[crow] = mkcd(0.0, 0.0);
       }
-      if (c > 0) {
-        const int cn = c - 1, jc = j0 + cn;
-        for (int t = tid; t <= cn; t += kThreads) {
+      // coefficients: identity on the old live columns, e_{nbe-1} for the
+      // fresh column F_{nbe-1} that enters slot m (slots m, m+1 alternate)
+      for (int idx = tid; idx < L::kCoefRows * S; idx += kThreads) {
+        int c = idx / S, slot = idx % S;
+        cd v = mkcd(0.0, 0.0);
+        if ((slot < m && c == kNB + slot) || (slot == m && c == nbe - 1)) v = mkcd(1.0, 0.0);
+        coef[idx] = v;
+      }
+      {
+        const int c = nbe - 1, jc = j0 + c;
+        for (int t = tid; t <= c; t += kThreads) {
           cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
-          if (t == cn - m) z = csub(z, sigma);
-          cand[fn * kNB + t] = z;
+          if (t == c - m) z = csub(z, sigma);
+          cand[m * kNB + t] = z;
         }
-        for (int crow = tid; crow < L::kCoefRows; crow += kThreads)
-          coef[crow * S + fn] = mkcd(crow == cn ? 1.0 : 0.0, 0.0);
       }
       __syncthreads();
+      for (int c = nbe - 1; c >= 0; --c) {
+        const int fs = m + ((nbe - 1 - c) & 1);  // slot holding F_c
+        const int fn = (fs == m) ? m + 1 : m;    // slot for F_{c-1}
+        // ---- reflector U = I - tau v v^H on the m + 1 candidates of row c
+        //      (survivors 0..m-1, fresh fs): x U = conj(alpha) e_fs, x = row c.
+        if (tid < 32) {
+          double rest2 = 0.0;  // sum of |x_q|^2 over the m survivors
+          for (int q = tid; q < m; q += 32) {
+            const cd x = cand[q * kNB + c];
+            rest2 = fma(x.x, x.x, fma(x.y, x.y, rest2));
+          }
+          for (int o = 16; o > 0; o >>= 1) rest2 += __shfl_xor_sync(0xffffffffu, rest2, o);
+          const cd xf = cand[fs * kNB + c];
+          const double af2 = fma(xf.x, xf.x, xf.y * xf.y);
+          const double af = sqrt(af2);
+          const double nrm2 = rest2 + af2;
+          const double nrm = sqrt(nrm2);
+          // y = conj(x); alpha = -exp(i arg y_fs) ||y||; v = y - alpha e_fs
+          cd ph = af > 0.0 ? mkcd(xf.x / af, -xf.y / af) : mkcd(1.0, 0.0);
+          const cd alpha = mkcd(-ph.x * nrm, -ph.y * nrm);
+          const bool trivial = !(rest2 > 0.0);
+          for (int q = tid; q <= m; q += 32) {
+            const int slot = q < m ? q : fs;
+            const cd x = cand[slot * kNB + c];
+            cd v = mkcd(x.x, -x.y);
+            if (slot == fs) v = csub(v, alpha);
+            lmul[slot] = v;
+          }
+          if (tid == 0) {
+            // ||v||^2 = 2 ||y||^2 + 2 |y_fs| ||y||
+            const double vv = 2.0 * nrm2 + 2.0 * af * nrm;
+            lmul[MAXM + 2].x = trivial ? 0.0 : 2.0 / vv;
+            // finalised diagonal entry of row c: conj(alpha) (x_fs when no reflection)
+            lmul[MAXM + 3] = trivial ? xf : mkcd(alpha.x, -alpha.y);
+            if (nrm <= sing_tol) s_sing = 1;  // |R(row, row)| = ||x|| at working precision
+          }
+        }
+        __syncthreads();
+        const double tau = lmul[MAXM + 2].x;
+        // ---- apply to window rows 0..c-1 and the nonzero coefficient rows;
+        //      load F_{c-1} into slot fn meanwhile.
+        if (tau != 0.0) {
+          const int nrow = c;
+          const int ncoef = (nbe - c) + m;
+          for (int e = tid; e < nrow + ncoef; e += kThreads) {
+            cd* base;
+            int stride;
+            if (e < nrow) {
+              base = cand + e;
+              stride = kNB;
+            } else {
+              const int ee = e - nrow;
+              const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
+              base = coef + crow * S;
+              stride = 1;
+            }
+            cd w = mkcd(0.0, 0.0);
+            for (int q = 0; q <= m; ++q) {
+              const int slot = q < m ? q : fs;
+              w = cfma(base[slot * stride], lmul[slot], w);
+            }
+            w = mkcd(w.x * tau, w.y * tau);
+            for (int q = 0; q <= m; ++q) {
+              const int slot = q < m ? q : fs;
+              const cd vc = mkcd(lmul[slot].x, -lmul[slot].y);
+              base[slot * stride] = cfms(w, vc, base[slot * stride]);
+            }
+          }
+        }
+        if (RHS) {
+          // back substitution with the finalised column F_c (slot fs)
+          __syncthreads();
+          const cd beta = lmul[MAXM + 3];
+          const cd f = (beta.x == 0.0 && beta.y == 0.0) ? mkcd(0.0, 0.0) : cdiv(rhs_s[c], beta);
+          const int nrow = c;
+          const int ncoef = (nbe - c) + m;
+          for (int e = tid; e < nrow + ncoef; e += kThreads) {
+            if (e < nrow) {
+              rhs_s[e] = cfms(f, cand[fs * kNB + e], rhs_s[e]);
+            } else {
+              const int ee = e - nrow;
+              const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
+              coefr[crow] = cfms(f, coef[crow * S + fs], coefr[crow]);
+            }
+          }
+        }
+        if (c > 0) {
+          const int cn = c - 1, jc = j0 + cn;
+          for (int t = tid; t <= cn; t += kThreads) {
+            cd z = mkcd(H[(k - nbe + t) + (size_t)jc * n], 0.0);
+            if (t == cn - m) z = csub(z, sigma);
+            cand[fn * kNB + t] = z;
+          }
+          for (int crow = tid; crow < L::kCoefRows; crow += kThreads)
+            coef[crow * S + fn] = mkcd(crow == cn ? 1.0 : 0.0, 0.0);
+        }
+        __syncthreads();
+      }
     }
 
     // ---- update the rows above the block (and the T rows)
@@ -304,7 +425,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
       }
       for (int qq = 0; qq < m; ++qq) {
         const cd zz = Z2[i + (size_t)qq * ldz];
-        const cd* cr = coef + (kNB + qq) * S;
+        const cd* cr = coef + (LB + qq) * S;
 #pragma unroll
         for (int q = 0; q < MAXM; ++q)
           if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
@@ -347,7 +468,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
           for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
           for (int qq = 0; qq < m; ++qq) {
             const cd zz = ZT[i + (size_t)qq * n];
-            const cd* cr = coef + (kNB + qq) * S;
+            const cd* cr = coef + (LB + qq) * S;
 #pragma unroll
             for (int q = 0; q < MAXM; ++q)
               if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
@@ -487,6 +608,8 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
   d.R = R; d.shifts = shifts; d.out = out; d.ldo = ldo; d.status = status;
   d.xhat_copy = xhat_copy; d.ldxc = ldxc; d.hnorm = hnorm; d.bhat = bhat; d.ldb = ldb;
   d.rhs = nullptr; d.ldr = 0; d.flip_out = 0;
+  d.gfull = GivensSched{nullptr, nullptr, 0};
+  d.gtail = d.gfull;
   cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
   // With a work list, the block takes list entries blockIdx.x, +gridDim.x, ...
   const int nwork = list != nullptr ? *count : s;
@@ -494,6 +617,19 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
     const int sh = list != nullptr ? list[w] : w;
     fp64_shift<MAXM>(d, sh, Z2, smem_raw, &s_piv, &s_sing);
   }
+}
+
+// Givens-panel sweep (Sec. 3.2): the same work list as solve_fp64_kernel.
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) solve_fp64_givens_kernel(FpSys d, int s,
+                                                                     cd* __restrict__ scratch,
+                                                                     size_t slot_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_piv;
+  __shared__ int s_sing;
+  cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
+  for (int w = blockIdx.x; w < s; w += gridDim.x)
+    fp64_shift<MAXM, false, true>(d, w, Z2, smem_raw, &s_piv, &s_sing);
 }
 
 // Dense right-hand side per shift (the transposed systems of Sec. 3.3, in the
@@ -818,6 +954,8 @@ int solve_fp64_trans(const Handle* h, int s, const double* shifts, const double*
     d.out = reinterpret_cast<cd*>(out); d.ldo = ldo; d.status = status;
     d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2; d.bhat = nullptr; d.ldb = 0;
     d.rhs = dvec; d.ldr = n; d.flip_out = 1;
+    d.gfull = GivensSched{nullptr, nullptr, 0};
+    d.gtail = d.gfull;
     if (m <= 1) rc = launch_rhs<1>(d, s, st);
     else if (m <= 2) rc = launch_rhs<2>(d, s, st);
     else if (m <= 4) rc = launch_rhs<4>(d, s, st);
@@ -837,6 +975,167 @@ int solve_fp64_trans(const Handle* h, int s, const double* shifts, const double*
   }
   if (dvec) cudaFreeAsync(dvec, st);
   if (Ht) cudaFreeAsync(Ht, st);
+  return rc;
+}
+// ---------------------------------------------------------------------------
+// Givens panel (Sec. 3.2): greedy annihilation schedule of Algorithm 9 for a
+// block of `rows` rows and rows + m columns, computed on the host once per
+// shape and device and kept in device memory.
+//
+// Row r (0-based) of the block holds nonzeros in columns r .. rows + m - 1;
+// the entries (r, c), r <= c < r + m, are zeroed, each by a rotation with a
+// partner (r, c2), c2 <= r + m, so that (r, r + m) remains.  An entry may take
+// part in a step when it is "ready" (in the band, not zeroed, not already a
+// partner in this step) and "available": every entry of the bottom row and
+// every (r, r) from the start, the entry above a zeroed one from the step
+// after.  Each step scans rows bottom-up and, in a row, pairs each candidate
+// c1 (ascending) with the largest free partner c2 > c1.
+// ---------------------------------------------------------------------------
+void greedy_rows(int rows, int m, std::vector<int>* rot, std::vector<int>* off) {
+  const int w = m + 1;  // band width per row
+  std::vector<char> ready((size_t)rows * w, 1), avail((size_t)rows * w, 0);
+  auto at = [w](int r, int c) { return (size_t)r * w + (c - r); };
+  for (int r = 0; r < rows; ++r)
+    for (int c = r; c <= r + m; ++c) avail[at(r, c)] = (r == rows - 1 || c == r) ? 1 : 0;
+  std::vector<std::pair<int, int>> busy, zeroed;
+  rot->clear();
+  off->assign(1, 0);
+  for (;;) {
+    for (auto& b : busy) ready[at(b.first, b.second)] = 1;
+    for (auto& z : zeroed)
+      if (z.first > 0) avail[at(z.first - 1, z.second)] = 1;
+    busy.clear();
+    zeroed.clear();
+    for (int r = rows - 1; r >= 0; --r) {
+      for (int c1 = r; c1 <= r + m; ++c1) {
+        if (!(ready[at(r, c1)] && avail[at(r, c1)])) continue;
+        for (int c2 = r + m; c2 > c1; --c2) {
+          if (!(ready[at(r, c2)] && avail[at(r, c2)])) continue;
+          rot->push_back(r | (c1 << 8) | (c2 << 16));
+          ready[at(r, c1)] = 0;
+          ready[at(r, c2)] = 0;
+          busy.push_back({r, c2});
+          if (r > 0) avail[at(r - 1, c1)] = 0;
+          zeroed.push_back({r, c1});
+          break;
+        }
+      }
+    }
+    if ((int)rot->size() == off->back()) break;  // empty step: done
+    off->push_back((int)rot->size());
+  }
+}
+
+namespace {
+
+struct SchedEntry {
+  int* rot = nullptr;
+  int* off = nullptr;
+  int nsteps = 0;
+};
+std::mutex g_sched_mu;
+std::map<std::tuple<int, int, int>, SchedEntry> g_sched;  // (device, rows, m)
+
+int givens_schedule(int rows, int m, GivensSched* out) {
+  int dev = 0;
+  SSV_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_sched_mu);
+  auto key = std::make_tuple(dev, rows, m);
+  auto it = g_sched.find(key);
+  if (it == g_sched.end()) {
+    std::vector<int> rot, off;
+    greedy_rows(rows, m, &rot, &off);
+    SchedEntry e;
+    e.nsteps = (int)off.size() - 1;
+    SSV_CUDA_TRY(cudaMalloc((void**)&e.rot, sizeof(int) * std::max<size_t>(1, rot.size())));
+    SSV_CUDA_TRY(cudaMalloc((void**)&e.off, sizeof(int) * off.size()));
+    SSV_CUDA_TRY(cudaMemcpy(e.rot, rot.data(), sizeof(int) * rot.size(), cudaMemcpyHostToDevice));
+    SSV_CUDA_TRY(cudaMemcpy(e.off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+    it = g_sched.emplace(key, e).first;
+  }
+  *out = GivensSched{it->second.rot, it->second.off, it->second.nsteps};
+  return SSV_OK;
+}
+
+template <int MAXM>
+int launch_givens(const FpSys& d, int s, cudaStream_t st) {
+  using GL = GivensLayout<MAXM>;
+  const bool track_t = (d.mode == SSV_XHAT || d.mode == SSV_X || d.xhat_copy != nullptr);
+  const size_t slot = (size_t)(d.p + d.n) * d.m + (track_t ? (size_t)d.n * d.m : 0);
+  auto kern = solve_fp64_givens_kernel<MAXM>;
+  SSV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GL::bytes));
+  int per_sm = 0;
+  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, GL::bytes));
+  per_sm = std::max(1, std::min(per_sm, 2));
+  const int grid = std::min(s, num_sms() * per_sm);
+  cd* scratch = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(cd) * slot * grid, st));
+  kern<<<grid, kThreads, GL::bytes, st>>>(d, s, scratch, slot);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return SSV_ECUDA;
+  }
+  return SSV_OK;
+}
+
+}  // namespace
+
+int solve_fp64_givens(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
+                      long long ldo, int* status, double* resid, cudaStream_t st) {
+  const int n = h->n, m = h->m, p = h->p;
+  const int nb = o->nb > 0 ? o->nb : kNBG;
+  if (nb > kNBG || m > 32) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  const int mode = o->mode == SSV_X ? SSV_XHAT : o->mode;
+  FpSys d;
+  d.n = n; d.m = m; d.p = p; d.nb = nb; d.mode = mode; d.H = h->H; d.Ct = h->Ct;
+  d.ldct = p > 0 ? p : 1; d.R = h->R; d.shifts = reinterpret_cast<const cd*>(shifts);
+  d.out = reinterpret_cast<cd*>(out); d.ldo = ldo; d.status = status;
+  d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2; d.bhat = nullptr; d.ldb = 0;
+  d.rhs = nullptr; d.ldr = 0; d.flip_out = 0;
+  d.gfull = GivensSched{nullptr, nullptr, 0};
+  d.gtail = d.gfull;
+  const int tail = (n - m) % nb;
+  int rc = SSV_OK;
+  if (n > m) {
+    rc = givens_schedule(std::min(nb, n - m), m, &d.gfull);
+    if (rc == SSV_OK && tail != 0 && n - m > nb) rc = givens_schedule(tail, m, &d.gtail);
+    if (rc == SSV_OK && n - m <= nb) d.gtail = d.gfull;
+  }
+  if (rc != SSV_OK) return rc;
+  cd* xcopy = nullptr;
+  if (resid != nullptr && (mode == SSV_G || mode == SSV_TF)) {
+    SSV_CUDA_TRY(cudaMallocAsync((void**)&xcopy, sizeof(cd) * (size_t)n * m * s, st));
+    d.xhat_copy = xcopy;
+    d.ldxc = n;
+  }
+  if (m <= 1) rc = launch_givens<1>(d, s, st);
+  else if (m <= 2) rc = launch_givens<2>(d, s, st);
+  else if (m <= 4) rc = launch_givens<4>(d, s, st);
+  else if (m <= 8) rc = launch_givens<8>(d, s, st);
+  else if (m <= 16) rc = launch_givens<16>(d, s, st);
+  else rc = launch_givens<32>(d, s, st);
+  if (rc == SSV_OK && status != nullptr) {
+    const int rows = (mode == SSV_G || mode == SSV_TF) ? p : n;
+    if (rows > 0) {
+      nonfinite_kernel<<<s, 256, 0, st>>>(reinterpret_cast<const cd*>(out), ldo, rows, m, s, status);
+      count_launch();
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        set_cuda_error(e);
+        rc = SSV_ECUDA;
+      }
+    }
+  }
+  if (rc == SSV_OK && resid != nullptr) {
+    const double* xh = xcopy ? reinterpret_cast<const double*>(xcopy) : out;
+    rc = backward_error_fp64(h, s, shifts, xh, xcopy ? n : ldo, resid, st);
+  }
+  if (xcopy) cudaFreeAsync(xcopy, st);
   return rc;
 }
 
@@ -1012,6 +1311,8 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
     d.status = status ? status[k] : nullptr;
     d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2; d.bhat = nullptr; d.ldb = 0;
     d.rhs = nullptr; d.ldr = 0; d.flip_out = 0;
+    d.gfull = GivensSched{nullptr, nullptr, 0};
+    d.gtail = d.gfull;
     bp->maxm = std::max(bp->maxm, h->m);
     bp->slot = std::max(bp->slot, (size_t)(h->p + h->n) * h->m + (track_t ? (size_t)h->n * h->m : 0));
     const double cost = (double)h->n * h->n * h->m * (1.0 + 2.0 * h->m / d.nb);

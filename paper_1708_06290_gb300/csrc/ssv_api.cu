@@ -51,6 +51,7 @@ static int check_opts(const ssv_opts* o) {
   if (o->precision != SSV_FP64 && o->precision != SSV_MIXED) return SSV_EINVAL;
   if (o->mode < SSV_G || o->mode > SSV_X) return SSV_EINVAL;
   if (o->nb < 0 || o->tile < 0 || o->max_refine < 0 || !(o->tol >= 0.0)) return SSV_EINVAL;
+  if (o->panel != SSV_PANEL_HOUSEHOLDER && o->panel != SSV_PANEL_GIVENS) return SSV_EINVAL;
   return SSV_OK;
 }
 
@@ -68,6 +69,7 @@ void ssv_default_opts(ssv_opts* o) {
   o->tile = 0;
   o->max_refine = 8;
   o->tol = 1e-14;
+  o->panel = SSV_PANEL_HOUSEHOLDER;
 }
 
 static int make_handle(int n, int m, int p, cudaStream_t st, Handle** out) {
@@ -167,7 +169,12 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
   if (!gmode && ldo < h->n) return SSV_EINVAL;
   if (o.mode == SSV_X && !h->has_q) return SSV_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
-  if (o.precision == SSV_MIXED) {
+  if (o.panel == SSV_PANEL_GIVENS) {
+    if (o.precision != SSV_FP64) return SSV_ENOTSUP;
+    void* tr = trace_begin("solve_fp64_givens", st);
+    rc = solve_fp64_givens(h, s, shifts, &o, out, ldo, status, resid, st);
+    trace_end(tr, st);
+  } else if (o.precision == SSV_MIXED) {
     rc = solve_mixed(h, s, shifts, &o, out, ldo, status, resid, st);
   } else {
     void* tr = trace_begin("solve_fp64", st);
@@ -221,6 +228,23 @@ int ssv_solve_trans(ssv_handle hh, int s, const double* shifts, const double* ch
   trace_end(tr, st);
   if (rc == SSV_OK && o.mode == SSV_X) rc = apply_q_fp64(h, s, out, ldo, out, ldo, st);
   return rc;
+}
+
+int ssv_givens_schedule(int rows, int m, int* rot, int max_rot, int* off, int max_steps,
+                        int* nsteps) {
+  if (rows < 1 || m < 1 || rows > 255 || rows + m > 255 || !rot || !off || !nsteps) return SSV_EINVAL;
+  std::vector<int> r, o;
+  greedy_rows(rows, m, &r, &o);
+  const int ns = (int)o.size() - 1;
+  if ((int)r.size() > max_rot || ns > max_steps) return SSV_EINVAL;
+  for (size_t j = 0; j < r.size(); ++j) {
+    rot[3 * j] = (r[j] & 255) + 1;
+    rot[3 * j + 1] = ((r[j] >> 8) & 255) + 1;
+    rot[3 * j + 2] = ((r[j] >> 16) & 255) + 1;
+  }
+  for (int t = 0; t <= ns; ++t) off[t] = o[t];
+  *nsteps = ns;
+  return (int)r.size();
 }
 
 static int check_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,

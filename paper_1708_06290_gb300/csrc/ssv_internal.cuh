@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "ssv.h"
 
 namespace ssv {
@@ -102,6 +104,12 @@ int solve_fp64_rhs(const Handle* h, int s, const double* shifts, const double* b
 int solve_fp64_trans(const Handle* h, int s, const double* shifts, const double* chat,
                      long long ldc, const ssv_opts* o, double* out, long long ldo, int* status,
                      cudaStream_t st);
+// FP64 sweep with the Givens panel and greedy schedule (Sec. 3.2); n_b <= 32
+int solve_fp64_givens(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
+                      long long ldo, int* status, double* resid, cudaStream_t st);
+// greedy annihilation schedule (Algorithm 9) of a block with `rows` rows and rows + m
+// columns: rotations packed r | c1 << 8 | c2 << 16 (0-based), step t = off[t] .. off[t+1]-1
+void greedy_rows(int rows, int m, std::vector<int>* rot, std::vector<int>* off);
 // FP64 solve restricted to the shifts with mask[j] != 0 (others untouched)
 int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, int nb,
                       double* out, long long ldo, int* status, const int* mask, void* xhat_copy,

@@ -50,7 +50,8 @@ class SsvError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("nb", ctypes.c_int),
-                ("tile", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("tile", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
+                ("panel", ctypes.c_int)]
 
 
 EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced",
@@ -58,7 +59,7 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc", "ssv_solve_many",
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
            "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
-           "ssv_solve_rhs", "ssv_solve_trans")
+           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule")
 
 _lib = None
 
@@ -89,6 +90,7 @@ def load(build_if_missing=True):
     L.ssv_solve_noalloc.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P]
     L.ssv_solve_rhs.argtypes = [P, I, P, P, LL, ctypes.POINTER(Opts), P, LL, P, P]
     L.ssv_solve_trans.argtypes = [P, I, P, P, LL, ctypes.POINTER(Opts), P, LL, P, P]
+    L.ssv_givens_schedule.argtypes = [I, I, P, I, P, I, ctypes.POINTER(I)]
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.ssv_solve_many.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
                                  ctypes.POINTER(LL), PP, P]
@@ -106,7 +108,7 @@ def load(build_if_missing=True):
     L.ssv_trace_read.argtypes = [I, ctypes.c_char_p, I, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(I), ctypes.POINTER(I)]
     for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
-           "ssv_solve_rhs", "ssv_solve_trans"):
+           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule"):
         getattr(L, f).restype = I
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
@@ -170,7 +172,10 @@ def _need_cuda(t, dtype, name):
         raise ValueError("%s must be %s" % (name, dtype))
 
 
-def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-14):
+_PANELS = {"householder": 0, "givens": 1}
+
+
+def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-14, panel="householder"):
     o = Opts()
     load().ssv_default_opts(ctypes.byref(o))
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
@@ -179,7 +184,22 @@ def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-14):
     o.tile = tile
     o.max_refine = max_refine
     o.tol = tol
+    o.panel = _PANELS[panel] if isinstance(panel, str) else int(panel)
     return o
+
+
+def givens_schedule(rows, m):
+    """The library's greedy Givens schedule (Algorithm 9) for a rows x (rows + m)
+    block: list of steps, each a list of (r, c1, c2), 1-based.  Host only."""
+    L = load()
+    nrot = rows * m
+    rot = (ctypes.c_int * (3 * max(nrot, 1)))()
+    off = (ctypes.c_int * (nrot + 2))()
+    ns = ctypes.c_int()
+    rc = L.ssv_givens_schedule(rows, m, ctypes.cast(rot, ctypes.c_void_p), nrot,
+                               ctypes.cast(off, ctypes.c_void_p), nrot + 1, ctypes.byref(ns))
+    _check(min(rc, 0), "ssv_givens_schedule")
+    return [[tuple(rot[3 * j:3 * j + 3]) for j in range(off[t], off[t + 1])] for t in range(ns.value)]
 
 
 class Handle:
@@ -211,7 +231,7 @@ class Handle:
         return self.p if _MODES.get(mode, mode) in (G, TF) else self.n
 
     def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=8, tol=1e-14,
-              out=None, status=None, resid=None, want_resid=False, stream=None):
+              out=None, status=None, resid=None, want_resid=False, stream=None, panel="householder"):
         """Solve all shifts.  Returns (out, status, resid).
 
         out is a column-major complex128 (rows, s*m) tensor, rows = p for
@@ -220,7 +240,7 @@ class Handle:
         L = load()
         _need_cuda(shifts, torch.complex128, "shifts")
         s = shifts.numel()
-        o = opts(precision, mode, nb, tile, max_refine, tol)
+        o = opts(precision, mode, nb, tile, max_refine, tol, panel)
         rows = self.out_rows(o.mode)
         dev = shifts.device
         if out is None:
