@@ -55,6 +55,12 @@ extern "C" {
 /* ---- options ----------------------------------------------------------- */
 #define SSV_FP64 0  /* every step in double / complex128 */
 #define SSV_MIXED 1 /* complex64 elimination + FP64-accurate refinement */
+#define SSV_DFLOAT 2 /* FP64 panels; the bulk updates of the rows above each block
+                        (the Z1 P1 and Z2 P2 products, most of the work) in
+                        double-float arithmetic on the FP32 pipe: pairs of FP32
+                        words, exact FMA products, two-sum accumulation (about 48
+                        significant bits; no refinement).  Entries must be within
+                        the FP32 exponent range.  ssv_solve only. */
 
 #define SSV_G 0    /* out(p x m) = C X = Ct Xhat                             */
 #define SSV_TF 1   /* out(p x m) = C (sigma I - A)^{-1} B = -Ct Xhat (Sec. 2) */

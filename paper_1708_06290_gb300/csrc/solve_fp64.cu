@@ -109,6 +109,8 @@ struct FpSys {
   const cd* rhs;     // dense right-hand sides (n x s, ld ldr) of an RHS sweep (p == 0)
   long long ldr;
   int flip_out;      // write output row i to row n-1-i (transposed systems)
+  const float* Hhi;   // double-float split of H (SSV_DFLOAT updates)
+  const float* Hlo;
   GivensSched gfull;  // Givens panel: schedule of full blocks (n_b rows)
   GivensSched gtail;  // and of the last, shorter block
 };
@@ -120,7 +122,7 @@ struct FpSys {
 // as it is produced, bottom-up), the rows above the block through the
 // accumulated coefficients `coefr`; the solution is T(:, live) y - Tr with Tr
 // the T rows of sum_c (-f_c) F_c and y from the final m x m block.
-template <int MAXM, bool RHS = false, bool GIVENS = false>
+template <int MAXM, bool RHS = false, bool GIVENS = false, bool DF = false>
 __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
                            unsigned char* smem_raw, int* s_piv_p, int* s_sing_p) {
   using L = Layout<MAXM>;
@@ -403,6 +405,102 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     }
 
     // ---- update the rows above the block (and the T rows)
+    if constexpr (DF) {
+      // double-float update (SSV_DFLOAT): the coefficients as FP32 pairs
+      // (re_hi, re_lo, im_hi, im_lo) in place, H as (Hhi, Hlo), Z2 split on the
+      // fly; exact FMA products, two-sum accumulation (48-bit class).  The Ct
+      // rows and the diagonal correction stay in FP64.
+      __syncthreads();
+      for (int idx = tid; idx < CR * S; idx += kThreads) {
+        const cd v = coef[idx];
+        const float rh = (float)v.x, ih = (float)v.y;
+        reinterpret_cast<float4*>(coef)[idx] =
+            make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+      }
+      __syncthreads();
+    }
+    auto coefd = [&](int crow, int q) -> cd {
+      if constexpr (DF) {
+        const float4 w = reinterpret_cast<const float4*>(coef)[crow * S + q];
+        return mkcd((double)w.x + (double)w.y, (double)w.z + (double)w.w);
+      } else {
+        return coef[crow * S + q];
+      }
+    };
+    if constexpr (DF) {
+      const float4* cf4 = reinterpret_cast<const float4*>(coef);
+      for (int i = tid; i < r; i += kThreads) {
+        cd acc[MAXM];
+        if (i < p) {
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
+          for (int c = 0; c < nbe; ++c) {
+            const double z = Ct[i + (size_t)(j0 + c) * ldct];
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) {
+              if (q < m) {
+                const cd w = coefd(c, q);
+                acc[q].x = fma(z, w.x, acc[q].x);
+                acc[q].y = fma(z, w.y, acc[q].y);
+              }
+            }
+          }
+          for (int qq = 0; qq < m; ++qq) {
+            const cd zz = Z2[i + (size_t)qq * ldz];
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q)
+              if (q < m) acc[q] = cfma(zz, coefd(LB + qq, q), acc[q]);
+          }
+        } else {
+          float rh[MAXM], rl[MAXM], ih[MAXM], il[MAXM];
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q) { rh[q] = 0.f; rl[q] = 0.f; ih[q] = 0.f; il[q] = 0.f; }
+          const size_t row = (size_t)(i - p);
+          for (int c = 0; c < nbe; ++c) {
+            const size_t hidx = row + (size_t)(j0 + c) * n;
+            const float zh = d.Hhi[hidx], zl = d.Hlo[hidx];
+            const float4* cr = cf4 + c * S;
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) {
+              if (q < m) {
+                const float4 w = cr[q];
+                df_mac(rh[q], rl[q], zh, zl, w.x, w.y);
+                df_mac(ih[q], il[q], zh, zl, w.z, w.w);
+              }
+            }
+          }
+          for (int qq = 0; qq < m; ++qq) {
+            const cd zz = Z2[i + (size_t)qq * ldz];
+            const float zrh = (float)zz.x, zrl = (float)(zz.x - (double)zrh);
+            const float zih = (float)zz.y, zil = (float)(zz.y - (double)zih);
+            const float4* cr = cf4 + (LB + qq) * S;
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) {
+              if (q < m) {
+                const float4 w = cr[q];
+                // (zr + i zi)(wr + i wi) = (zr wr - zi wi) + i (zr wi + zi wr)
+                df_mac(rh[q], rl[q], zrh, zrl, w.x, w.y);
+                df_mac(rh[q], rl[q], -zih, -zil, w.z, w.w);
+                df_mac(ih[q], il[q], zrh, zrl, w.z, w.w);
+                df_mac(ih[q], il[q], zih, zil, w.x, w.y);
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            acc[q] = mkcd((double)rh[q] + (double)rl[q], (double)ih[q] + (double)il[q]);
+        }
+        const int cd_ = i - (r - m);  // diagonal correction of fresh column cd_
+        if (cd_ >= 0 && cd_ < min(m, nbe)) {
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            if (q < m) acc[q] = cfms(sigma, coefd(cd_, q), acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q < m) Z2[i + (size_t)q * ldz] = acc[q];
+      }
+    } else
     for (int i = tid; i < r; i += kThreads) {
       cd acc[MAXM];
       cd racc = mkcd(0.0, 0.0);
@@ -460,18 +558,16 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
           Tr[i] = tr;
         }
         if (i < lo) {
-          const cd* cr = coef + (i - j0) * S;
 #pragma unroll
-          for (int q = 0; q < MAXM; ++q) acc[q] = cr[q];
+          for (int q = 0; q < MAXM; ++q) acc[q] = coefd(i - j0, q);
         } else {
 #pragma unroll
           for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);
           for (int qq = 0; qq < m; ++qq) {
             const cd zz = ZT[i + (size_t)qq * n];
-            const cd* cr = coef + (LB + qq) * S;
 #pragma unroll
             for (int q = 0; q < MAXM; ++q)
-              if (q < m) acc[q] = cfma(zz, cr[q], acc[q]);
+              if (q < m) acc[q] = cfma(zz, coefd(LB + qq, q), acc[q]);
           }
         }
 #pragma unroll
@@ -592,14 +688,15 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   __syncthreads();
 }
 
-template <int MAXM>
+template <int MAXM, bool DF = false>
 __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
     int n, int m, int p, int nb, const double* __restrict__ H, const double* __restrict__ Ct,
     int ldct, const double* __restrict__ R, int s, const cd* __restrict__ shifts, int mode,
     cd* __restrict__ scratch, size_t slot_stride, cd* __restrict__ out, long long ldo,
     int* __restrict__ status, cd* __restrict__ xhat_copy, long long ldxc,
     const double* __restrict__ hnorm, const int* __restrict__ list,
-    const int* __restrict__ count, const cd* __restrict__ bhat, long long ldb) {
+    const int* __restrict__ count, const cd* __restrict__ bhat, long long ldb,
+    const float* __restrict__ Hhi, const float* __restrict__ Hlo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_piv;
   __shared__ int s_sing;
@@ -608,6 +705,7 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
   d.R = R; d.shifts = shifts; d.out = out; d.ldo = ldo; d.status = status;
   d.xhat_copy = xhat_copy; d.ldxc = ldxc; d.hnorm = hnorm; d.bhat = bhat; d.ldb = ldb;
   d.rhs = nullptr; d.ldr = 0; d.flip_out = 0;
+  d.Hhi = Hhi; d.Hlo = Hlo;
   d.gfull = GivensSched{nullptr, nullptr, 0};
   d.gtail = d.gfull;
   cd* Z2 = scratch + (size_t)blockIdx.x * slot_stride;
@@ -615,7 +713,7 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
   const int nwork = list != nullptr ? *count : s;
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int sh = list != nullptr ? list[w] : w;
-    fp64_shift<MAXM>(d, sh, Z2, smem_raw, &s_piv, &s_sing);
+    fp64_shift<MAXM, false, false, DF>(d, sh, Z2, smem_raw, &s_piv, &s_sing);
   }
 }
 
@@ -722,7 +820,7 @@ __global__ void nonfinite_kernel(const cd* __restrict__ out, long long ldo, int 
   if (threadIdx.x == 0 && bad && status[sh] == SSV_SHIFT_OK) status[sh] = SSV_SHIFT_NONFINITE;
 }
 
-template <int MAXM>
+template <int MAXM, bool DF = false>
 int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode, double* out,
                  long long ldo, int* status, cd* xhat_copy, long long ldxc, cudaStream_t st,
                  const int* list = nullptr, const int* count = nullptr,
@@ -733,7 +831,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
   const size_t slot = (size_t)(p + n) * m + (track_t ? (size_t)n * m : 0);
   int dev = 0;
   SSV_CUDA_TRY(cudaGetDevice(&dev));
-  auto kern = solve_fp64_kernel<MAXM>;
+  auto kern = solve_fp64_kernel<MAXM, DF>;
   SSV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
   int per_sm = 0;
   SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L::bytes));
@@ -744,7 +842,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
   kern<<<grid, kThreads, L::bytes, st>>>(n, m, p, nb, h->H, h->Ct, p > 0 ? p : 1, h->R, s,
                                          reinterpret_cast<const cd*>(shifts), mode, scratch, slot,
                                          reinterpret_cast<cd*>(out), ldo, status, xhat_copy, ldxc,
-                                         h->hnorm2, list, count, bhat, ldb);
+                                         h->hnorm2, list, count, bhat, ldb, h->Hhi, h->Hlo);
   count_launch();
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaFreeAsync(scratch, st);
@@ -838,7 +936,7 @@ size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) {
 int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                long long ldo, int* status, double* resid, cudaStream_t st) {
   const int m = h->m;
-  int nb = o->nb > 0 ? o->nb : tuned_nb(h->n, m, h->p, SSV_FP64, o->mode);
+  int nb = o->nb > 0 ? o->nb : tuned_nb(h->n, m, h->p, o->precision, o->mode);
   if (nb > kNB) return SSV_ENOTSUP;
   if (s == 0) return SSV_OK;
   cd* xcopy = nullptr;
@@ -848,13 +946,23 @@ int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, 
     SSV_CUDA_TRY(cudaMallocAsync((void**)&xcopy, sizeof(cd) * (size_t)h->n * m * s, st));
   }
   int rc;
-  if (m <= 1) rc = launch_solve<1>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
-  else if (m <= 2) rc = launch_solve<2>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
-  else if (m <= 4) rc = launch_solve<4>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
-  else if (m <= 8) rc = launch_solve<8>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
-  else if (m <= 16) rc = launch_solve<16>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
-  else if (m <= 32) rc = launch_solve<32>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
-  else rc = SSV_ENOTSUP;
+  if (o->precision == SSV_DFLOAT) {
+    if (m <= 1) rc = launch_solve<1, true>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 2) rc = launch_solve<2, true>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 4) rc = launch_solve<4, true>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 8) rc = launch_solve<8, true>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 16) rc = launch_solve<16, true>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 32) rc = launch_solve<32, true>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else rc = SSV_ENOTSUP;
+  } else {
+    if (m <= 1) rc = launch_solve<1>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 2) rc = launch_solve<2>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 4) rc = launch_solve<4>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 8) rc = launch_solve<8>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 16) rc = launch_solve<16>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else if (m <= 32) rc = launch_solve<32>(h, s, shifts, nb, o->mode, out, ldo, status, xcopy, ldxc, st);
+    else rc = SSV_ENOTSUP;
+  }
   if (rc == SSV_OK && resid != nullptr) {
     const double* xh = xcopy ? reinterpret_cast<const double*>(xcopy) : out;
     long long ldx = xcopy ? ldxc : ldo;
@@ -1203,7 +1311,7 @@ int launch_solve_noalloc(const Handle* h, int s, const double* shifts, int nb, i
                                          reinterpret_cast<const cd*>(shifts), mode,
                                          reinterpret_cast<cd*>(base), slot,
                                          reinterpret_cast<cd*>(out), ldo, status, nullptr, 0,
-                                         h->hnorm2, nullptr, nullptr, nullptr, 0);
+                                         h->hnorm2, nullptr, nullptr, nullptr, 0, nullptr, nullptr);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   if (status != nullptr) {

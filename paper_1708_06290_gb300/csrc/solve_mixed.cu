@@ -98,20 +98,6 @@ struct Smem {
   }
 };
 
-// s = s_hi + s_lo accumulates a_hi*b_hi exactly (FMA error term) plus the FP32
-// cross terms a_hi*b_lo + a_lo*b_hi; the high sum is kept with two-sum.
-__device__ __forceinline__ void df_mac(float& s_hi, float& s_lo, float a_hi, float a_lo, float b_hi,
-                                       float b_lo) {
-  const float p = a_hi * b_hi;
-  const float e = fmaf(a_hi, b_hi, -p);
-  const float t = fmaf(a_hi, b_lo, fmaf(a_lo, b_hi, e));
-  const float s = s_hi + p;
-  const float bp = s - s_hi;
-  const float err = (s_hi - (s - bp)) + (p - bp);
-  s_hi = s;
-  s_lo += err + t;
-}
-
 // Block-wide sum of two doubles; every thread gets the totals.
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
   for (int o = 16; o > 0; o >>= 1) {

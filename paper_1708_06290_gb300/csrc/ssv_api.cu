@@ -48,7 +48,8 @@ static size_t handle_bytes(int n, int m, int p) {
 }
 
 static int check_opts(const ssv_opts* o) {
-  if (o->precision != SSV_FP64 && o->precision != SSV_MIXED) return SSV_EINVAL;
+  if (o->precision != SSV_FP64 && o->precision != SSV_MIXED && o->precision != SSV_DFLOAT)
+    return SSV_EINVAL;
   if (o->mode < SSV_G || o->mode > SSV_X) return SSV_EINVAL;
   if (o->nb < 0 || o->tile < 0 || o->max_refine < 0 || !(o->tol >= 0.0)) return SSV_EINVAL;
   if (o->panel != SSV_PANEL_HOUSEHOLDER && o->panel != SSV_PANEL_GIVENS) return SSV_EINVAL;
@@ -177,7 +178,7 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
   } else if (o.precision == SSV_MIXED) {
     rc = solve_mixed(h, s, shifts, &o, out, ldo, status, resid, st);
   } else {
-    void* tr = trace_begin("solve_fp64", st);
+    void* tr = trace_begin(o.precision == SSV_DFLOAT ? "solve_dfloat" : "solve_fp64", st);
     rc = solve_fp64(h, s, shifts, &o, out, ldo, status, resid, st);
     trace_end(tr, st);
   }

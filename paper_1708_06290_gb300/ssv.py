@@ -29,6 +29,7 @@ SHIFT_NONFINITE = 3
 
 FP64 = 0
 MIXED = 1
+DFLOAT = 2
 
 G = 0
 TF = 1
@@ -36,7 +37,7 @@ XHAT = 2
 X = 3
 
 _MODES = {"g": G, "tf": TF, "xhat": XHAT, "x": X}
-_PREC = {"fp64": FP64, "mixed": MIXED}
+_PREC = {"fp64": FP64, "mixed": MIXED, "dfloat": DFLOAT}
 
 
 class SsvError(RuntimeError):

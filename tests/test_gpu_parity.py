@@ -257,3 +257,45 @@ def test_bounded_barrier_times_out_and_device_stays_usable():
     out, st, _ = h.solve(shifts_dev([0.5j]), mode="g")
     X, _ = oracle.dense_solve(sysr.A, sysr.B, [0.5j])
     assert relerr(blocks(out, 2)[0], oracle.transfer(sysr.C, X)[0]) < REL_TOL
+
+
+# --------------------------------------------------------------------------
+# double-float bulk updates (SSV_DFLOAT): FP64 panels, the updates of the rows
+# above each block in FP32 pairs (48-bit class, no refinement)
+# --------------------------------------------------------------------------
+
+def test_dfloat_small_workload_all_shifts():
+    sysr, sig = W.workload_small()
+    h = gpu_system(sysr)
+    _check_against_dense(sysr, sig, h, precision="dfloat")
+
+
+@pytest.mark.parametrize("n,m,p,nb", [(517, 3, 2, 64), (200, 8, 4, 16), (333, 16, 3, 0),
+                                      (260, 32, 2, 64), (129, 1, 1, 64), (97, 8, 3, 5), (13, 12, 2, 4)])
+def test_dfloat_ragged_sizes(n, m, p, nb):
+    sysr = W.random_system(n, m, p, seed=950 + n + nb)
+    sig = np.concatenate([W.imag_axis_logspace(-2, 2, 5), [-1.7 + 0.4j, -2.6 - 0.2j, 0.3 + 0.1j]])
+    h = gpu_system(sysr)
+    _check_against_dense(sysr, sig, h, nb=nb, precision="dfloat")
+
+
+def test_dfloat_precision_workload_sampled():
+    """n = 5000, m = p = 16, all 2000 grid shifts with double-float updates: every
+    backward error <= 1e-12 and the sampled shifts match the oracle."""
+    sysr, sig = W.workload_precision()
+    h = gpu_system(sysr)
+    out, status, resid = h.solve(shifts_dev(sig), mode="g", precision="dfloat", want_resid=True)
+    G = blocks(out, sysr.m)
+    st = status.cpu().numpy()
+    assert (st == 0).all()
+    assert resid.cpu().numpy().max() <= BWD_TOL
+    inside = np.where(np.abs(sig + 2.0) < 1.0)[0]
+    idx = np.concatenate([np.linspace(0, len(sig) - 1, 8).astype(int), inside[:: max(1, len(inside) // 8)][:8]])
+    Ho, Ro, Co, _ = oracle.reduce(sysr.A, sysr.B, sysr.C)
+    Go, sto, cond = oracle.reduced_solve(Ho, Ro, Co, sig[idx], want="g", cond=True)
+    checked = 0
+    for k, j in enumerate(idx):
+        if cond[k] <= KAPPA_GATE:
+            assert relerr(G[j], Go[k]) < REL_TOL, (j, cond[k])
+            checked += 1
+    assert checked >= 8
