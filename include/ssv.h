@@ -59,8 +59,10 @@ extern "C" {
                         (the Z1 P1 and Z2 P2 products, most of the work) in
                         double-float arithmetic on the FP32 pipe: pairs of FP32
                         words, exact FMA products, two-sum accumulation (about 48
-                        significant bits; no refinement).  Entries must be within
-                        the FP32 exponent range.  ssv_solve only. */
+                        significant bits; no refinement).  A shift is reported
+                        singular when a finalised diagonal entry is <= n 2^-47
+                        ||H - sigma I||_F.  Entries must be within the FP32
+                        exponent range.  ssv_solve only. */
 
 #define SSV_G 0    /* out(p x m) = C X = Ct Xhat                             */
 #define SSV_TF 1   /* out(p x m) = C (sigma I - A)^{-1} B = -Ct Xhat (Sec. 2) */
@@ -85,7 +87,9 @@ typedef struct ssv_opts {
 typedef struct ssv_handle_s* ssv_handle;
 
 /* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 8,
- * tol = 1e-14, panel = SSV_PANEL_HOUSEHOLDER. */
+ * tol = 1e-13, panel = SSV_PANEL_HOUSEHOLDER.  (The mixed path certifies each
+ * shift with a double-float residual whose own error is about 1e-14 of
+ * ||H - sigma I|| ||Xhat||; 1e-13 leaves a 10x margin above it.) */
 void ssv_default_opts(ssv_opts* o);
 
 /*

@@ -164,7 +164,8 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   // of magnitude <= n eps ||H - sigma I||_F marks the shift singular.
   const double mnorm2 = fmax(hnorm[0] - 2.0 * sigma.x * hnorm[1] +
                                  (double)n * (sigma.x * sigma.x + sigma.y * sigma.y), 0.0);
-  const double sing_tol = (double)n * 2.220446049250313e-16 * sqrt(mnorm2);
+  // (with double-float bulk updates the working precision is 2^-47)
+  const double sing_tol = (double)n * (DF ? 7.105427357601002e-15 : 2.220446049250313e-16) * sqrt(mnorm2);
   // ---- shift setup: Z2 = last m columns of [Ct; H] - sigma on the diagonal
   for (long long idx = tid; idx < (long long)ldz * m; idx += kThreads) {
     int i = (int)(idx % ldz), q = (int)(idx / ldz);
@@ -560,6 +561,29 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
         if (i < lo) {
 #pragma unroll
           for (int q = 0; q < MAXM; ++q) acc[q] = coefd(i - j0, q);
+        } else if constexpr (DF) {
+          float rh[MAXM], rl[MAXM], ih[MAXM], il[MAXM];
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q) { rh[q] = 0.f; rl[q] = 0.f; ih[q] = 0.f; il[q] = 0.f; }
+          for (int qq = 0; qq < m; ++qq) {
+            const cd zz = ZT[i + (size_t)qq * n];
+            const float zrh = (float)zz.x, zrl = (float)(zz.x - (double)zrh);
+            const float zih = (float)zz.y, zil = (float)(zz.y - (double)zih);
+            const float4* cr = reinterpret_cast<const float4*>(coef) + (LB + qq) * S;
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) {
+              if (q < m) {
+                const float4 w = cr[q];
+                df_mac(rh[q], rl[q], zrh, zrl, w.x, w.y);
+                df_mac(rh[q], rl[q], -zih, -zil, w.z, w.w);
+                df_mac(ih[q], il[q], zrh, zrl, w.z, w.w);
+                df_mac(ih[q], il[q], zih, zil, w.x, w.y);
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            acc[q] = mkcd((double)rh[q] + (double)rl[q], (double)ih[q] + (double)il[q]);
         } else {
 #pragma unroll
           for (int q = 0; q < MAXM; ++q) acc[q] = mkcd(0.0, 0.0);

@@ -1,22 +1,22 @@
-// Mixed-precision shifted solve: complex64 elimination sweeps with iterative
-// refinement whose residual R - (H - sigma I) Xhat is computed FP64-accurately.
+// Mixed-precision shifted solve: a first solve with double-float bulk updates,
+// then iterative refinement with complex64 correction sweeps whose residual
+// R - (H - sigma I) Xhat is computed FP64-accurately.
 //
-// Per shift, one thread block runs
-//   1. sweep 0: the blocked bottom-up window elimination of Sec. 3.1 /
-//      Algorithm 8 in complex64 (one Householder reflector per row over the m
-//      live + 1 fresh candidate columns), carrying the rows of the accumulated
-//      column transformation T (the "Q*" rows of Sec. 3.3), so that
-//      Xhat0 = T(:, live) Wm^{-1} R(1:m, 1:m) is formed (stored in complex128);
+// Per shift:
+//   1. first solve: the FP64 sweep of Sec. 3.1 / Algorithm 8 with its bulk
+//      updates (the rows above each block) in double-float on the FP32 pipe
+//      (SSV_DFLOAT), carrying the rows of the accumulated column
+//      transformation T (the "Q*" rows of Sec. 3.3) so that Xhat0 is formed;
 //   2. refinement: E = R - (H - sigma I) Xhat with H = Hhi + Hlo (two FP32
 //      words) and Xhat split the same way, each product formed exactly by an
 //      FMA and accumulated in double-float (Dekker/Knuth two-sum), giving
 //      ~48-bit residuals at FP32 throughput (native FP64 is 60x slower on
 //      this GPU); the normwise backward error decides convergence;
-//   3. a correction sweep solves (H - sigma I) D = E for the dense right-hand
-//      side E by carrying E as extra window columns that are back-substituted
-//      on the fly with each finalised column (the technique of Sec. 3.3 for
-//      unreduced right-hand sides, here in the bottom-up RQ direction), and
-//      Xhat += D.
+//   3. a correction sweep in complex64 solves (H - sigma I) D = E for the dense
+//      right-hand side E by carrying E as extra window columns that are
+//      back-substituted on the fly with each finalised column (the technique
+//      of Sec. 3.3 for unreduced right-hand sides, here in the bottom-up RQ
+//      direction), and Xhat += D.
 // Shifts that do not reach the tolerance are flagged; the host re-solves them
 // with the FP64 kernel.  Outputs: G = Ct Xhat (FP64) or Xhat.
 #include <algorithm>
@@ -97,28 +97,6 @@ struct Smem {
     red = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(xs) + L::xs_floats * sizeof(float));
   }
 };
-
-// Block-wide sum of two doubles; every thread gets the totals.
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) {
-    red[w] = a;
-    red[32 + w] = b;
-  }
-  __syncthreads();
-  a = 0.0;
-  b = 0.0;
-  for (int i = 0; i < nw; ++i) {
-    a += red[i];
-    b += red[32 + i];
-  }
-  __syncthreads();
-}
 
 // a0/a1 (rows ia, ib < r) += sum_c Hhi(row, j0 + c) * P(c, :), P rows of `ps`
 // complex entries in shared memory (16-byte aligned rows when MAXM >= 2).
@@ -743,9 +721,11 @@ __global__ void mixed_check_kernel(int n, int m, const double* __restrict__ R,
     // A correction must shrink the backward error by at least 4x (the
     // contraction factor of FP32-based refinement is ~kappa * u32 * growth);
     // slower shifts go to the FP64 sweep at once instead of iterating.
-    if (e <= tol) f |= kFlagOk;
-    else if (!(e == e) || it >= max_refine || (it > 0 && e > 0.25 * prev) || (f & kFlagSing))
-      f |= kFlagFail;
+    // a shift flagged singular goes to the FP64 re-solve (which reports it)
+    // even when its backward error is small
+    if (f & kFlagSing) f |= kFlagFail;
+    else if (e <= tol) f |= kFlagOk;
+    else if (!(e == e) || it >= max_refine || (it > 0 && e > 0.25 * prev)) f |= kFlagFail;
     flags[sh] = f;
   }
 }
@@ -828,6 +808,13 @@ __global__ void mixed_init_kernel(int s, int* __restrict__ flags, double* __rest
   if (blockIdx.x == 0 && threadIdx.x == 0) *count = s;
 }
 
+// Statuses of the first solve -> flags (singular or non-finite shifts go to
+// the FP64 re-solve like every other failure).
+__global__ void mixed_status_kernel(int s, const int* __restrict__ st0, int* __restrict__ flags) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < s; j += gridDim.x * blockDim.x)
+    if (st0[j] != SSV_SHIFT_OK) flags[j] |= kFlagSing;
+}
+
 // Scratch of one mixed solve, carved from one stream-ordered allocation.
 struct MixedScratch {
   cd* X;         // s * n * m
@@ -838,6 +825,7 @@ struct MixedScratch {
   int* flags;    // s
   int* list;     // s
   int* fallback; // s
+  int* st0;      // s: statuses of the first (double-float) solve
   int* count;    // 1
   size_t bytes;
 };
@@ -854,7 +842,7 @@ size_t mixed_layout(int n, int m, int s, int grid, size_t slot_bytes, MixedScrat
   size_t oX = take(sizeof(cd) * nm * s), oE = take(sizeof(cf) * nm * s);
   size_t oS = take(slot_bytes * grid), oA = take(sizeof(double) * 2 * s),
          oT = take(sizeof(double) * s), oF = take(sizeof(int) * s), oL = take(sizeof(int) * s),
-         oB = take(sizeof(int) * s), oC = take(sizeof(int));
+         oB = take(sizeof(int) * s), oS0 = take(sizeof(int) * s), oC = take(sizeof(int));
   if (ms && base) {
     ms->X = reinterpret_cast<cd*>(base + oX);
     ms->E = reinterpret_cast<cf*>(base + oE);
@@ -864,6 +852,7 @@ size_t mixed_layout(int n, int m, int s, int grid, size_t slot_bytes, MixedScrat
     ms->flags = reinterpret_cast<int*>(base + oF);
     ms->list = reinterpret_cast<int*>(base + oL);
     ms->fallback = reinterpret_cast<int*>(base + oB);
+    ms->st0 = reinterpret_cast<int*>(base + oS0);
     ms->count = reinterpret_cast<int*>(base + oC);
     ms->bytes = off;
   }
@@ -880,14 +869,11 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
   using L = LayoutM<MAXM>;
   const int n = h->n, m = h->m, p = h->p;
   const size_t slot_bytes = (size_t)n * m * 3 * sizeof(cf);
-  auto k0 = mixed_sweep_kernel<MAXM, false>;
   auto k1 = mixed_sweep_kernel<MAXM, true>;
-  SSV_CUDA_TRY(cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
   SSV_CUDA_TRY(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
-  int occ0 = 0, occ1 = 0;
-  SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k0, kThreads, L::bytes));
+  int occ1 = 0;
   SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k1, kThreads, L::bytes));
-  const int per_sm = std::max(1, std::min(std::max(occ0, occ1), kSweepBlocksPerSm));
+  const int per_sm = std::max(1, std::min(occ1, kSweepBlocksPerSm));
   const int grid = std::max(1, std::min(s, num_sms() * per_sm));
   const size_t total = mixed_layout(n, m, s, grid, slot_bytes, nullptr, nullptr);
   unsigned char* base = nullptr;
@@ -900,10 +886,19 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
   mixed_init_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(s, ms.flags, ms.eta, ms.acc,
                                                                      ms.list, ms.count);
   count_launch();
+  // first solve: the double-float sweep (FP64 panels, FP32-pair bulk updates)
+  // writes Xhat of every shift; its singular shifts are flagged
   void* tr = trace_begin("mixed_sweep0", st);
-  k0<<<grid, kThreads, L::bytes, st>>>(n, m, nb, h->Hhi, h->R, sd, ms.list, ms.count, ms.slots,
-                                      slot_bytes, ms.X, ms.E, ms.flags, h->hnorm2);
-  count_launch();
+  {
+    ssv_opts od;
+    ssv_default_opts(&od);
+    od.precision = SSV_DFLOAT;
+    od.mode = SSV_XHAT;
+    int rc0 = solve_fp64(h, s, shifts, &od, reinterpret_cast<double*>(ms.X), n, ms.st0, nullptr, st);
+    if (rc0 != SSV_OK) return rc0;
+    mixed_status_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(s, ms.st0, ms.flags);
+    count_launch();
+  }
   trace_end(tr, st);
   const int rgrid = num_sms() * kResidBlocksPerSm;
   for (int it = 0; it <= max_refine; ++it) {

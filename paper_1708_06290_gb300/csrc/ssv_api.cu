@@ -69,7 +69,7 @@ void ssv_default_opts(ssv_opts* o) {
   o->nb = 0;
   o->tile = 0;
   o->max_refine = 8;
-  o->tol = 1e-14;
+  o->tol = 1e-13;
   o->panel = SSV_PANEL_HOUSEHOLDER;
 }
 

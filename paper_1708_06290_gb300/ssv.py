@@ -176,7 +176,7 @@ def _need_cuda(t, dtype, name):
 _PANELS = {"householder": 0, "givens": 1}
 
 
-def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-14, panel="householder"):
+def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-13, panel="householder"):
     o = Opts()
     load().ssv_default_opts(ctypes.byref(o))
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
@@ -231,7 +231,7 @@ class Handle:
     def out_rows(self, mode):
         return self.p if _MODES.get(mode, mode) in (G, TF) else self.n
 
-    def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=8, tol=1e-14,
+    def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=8, tol=1e-13,
               out=None, status=None, resid=None, want_resid=False, stream=None, panel="householder"):
         """Solve all shifts.  Returns (out, status, resid).
 

@@ -52,7 +52,7 @@ def test_strerror_and_defaults(lib):
     assert lib.ssv_strerror(12345) == b"unknown error code"
     o = ssv.Opts()
     lib.ssv_default_opts(ctypes.byref(o))
-    assert o.precision == ssv.FP64 and o.mode == ssv.G and o.max_refine == 8 and o.tol == 1e-14
+    assert o.precision == ssv.FP64 and o.mode == ssv.G and o.max_refine == 8 and o.tol == 1e-13
 
 
 def test_argument_validation_needs_no_gpu(lib):

@@ -299,3 +299,17 @@ def test_dfloat_precision_workload_sampled():
             assert relerr(G[j], Go[k]) < REL_TOL, (j, cond[k])
             checked += 1
     assert checked >= 8
+
+
+def test_dfloat_exact_singular_shift_is_reported():
+    n, m, p = 40, 3, 2
+    rng = np.random.default_rng(5)
+    A = np.triu(rng.standard_normal((n, n))) - 2 * np.eye(n)
+    B = np.eye(n)[:, :m]
+    C = rng.standard_normal((p, n))
+    h = ssv.reduce(dev(A), dev(B), dev(C))
+    sig = np.array([A[n - 1, n - 1] + 0j, A[17, 17] + 0j, 0.5j])
+    out, status, _ = h.solve(shifts_dev(sig), mode="g", precision="dfloat")
+    status = status.cpu().numpy()
+    assert status[0] == ssv.SHIFT_SINGULAR and status[1] == ssv.SHIFT_SINGULAR
+    assert status[2] == ssv.SHIFT_OK
