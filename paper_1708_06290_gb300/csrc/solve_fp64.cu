@@ -278,6 +278,127 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
         coef[idx] = v;
       }
       __syncthreads();
+    } else if constexpr (DF) {
+      // ---- panel in double-float: the window block `cand` and the
+      // coefficients `coef` are held as FP32 pairs (re_hi, re_lo, im_hi, im_lo);
+      // each row's reflector is formed in FP64 from them (a few scalars per
+      // row) and applied in double-float on the FP32 pipe.
+      float4* cand4 = reinterpret_cast<float4*>(cand);
+      float4* coef4 = reinterpret_cast<float4*>(coef);
+      float4* vf = reinterpret_cast<float4*>(Yb);  // reflector v and tau (slot MAXM + 2)
+      auto split4 = [](cd z) -> float4 {
+        const float rh = (float)z.x, ih = (float)z.y;
+        return make_float4(rh, (float)(z.x - (double)rh), ih, (float)(z.y - (double)ih));
+      };
+      auto join4 = [](float4 w) -> cd { return mkcd((double)w.x + (double)w.y, (double)w.z + (double)w.w); };
+      // entry (global row gr, fresh column jc) of H - sigma I as FP32 pairs
+      auto fresh4 = [&](int gr, int jc) -> float4 {
+        const size_t hidx = (size_t)gr + (size_t)jc * n;
+        if (gr == jc) return split4(csub(mkcd((double)d.Hhi[hidx] + (double)d.Hlo[hidx], 0.0), sigma));
+        return make_float4(d.Hhi[hidx], d.Hlo[hidx], 0.f, 0.f);
+      };
+      for (int idx = tid; idx < m * nbe; idx += kThreads) {
+        int t = idx % nbe, q = idx / nbe;
+        cand4[q * kNB + t] = split4(Z2[(r + t) + (size_t)q * ldz]);
+      }
+      for (int idx = tid; idx < L::kCoefRows * S; idx += kThreads) {
+        int c = idx / S, slot = idx % S;
+        const bool one = (slot < m && c == kNB + slot) || (slot == m && c == nbe - 1);
+        coef4[idx] = make_float4(one ? 1.f : 0.f, 0.f, 0.f, 0.f);
+      }
+      {
+        const int c = nbe - 1, jc = j0 + c;
+        for (int t = tid; t <= c; t += kThreads) cand4[m * kNB + t] = fresh4(k - nbe + t, jc);
+      }
+      __syncthreads();
+      for (int c = nbe - 1; c >= 0; --c) {
+        const int fs = m + ((nbe - 1 - c) & 1);
+        const int fn = (fs == m) ? m + 1 : m;
+        if (tid < 32) {
+          double rest2 = 0.0;
+          for (int q = tid; q < m; q += 32) {
+            const cd x = join4(cand4[q * kNB + c]);
+            rest2 = fma(x.x, x.x, fma(x.y, x.y, rest2));
+          }
+          for (int o = 16; o > 0; o >>= 1) rest2 += __shfl_xor_sync(0xffffffffu, rest2, o);
+          const cd xf = join4(cand4[fs * kNB + c]);
+          const double af2 = fma(xf.x, xf.x, xf.y * xf.y);
+          const double af = sqrt(af2);
+          const double nrm2 = rest2 + af2;
+          const double nrm = sqrt(nrm2);
+          const cd ph = af > 0.0 ? mkcd(xf.x / af, -xf.y / af) : mkcd(1.0, 0.0);
+          const cd alpha = mkcd(-ph.x * nrm, -ph.y * nrm);
+          const bool trivial = !(rest2 > 0.0);
+          for (int q = tid; q <= m; q += 32) {
+            const int slot = q < m ? q : fs;
+            const cd x = join4(cand4[slot * kNB + c]);
+            cd v = mkcd(x.x, -x.y);
+            if (slot == fs) v = csub(v, alpha);
+            vf[slot] = split4(v);
+          }
+          if (tid == 0) {
+            const double vv = 2.0 * nrm2 + 2.0 * af * nrm;
+            const double tau = trivial ? 0.0 : 2.0 / vv;
+            const float th = (float)tau;
+            vf[MAXM + 2] = make_float4(th, (float)(tau - (double)th), 0.f, 0.f);
+            if (nrm <= sing_tol) s_sing = 1;
+          }
+        }
+        __syncthreads();
+        const float4 tauf = vf[MAXM + 2];
+        if (tauf.x != 0.0f) {
+          const int nrow = c;
+          const int ncoef = (nbe - c) + m;
+          for (int e = tid; e < nrow + ncoef; e += kThreads) {
+            float4* base;
+            int stride;
+            if (e < nrow) {
+              base = cand4 + e;
+              stride = kNB;
+            } else {
+              const int ee = e - nrow;
+              const int crow = ee < nbe - c ? c + ee : kNB + (ee - (nbe - c));
+              base = coef4 + crow * S;
+              stride = 1;
+            }
+            // w = sum_slot base(slot) v(slot)
+            float wrh = 0.f, wrl = 0.f, wih = 0.f, wil = 0.f;
+            for (int q = 0; q <= m; ++q) {
+              const int slot = q < m ? q : fs;
+              const float4 x = base[slot * stride], v = vf[slot];
+              df_mac(wrh, wrl, x.x, x.y, v.x, v.y);
+              df_mac(wrh, wrl, -x.z, -x.w, v.z, v.w);
+              df_mac(wih, wil, x.x, x.y, v.z, v.w);
+              df_mac(wih, wil, x.z, x.w, v.x, v.y);
+            }
+            // t = tau w (double-float products, normalised)
+            float trh = 0.f, trl = 0.f, tih = 0.f, til = 0.f;
+            df_mac(trh, trl, tauf.x, tauf.y, wrh, wrl);
+            df_mac(tih, til, tauf.x, tauf.y, wih, wil);
+            // base(slot) -= t conj(v(slot))
+            for (int q = 0; q <= m; ++q) {
+              const int slot = q < m ? q : fs;
+              float4 x = base[slot * stride];
+              const float4 v = vf[slot];
+              float xrh = x.x, xrl = x.y, xih = x.z, xil = x.w;
+              df_mac(xrh, xrl, -trh, -trl, v.x, v.y);
+              df_mac(xrh, xrl, -tih, -til, v.z, v.w);
+              df_mac(xih, xil, -tih, -til, v.x, v.y);
+              df_mac(xih, xil, trh, trl, v.z, v.w);
+              float sr = xrh + xrl, si = xih + xil;
+              x = make_float4(sr, xrl - (sr - xrh), si, xil - (si - xih));
+              base[slot * stride] = x;
+            }
+          }
+        }
+        if (c > 0) {
+          const int cn = c - 1, jc = j0 + cn;
+          for (int t = tid; t <= cn; t += kThreads) cand4[fn * kNB + t] = fresh4(k - nbe + t, jc);
+          for (int crow = tid; crow < L::kCoefRows; crow += kThreads)
+            coef4[crow * S + fn] = make_float4(crow == cn ? 1.f : 0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+      }
     } else {
       // stage the live rows of the block and reset coefficients
       for (int idx = tid; idx < m * nbe; idx += kThreads) {
@@ -408,17 +529,11 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     // ---- update the rows above the block (and the T rows)
     if constexpr (DF) {
       // double-float update (SSV_DFLOAT): the coefficients as FP32 pairs
-      // (re_hi, re_lo, im_hi, im_lo) in place, H as (Hhi, Hlo), Z2 split on the
+      // (re_hi, re_lo, im_hi, im_lo), H as (Hhi, Hlo), Z2 split on the
       // fly; exact FMA products, two-sum accumulation (48-bit class).  The Ct
       // rows and the diagonal correction stay in FP64.
-      __syncthreads();
-      for (int idx = tid; idx < CR * S; idx += kThreads) {
-        const cd v = coef[idx];
-        const float rh = (float)v.x, ih = (float)v.y;
-        reinterpret_cast<float4*>(coef)[idx] =
-            make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
-      }
-      __syncthreads();
+      // (the double-float panel above left `coef` in this form already)
+      static_assert(!(DF && (GIVENS || RHS)), "double-float updates need the double-float panel");
     }
     auto coefd = [&](int crow, int q) -> cd {
       if constexpr (DF) {
@@ -713,7 +828,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
 }
 
 template <int MAXM, bool DF = false>
-__global__ void __launch_bounds__(kThreads) solve_fp64_kernel(
+__global__ void __launch_bounds__(kThreads, MAXM <= 16 ? 2 : 1) solve_fp64_kernel(
     int n, int m, int p, int nb, const double* __restrict__ H, const double* __restrict__ Ct,
     int ldct, const double* __restrict__ R, int s, const cd* __restrict__ shifts, int mode,
     cd* __restrict__ scratch, size_t slot_stride, cd* __restrict__ out, long long ldo,
