@@ -463,10 +463,10 @@ def main():
         "flops_per_launch": flops_floor, "launch_ms": solve_ms,
         "flops_definition": "2 n^2 m + 4 n m p per shift (trailing update Z1 P1 + Ct rows)",
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of one solve_fp64_kernel launch
-        # on 152 shifts of this workload (2.986672 + 3.463191 GB, profiles/
+        # on 152 shifts of this workload (3.002227 + 3.462814 GB, profiles/
         # solve_fp64_kernel_n5000_m16_152shifts.md), scaled by shifts to this launch: each
         # shift streams its own Z2 state, so traffic grows in proportion to the shifts.
-        "traffic": (2.986672e9 + 3.463191e9) * s / 152.0 if args.nb in (0, 128) else None,
+        "traffic": (3.002227e9 + 3.462814e9) * s / 152.0 if args.nb in (0, 128) else None,
         "traffic_source": "ncu capture of 152 shifts at n_b=128, scaled to %d shifts" % s,
     }
     line = {
