@@ -11,6 +11,8 @@ All arithmetic is IEEE double (complex128), done in ``csrc/ssv_oracle.c``:
   on the full matrix (the plain definition of the shifted solve, Sec. 1).
 * :func:`dense_solve_vec` -- one right-hand side per shift, x = (A - sigma I)^{-1} b
   or x = (A - sigma I)^{-T} c (Sec. 3.3), same LU.
+* :func:`tf_norm2` -- ||C (sigma I - A)^{-1} B||_2 per shift (structured pseudospectra,
+  Sec. 1), largest singular value of G by the library SVD.
 * :func:`reduce` -- controller-Hessenberg form (H, R, Ct[, Q]) of (A, B, C) by
   unblocked Householder reflectors in the order of Algorithm 1 (Sec. 2).
 * :func:`reduced_solve` -- Xhat = (H - sigma I)^{-1} R (or G = Ct Xhat) by
@@ -161,6 +163,16 @@ def reduced_solve(H, R, Ct, sigmas, want="xhat", cond=False):
 def transfer(C, X):
     """G = C X for a stack of solutions X (s, n, m) -> (s, p, m)."""
     return np.einsum("pn,snm->spm", np.asarray(C, dtype=np.float64), X)
+
+
+def tf_norm2(G):
+    """||G(sigma_j)||_2 for a stack G (s, p, m): the quantity whose level sets are the
+    structured pseudospectrum of (A, B, C) (Sec. 1, the set of z with
+    ||C (zI - A)^{-1} B||_2 >= 1/eps).  Largest singular value by the library SVD."""
+    G = np.asarray(G, dtype=np.complex128)
+    if G.shape[1] == 0 or G.shape[2] == 0:
+        return np.zeros(G.shape[0])
+    return np.array([np.linalg.svd(g, compute_uv=False)[0] for g in G])
 
 
 def backward_error(Mfun_H, sigma, X, R):

@@ -399,3 +399,43 @@ def test_greedy_schedule_applied_as_givens_rotations_gives_an_rq_factor():
         assert abs(Z[r, r + d]) > 1e-3
     assert np.linalg.norm(Q.conj().T @ Q - np.eye(ncol)) < 1e-13
     assert np.linalg.norm(Z0 @ Q - Z) < 1e-12 * np.linalg.norm(Z0)
+
+
+# --------------------------------------------------------------------------
+# tf_norm2: ||C (zI - A)^{-1} B||_2, the structured-pseudospectrum function
+# --------------------------------------------------------------------------
+
+def test_tf_norm2_single_input_single_output_closed_form(ora):
+    """m = p = 1, diagonal A: |sum_i c_i b_i / (z - a_i)|."""
+    a, sysd = W.diagonal_system(12, 1, 1, seed=31)
+    z = np.array([0.3j, -1.2 + 0.8j, -4.0 - 0.1j])
+    X, _ = ora.dense_solve(sysd.A, sysd.B, z)
+    nrm = ora.tf_norm2(ora.transfer(sysd.C, X))
+    for j, zz in enumerate(z):
+        exact = abs(np.sum(sysd.C[0] * sysd.B[:, 0] / (zz - a)))
+        assert abs(nrm[j] - exact) <= 1e-13 * exact
+
+
+def test_tf_norm2_normal_matrix_is_the_inverse_distance_to_the_spectrum(ora):
+    """B = C^T = I and A = diag(a): ||(zI - A)^{-1}||_2 = 1 / min_i |z - a_i|, so the
+    structured pseudospectrum is the union of the discs of radius eps around a_i."""
+    n = 9
+    a = -np.linspace(0.5, 3.5, n)
+    A = np.diag(a)
+    z = np.array([0.2j, -2.0 + 0.05j, -0.9 - 0.4j])
+    X, _ = ora.dense_solve(A, np.eye(n), z)
+    nrm = ora.tf_norm2(ora.transfer(np.eye(n), X))
+    for j, zz in enumerate(z):
+        exact = 1.0 / np.min(np.abs(zz - a))
+        assert abs(nrm[j] - exact) <= 1e-13 * exact
+
+
+def test_tf_norm2_single_input_is_the_vector_norm(ora):
+    """m = 1: G(z) is a p-vector and its 2-norm is sqrt(sum_k |G_k|^2) in closed form."""
+    a, sysd = W.diagonal_system(15, 1, 4, seed=32)
+    z = np.array([0.7j, -2.3 + 0.2j])
+    X, _ = ora.dense_solve(sysd.A, sysd.B, z)
+    nrm = ora.tf_norm2(ora.transfer(sysd.C, X))
+    for j, zz in enumerate(z):
+        g = sysd.C @ (-sysd.B[:, 0] / (zz - a))  # C (A - zI)^{-1} b
+        assert abs(nrm[j] - np.sqrt(np.sum(np.abs(g) ** 2))) <= 1e-13 * nrm[j]
