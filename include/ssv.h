@@ -181,6 +181,20 @@ int ssv_givens_schedule(int rows, int m, int* rot, int max_rot, int* off, int ma
                         int* nsteps);
 
 /*
+ * ssv_tf_norm2 -- ||C (sigma_j I - A)^{-1} B||_2 for every shift: the function
+ * whose level sets {z : ||C (zI - A)^{-1} B||_2 >= 1/eps} are the structured
+ * pseudospectra of (A, B, C) (Sec. 1).  Solves for G(sigma_j) with the
+ * precision of o (mode ignored), then the largest singular value of each
+ * p x m block by Jacobi on G^H G or G G^H (one warp per shift).
+ *   norms (device): s doubles (NaN for a shift whose G is not finite);
+ *   status (device, may be NULL): s ints from the solve.
+ *   Requires 1 <= min(m, p) <= 32.
+ * Errors: SSV_EINVAL, SSV_ENOTSUP, SSV_ENOMEM, SSV_ECUDA.
+ */
+int ssv_tf_norm2(ssv_handle h, int s, const double* shifts, const ssv_opts* o, double* norms,
+                 int* status, void* stream);
+
+/*
  * ssv_solve_many -- many reduced systems of uneven n, m and shift counts in
  * one persistent launch (FP64: one kernel over a cost-ordered worklist of
  * (system, shift) items, Sec. 3 applied to several systems at once; MIXED:

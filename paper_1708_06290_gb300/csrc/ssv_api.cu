@@ -248,6 +248,24 @@ int ssv_givens_schedule(int rows, int m, int* rot, int max_rot, int* off, int ma
   return (int)r.size();
 }
 
+int ssv_tf_norm2(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, double* norms,
+                 int* status, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || s < 0) return SSV_EINVAL;
+  ssv_opts o;
+  if (o_in) o = *o_in; else ssv_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc != SSV_OK) return rc;
+  if (o.panel != SSV_PANEL_HOUSEHOLDER) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  if (!shifts || !norms) return SSV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  void* tr = trace_begin("tf_norm2", st);
+  rc = tf_norm2(h, s, shifts, &o, norms, status, st);
+  trace_end(tr, st);
+  return rc;
+}
+
 static int check_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
                       const ssv_opts& o, double* const* outs, const long long* ldos) {
   if (nsys < 0 || (nsys > 0 && (!hs || !s || !shifts || !outs || !ldos))) return SSV_EINVAL;

@@ -121,6 +121,9 @@ int solve_fp64_trans(const Handle* h, int s, const double* shifts, const double*
 // FP64 sweep with the Givens panel and greedy schedule (Sec. 3.2); n_b <= 32
 int solve_fp64_givens(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                       long long ldo, int* status, double* resid, cudaStream_t st);
+// ||C (sigma I - A)^{-1} B||_2 per shift (structured pseudospectra, Sec. 1), tf_norm.cu
+int tf_norm2(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* norms,
+             int* status, cudaStream_t st);
 // greedy annihilation schedule (Algorithm 9) of a block with `rows` rows and rows + m
 // columns: rotations packed r | c1 << 8 | c2 << 16 (0-based), step t = off[t] .. off[t+1]-1
 void greedy_rows(int rows, int m, std::vector<int>* rot, std::vector<int>* off);

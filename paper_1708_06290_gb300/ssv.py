@@ -60,7 +60,7 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc", "ssv_solve_many",
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
            "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
-           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule")
+           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2")
 
 _lib = None
 
@@ -92,6 +92,7 @@ def load(build_if_missing=True):
     L.ssv_solve_rhs.argtypes = [P, I, P, P, LL, ctypes.POINTER(Opts), P, LL, P, P]
     L.ssv_solve_trans.argtypes = [P, I, P, P, LL, ctypes.POINTER(Opts), P, LL, P, P]
     L.ssv_givens_schedule.argtypes = [I, I, P, I, P, I, ctypes.POINTER(I)]
+    L.ssv_tf_norm2.argtypes = [P, I, P, ctypes.POINTER(Opts), P, P, P]
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.ssv_solve_many.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
                                  ctypes.POINTER(LL), PP, P]
@@ -109,7 +110,7 @@ def load(build_if_missing=True):
     L.ssv_trace_read.argtypes = [I, ctypes.c_char_p, I, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(I), ctypes.POINTER(I)]
     for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
-           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule"):
+           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2"):
         getattr(L, f).restype = I
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
@@ -308,6 +309,21 @@ class Handle:
                                ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream))
         _check(rc, "ssv_solve_trans")
         return out, status
+
+    def tf_norm2(self, shifts, precision="fp64", nb=0, stream=None):
+        """||C (sigma_j I - A)^{-1} B||_2 per shift (structured pseudospectra, Sec. 1).
+        Returns (norms float64 (s,), status int32 (s,))."""
+        L = load()
+        _need_cuda(shifts, torch.complex128, "shifts")
+        s = shifts.numel()
+        o = opts(precision, "g", nb)
+        norms = torch.empty(s, dtype=torch.float64, device=shifts.device)
+        status = torch.empty(s, dtype=torch.int32, device=shifts.device)
+        rc = L.ssv_tf_norm2(self.ptr, s, ctypes.c_void_p(shifts.data_ptr()), ctypes.byref(o),
+                            ctypes.c_void_p(norms.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                            _stream_ptr(stream))
+        _check(rc, "ssv_tf_norm2")
+        return norms, status
 
     def apply_q(self, xhat, out=None, stream=None):
         L = load()
