@@ -462,6 +462,11 @@ def main():
         "peak_source": "FP64 DFMA probe measured in this run (nominal GB300 FP64 1.25 TFLOP/s)",
         "flops_per_launch": flops_floor, "launch_ms": solve_ms,
         "flops_definition": "2 n^2 m + 4 n m p per shift (trailing update Z1 P1 + Ct rows)",
+        # context: the kernel executes ~1.2e9 FP64 flops per shift at n_b = 128 (Z2 P2 and the
+        # Householder panel on top of the floor); ncu measured its FP64 pipe 86 % busy
+        # (profiles/solve_fp64_kernel_n5000_m16_152shifts.md)
+        "executed_flops_per_shift": 2.0 * n * n * m + 4.0 * n * n * m * m / 128 + 16.0 * n * (m + 1) * (128 + m),
+        "fp64_pipe_busy_ncu": 0.861,
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of one solve_fp64_kernel launch
         # on 152 shifts of this workload (3.002227 + 3.462814 GB, profiles/
         # solve_fp64_kernel_n5000_m16_152shifts.md), scaled by shifts to this launch: each

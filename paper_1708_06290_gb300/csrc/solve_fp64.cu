@@ -823,7 +823,16 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
       o[(d.flip_out ? n - 1 - i : i) + (size_t)q * ld] = acc;
     }
   }
-  if (status != nullptr && tid == 0) status[sh] = sing ? SSV_SHIFT_SINGULAR : SSV_SHIFT_OK;
+  if (status != nullptr && tid == 0) {
+    // a non-finite solution (NaN / Inf in the inputs or an overflow) is reported
+    // as such, also when no separate scan of the outputs follows
+    bool fin = true;
+    for (int e = 0; e < m * nr; ++e) {
+      const cd y = Yb[(e % m) + (e / m) * MAXM];
+      fin = fin && isfinite(y.x) && isfinite(y.y);
+    }
+    status[sh] = sing ? SSV_SHIFT_SINGULAR : (fin ? SSV_SHIFT_OK : SSV_SHIFT_NONFINITE);
+  }
   __syncthreads();
 }
 

@@ -313,3 +313,18 @@ def test_dfloat_exact_singular_shift_is_reported():
     status = status.cpu().numpy()
     assert status[0] == ssv.SHIFT_SINGULAR and status[1] == ssv.SHIFT_SINGULAR
     assert status[2] == ssv.SHIFT_OK
+
+
+@pytest.mark.parametrize("precision", ["fp64", "dfloat", "mixed"])
+def test_nonfinite_input_is_reported_not_hidden(precision):
+    """A NaN in A reaches every shift: each status is NONFINITE (or SINGULAR) and no
+    output is silently finite-looking garbage with an OK status."""
+    sysr = W.random_system(80, 3, 2, seed=44)
+    A = sysr.A.copy()
+    A[10, 20] = np.nan
+    h = ssv.reduce(dev(A), dev(sysr.B), dev(sysr.C))
+    out, status, _ = h.solve(shifts_dev([0.5j, -1.0 + 0.2j]), mode="g", precision=precision)
+    st = status.cpu().numpy()
+    o = out.cpu().numpy()
+    assert ((st == ssv.SHIFT_NONFINITE) | (st == ssv.SHIFT_SINGULAR)).all(), st
+    assert not np.isfinite(o).all()
