@@ -240,7 +240,8 @@ def serving_measurement(ssv, dev, args):
 
 def batching_measurement(ssv, dev, args):
     """The batching workload: 64 systems, n ~ U{200..3000}, m in {1,2,4,8},
-    16..512 shifts each, one ssv_solve_many launch (FP64); reductions untimed."""
+    16..512 shifts each, one ssv_solve_many launch per precision (FP64 and the
+    double-float updates); reductions untimed."""
     import torch
 
     work = W.workload_batching()
@@ -248,21 +249,25 @@ def batching_measurement(ssv, dev, args):
     handles = [ssv.reduce(to(sy.A), to(sy.B), to(sy.C)) for sy, _ in work]
     shifts = [torch.from_numpy(sig.astype(np.complex128)).to(dev) for _, sig in work]
     total = sum(int(x.numel()) for x in shifts)
-    ssv.solve_many(handles, shifts, mode="g")
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ssv.solve_many(handles, shifts, mode="g")
-        e1.record()
+    res = {"systems": len(work), "shifts": total, "launches_per_batch": 1}
+    for prec in ("fp64", "dfloat"):
+        ssv.solve_many(handles, shifts, mode="g", precision=prec)
         torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ssv.solve_many(handles, shifts, mode="g", precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        if prec == "fp64":
+            res.update({"ms": ms, "shift_solves_per_s": total / (ms * 1e-3)})
+        res[prec] = {"ms": ms, "shift_solves_per_s": total / (ms * 1e-3)}
     for h in handles:
         h.close()
-    ms = float(np.median(ts))
-    return {"systems": len(work), "shifts": total, "ms": ms,
-            "shift_solves_per_s": total / (ms * 1e-3), "launches_per_batch": 1}
+    return res
 
 
 def profile_solve(args):

@@ -196,9 +196,9 @@ int ssv_tf_norm2(ssv_handle h, int s, const double* shifts, const ssv_opts* o, d
 
 /*
  * ssv_solve_many -- many reduced systems of uneven n, m and shift counts in
- * one persistent launch (FP64: one kernel over a cost-ordered worklist of
- * (system, shift) items, Sec. 3 applied to several systems at once; MIXED:
- * the systems are solved one after another on the stream).
+ * one persistent launch (FP64 and SSV_DFLOAT: one kernel over a cost-ordered
+ * worklist of (system, shift) items, Sec. 3 applied to several systems at
+ * once; MIXED: the systems are solved one after another on the stream).
  *   nsys systems; hs[k] handle, s[k] shifts at shifts[k] (device), results in
  *   outs[k] (device, layout as ssv_solve with leading dimension ldos[k]),
  *   statuses in status[k] (device, or status == NULL / status[k] == NULL).
@@ -218,7 +218,7 @@ int ssv_solve_many(int nsys, const ssv_handle* hs, const int* s, const double* c
  * that ssv_batch_run is a single kernel launch with constant arguments that
  * can be captured into a CUDA graph and replayed; between runs the caller may
  * rewrite the contents (not the addresses) of the shift buffers.
- *   ssv_batch_create: arguments as ssv_solve_many (precision must be SSV_FP64;
+ *   ssv_batch_create: arguments as ssv_solve_many (precision SSV_FP64 or SSV_DFLOAT;
  *   nb = 0 takes the autotuned or default block width per system); allocates
  *   the plan (device descriptors, worklist, scratch) synchronously.
  *   ssv_batch_run: enqueue the batch on `stream`.

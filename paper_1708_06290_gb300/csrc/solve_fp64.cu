@@ -935,8 +935,8 @@ __global__ void flipped_rhs_kernel(const double* __restrict__ Ct, int ldct, int 
 
 // Many systems in one launch: work item w = (system, shift) from `items`
 // (system in the high 32 bits), ordered by decreasing cost.
-template <int MAXM>
-__global__ void __launch_bounds__(kThreads) solve_fp64_batch_kernel(
+template <int MAXM, bool DF = false>
+__global__ void __launch_bounds__(kThreads, MAXM <= 16 ? 2 : 1) solve_fp64_batch_kernel(
     const FpSys* __restrict__ systems, const unsigned long long* __restrict__ items, int nitems,
     cd* __restrict__ scratch, size_t slot_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -946,7 +946,7 @@ __global__ void __launch_bounds__(kThreads) solve_fp64_batch_kernel(
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const unsigned long long it = items[w];
     const FpSys d = systems[(int)(it >> 32)];
-    fp64_shift<MAXM>(d, (int)(it & 0xffffffffu), Z2, smem_raw, &s_piv, &s_sing);
+    fp64_shift<MAXM, false, false, DF>(d, (int)(it & 0xffffffffu), Z2, smem_raw, &s_piv, &s_sing);
   }
 }
 
@@ -1508,6 +1508,7 @@ struct BatchPlan {
   bool stream_ordered = false;  // buffers from cudaMallocAsync on `stream`
   cudaStream_t stream = nullptr;
   int maxm = 1;
+  bool dfloat = false;  // SSV_DFLOAT: double-float bulk updates
   int nitems = 0;
   int grid = 0;
   size_t slot = 0;
@@ -1519,10 +1520,10 @@ struct BatchPlan {
 
 namespace {
 
-template <int MAXM>
+template <int MAXM, bool DF>
 int batch_config(BatchPlan* bp) {
   using L = Layout<MAXM>;
-  auto kern = solve_fp64_batch_kernel<MAXM>;
+  auto kern = solve_fp64_batch_kernel<MAXM, DF>;
   SSV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
   int per_sm = 0;
   SSV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L::bytes));
@@ -1534,9 +1535,12 @@ int batch_config(BatchPlan* bp) {
 
 template <int MAXM>
 void batch_launch(const BatchPlan* bp, cudaStream_t st) {
-  solve_fp64_batch_kernel<MAXM><<<bp->grid, kThreads, bp->smem, st>>>(bp->systems, bp->items,
-                                                                     bp->nitems, bp->scratch,
-                                                                     bp->slot);
+  if (bp->dfloat)
+    solve_fp64_batch_kernel<MAXM, true><<<bp->grid, kThreads, bp->smem, st>>>(
+        bp->systems, bp->items, bp->nitems, bp->scratch, bp->slot);
+  else
+    solve_fp64_batch_kernel<MAXM, false><<<bp->grid, kThreads, bp->smem, st>>>(
+        bp->systems, bp->items, bp->nitems, bp->scratch, bp->slot);
   count_launch();
 }
 
@@ -1546,9 +1550,10 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
                  const ssv_opts* o, double* const* outs, const long long* ldos, int* const* status,
                  BatchPlan** out, cudaStream_t stream_ordered) {
   *out = nullptr;
-  if (o->precision != SSV_FP64 || o->mode == SSV_X) return SSV_ENOTSUP;
+  if ((o->precision != SSV_FP64 && o->precision != SSV_DFLOAT) || o->mode == SSV_X) return SSV_ENOTSUP;
   BatchPlan* bp = new (std::nothrow) BatchPlan();
   if (!bp) return SSV_ENOMEM;
+  bp->dfloat = o->precision == SSV_DFLOAT;
   cudaGetDevice(&bp->dev);
   bp->stream_ordered = stream_ordered != nullptr;
   bp->stream = stream_ordered;
@@ -1559,7 +1564,7 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
     const Handle* h = hs[k];
     FpSys& d = sys[k];
     d.n = h->n; d.m = h->m; d.p = h->p;
-    d.nb = o->nb > 0 ? o->nb : tuned_nb(h->n, h->m, h->p, SSV_FP64, o->mode);
+    d.nb = o->nb > 0 ? o->nb : tuned_nb(h->n, h->m, h->p, o->precision, o->mode);
     if (d.nb > kNB || h->m > 32) { delete bp; return SSV_ENOTSUP; }
     d.mode = o->mode; d.H = h->H; d.Ct = h->Ct; d.ldct = h->p > 0 ? h->p : 1; d.R = h->R;
     d.shifts = reinterpret_cast<const cd*>(shifts[k]);
@@ -1567,6 +1572,7 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
     d.status = status ? status[k] : nullptr;
     d.xhat_copy = nullptr; d.ldxc = 0; d.hnorm = h->hnorm2; d.bhat = nullptr; d.ldb = 0;
     d.rhs = nullptr; d.ldr = 0; d.flip_out = 0;
+    d.Hhi = h->Hhi; d.Hlo = h->Hlo;
     d.gfull = GivensSched{nullptr, nullptr, 0};
     d.gtail = d.gfull;
     bp->maxm = std::max(bp->maxm, h->m);
@@ -1583,12 +1589,13 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
   int rc = SSV_OK;
   const int mm = bp->maxm;
   if (bp->nitems > 0) {
-    if (mm <= 1) rc = batch_config<1>(bp);
-    else if (mm <= 2) rc = batch_config<2>(bp);
-    else if (mm <= 4) rc = batch_config<4>(bp);
-    else if (mm <= 8) rc = batch_config<8>(bp);
-    else if (mm <= 16) rc = batch_config<16>(bp);
-    else rc = batch_config<32>(bp);
+    const bool df = bp->dfloat;
+    if (mm <= 1) rc = df ? batch_config<1, true>(bp) : batch_config<1, false>(bp);
+    else if (mm <= 2) rc = df ? batch_config<2, true>(bp) : batch_config<2, false>(bp);
+    else if (mm <= 4) rc = df ? batch_config<4, true>(bp) : batch_config<4, false>(bp);
+    else if (mm <= 8) rc = df ? batch_config<8, true>(bp) : batch_config<8, false>(bp);
+    else if (mm <= 16) rc = df ? batch_config<16, true>(bp) : batch_config<16, false>(bp);
+    else rc = df ? batch_config<32, true>(bp) : batch_config<32, false>(bp);
   }
   cudaError_t e = cudaSuccess;
   if (rc == SSV_OK && bp->nitems > 0) {

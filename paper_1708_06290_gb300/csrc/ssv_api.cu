@@ -327,7 +327,7 @@ int ssv_batch_create(int nsys, const ssv_handle* hs, const int* s, const double*
   if (o_in) o = *o_in; else ssv_default_opts(&o);
   int rc = check_many(nsys, hs, s, shifts, o, outs, ldos);
   if (rc != SSV_OK) return rc;
-  if (o.precision != SSV_FP64) return SSV_ENOTSUP;
+  if (o.precision == SSV_MIXED) return SSV_ENOTSUP;
   BatchPlan* bp = nullptr;
   rc = batch_create(nsys, reinterpret_cast<const Handle* const*>(hs), s, shifts, &o, outs, ldos,
                     status, &bp, nullptr);

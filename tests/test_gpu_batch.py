@@ -118,3 +118,21 @@ def test_solve_many_mixed_precision(batch):
         assert (sts[k].cpu().numpy() == 0).all()
         for j in range(len(sig)):
             assert relerr(got[j], ref[j]) < REL_TOL
+
+
+def test_solve_many_dfloat_equals_solo_dfloat_solves(batch):
+    """The double-float updates in the many-systems launch give each system the
+    same result as its own SSV_DFLOAT solve, and match the oracle."""
+    systems, handles, shifts = batch
+    outs, sts = ssv.solve_many(handles, shifts, mode="g", precision="dfloat")
+    for k, (h, x, o, st) in enumerate(zip(handles, shifts, outs, sts)):
+        ref, st_ref, _ = h.solve(x, mode="g", precision="dfloat")
+        assert torch.equal(st, st_ref)
+        assert torch.equal(o, ref)
+    for k in (0, 5, 11):
+        sysk, sig = systems[k]
+        X, _ = oracle.dense_solve(sysk.A, sysk.B, sig)
+        ref = oracle.transfer(sysk.C, X)
+        got = blocks(outs[k], sysk.m)
+        for j in range(len(sig)):
+            assert relerr(got[j], ref[j]) < REL_TOL
