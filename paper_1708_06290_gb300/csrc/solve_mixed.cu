@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, 2) mixed_sweep_kernel(
 // double-float accumulation.  E is stored as complex64; ||E||_F^2 and
 // ||Xhat||_F^2 are accumulated per shift in acc (FP64 atomics).
 template <int MAXM>
-__global__ void __launch_bounds__(kRT) mixed_residual_kernel(
+__global__ void __launch_bounds__(kRT, 4) mixed_residual_kernel(
     int n, int m, const float* __restrict__ Hhi, const float* __restrict__ Hlo,
     const double* __restrict__ R, const cd* __restrict__ shifts, const int* __restrict__ list,
     const int* __restrict__ count, const cd* __restrict__ Xall, cf* __restrict__ Eall,
