@@ -216,26 +216,32 @@ def serving_measurement(ssv, dev, args):
     t_reduce = time.perf_counter() - t0
     budget = int(args.serving_budget_gb * (1 << 30))
     nreq = args.serving_requests
-    warm = make_requests(W.serving_requests(8, 100.0, seed=900))
-    Server(handles, slots=4, mem_budget=budget).run(warm, realtime=False)
-    sat = Server(handles, slots=4, mem_budget=budget).run(
-        make_requests(W.serving_requests(nreq, 1.0, seed=901)), realtime=False)
-    req_rate = sat["requests"] / sat["wall_s"]
-    loads = {}
-    for f in (0.5, 0.8, 0.95):
-        st = Server(handles, slots=4, mem_budget=budget).run(
-            make_requests(W.serving_requests(nreq, f * req_rate, seed=902 + int(100 * f))),
-            realtime=True)
-        loads["%.2f" % f] = {k: st[k] for k in ("p50_ms", "p99_ms", "shift_solves_per_s",
-                                                 "requests", "batches", "max_inflight_batches")}
+
+    def one(precision):
+        warm = make_requests(W.serving_requests(8, 100.0, seed=900))
+        Server(handles, slots=4, mem_budget=budget, precision=precision).run(warm, realtime=False)
+        sat = Server(handles, slots=4, mem_budget=budget, precision=precision).run(
+            make_requests(W.serving_requests(nreq, 1.0, seed=901)), realtime=False)
+        req_rate = sat["requests"] / sat["wall_s"]
+        loads = {}
+        for f in (0.5, 0.8, 0.95):
+            st = Server(handles, slots=4, mem_budget=budget, precision=precision).run(
+                make_requests(W.serving_requests(nreq, f * req_rate, seed=902 + int(100 * f))),
+                realtime=True)
+            loads["%.2f" % f] = {k: st[k] for k in ("p50_ms", "p99_ms", "shift_solves_per_s",
+                                                     "requests", "batches", "max_inflight_batches")}
+        return {"saturated": {"requests_per_s": req_rate,
+                              "shift_solves_per_s": sat["shift_solves_per_s"],
+                              "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"]},
+                "poisson": loads}
+
+    res = one("fp64")
+    res_df = one("dfloat")
     for h in handles:
         h.close()
     return {"systems_n": [sy.n for sy in systems], "systems_m": [sy.m for sy in systems],
-            "reduce_s": t_reduce, "budget_bytes": budget,
-            "saturated": {"requests_per_s": req_rate,
-                          "shift_solves_per_s": sat["shift_solves_per_s"],
-                          "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"]},
-            "poisson": loads}
+            "reduce_s": t_reduce, "budget_bytes": budget, "precision": "fp64", **res,
+            "dfloat": res_df}
 
 
 def batching_measurement(ssv, dev, args):

@@ -24,7 +24,7 @@ def _requests(count, rate, seed):
     return reqs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "dfloat", "mixed"])
 def test_each_result_is_the_same_alone_and_in_the_mix(handles, precision):
     reqs = _requests(30, 400.0, seed=11)
     srv = Server(handles, slots=4, mem_budget=2 << 30, max_batch_shifts=96, precision=precision)
@@ -35,7 +35,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(handles, precision):
         assert (r.status.cpu().numpy() == 0).all()
         alone, st, _ = handles[r.system].solve(shifts_dev(r.shifts), mode="g", precision=precision)
         torch.cuda.synchronize()
-        if precision == "fp64":
+        if precision in ("fp64", "dfloat"):
             assert torch.equal(r.result, alone)
         else:
             a, b = r.result.cpu().numpy(), alone.cpu().numpy()
