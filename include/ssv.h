@@ -55,14 +55,17 @@ extern "C" {
 /* ---- options ----------------------------------------------------------- */
 #define SSV_FP64 0  /* every step in double / complex128 */
 #define SSV_MIXED 1 /* complex64 elimination + FP64-accurate refinement */
-#define SSV_DFLOAT 2 /* FP64 panels; the bulk updates of the rows above each block
-                        (the Z1 P1 and Z2 P2 products, most of the work) in
+#define SSV_DFLOAT 2 /* the window panels (reflectors formed in double-word
+                        scalars) and the bulk updates of the rows above each
+                        block (the Z1 P1 and Z2 P2 products, most of the work) in
                         double-float arithmetic on the FP32 pipe: pairs of FP32
                         words, exact FMA products, two-sum accumulation (about 48
                         significant bits; no refinement).  A shift is reported
                         singular when a finalised diagonal entry is <= n 2^-47
-                        ||H - sigma I||_F.  Entries must be within the FP32
-                        exponent range.  ssv_solve only. */
+                        ||H - sigma I||_F.  Entries of H - sigma I and their
+                        squares must be within the FP32 exponent range (moduli
+                        between about 1e-18 and 1e18).  ssv_solve, the
+                        many-systems launch and batch plans. */
 
 #define SSV_G 0    /* out(p x m) = C X = Ct Xhat                             */
 #define SSV_TF 1   /* out(p x m) = C (sigma I - A)^{-1} B = -Ct Xhat (Sec. 2) */
@@ -75,7 +78,7 @@ extern "C" {
                                    Algorithm 9 (Sec. 3.2); n_b <= 32, m <= 32 */
 
 typedef struct ssv_opts {
-  int precision;           /* SSV_FP64 or SSV_MIXED */
+  int precision;           /* SSV_FP64, SSV_MIXED or SSV_DFLOAT */
   int mode;                /* SSV_G, SSV_TF, SSV_XHAT, SSV_X */
   int nb;                  /* rows per elimination block n_b; 0 = default */
   int tile;                /* shifts per thread block; 0 = default */

@@ -115,6 +115,41 @@ struct FpSys {
   GivensSched gtail;  // and of the last, shorter block
 };
 
+// Double-word scalars (hi + lo, |lo| <= ulp(hi) / 2) on the FP32 pipe, for the
+// few per-row reflector quantities of the double-float panel: Knuth's two-sum,
+// Dekker's fast two-sum, FMA-exact products, one correction step for the
+// quotient and for the square root (Newton on s^2 = x).  About 44 bits each.
+struct dw {
+  float hi, lo;
+};
+__device__ __forceinline__ dw dw_fast(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return dw{s, b - (s - a)};
+}
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+  const float s = x.hi + y.hi;
+  const float bb = s - x.hi;
+  const float e = (x.hi - (s - bb)) + (y.hi - bb);
+  return dw_fast(s, e + (x.lo + y.lo));
+}
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+  const float p = x.hi * y.hi;
+  const float e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)));
+  return dw_fast(p, e);
+}
+__device__ __forceinline__ dw dw_div(dw x, dw y) {
+  const float q1 = x.hi / y.hi;
+  // x - q1 y: the leading part is exact by FMA
+  const float r = fmaf(-q1, y.hi, x.hi) + fmaf(-q1, y.lo, x.lo);
+  return dw_fast(q1, r / y.hi);
+}
+__device__ __forceinline__ dw dw_sqrt(dw x) {
+  if (!(x.hi > 0.f)) return dw{0.f, 0.f};
+  const float s = sqrtf(x.hi);
+  const float e = fmaf(-s, s, x.hi) + x.lo;
+  return dw_fast(s, e / (2.f * s));
+}
+
 // Solve shift sh of system d with the window state in Z2 (and ZT).  With RHS,
 // the dense right-hand side d.rhs(:, sh) is carried through the sweep: each
 // finalised column F_c (diagonal beta_c) removes f_c = rhs_c / beta_c times
@@ -281,16 +316,17 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     } else if constexpr (DF) {
       // ---- panel in double-float: the window block `cand` and the
       // coefficients `coef` are held as FP32 pairs (re_hi, re_lo, im_hi, im_lo);
-      // each row's reflector is formed in FP64 from them (a few scalars per
-      // row) and applied in double-float on the FP32 pipe.
+      // each row's reflector is formed from them in double-word scalars and
+      // applied in double-float, all on the FP32 pipe.
       float4* cand4 = reinterpret_cast<float4*>(cand);
       float4* coef4 = reinterpret_cast<float4*>(coef);
       float4* vf = reinterpret_cast<float4*>(Yb);  // reflector v and tau (slot MAXM + 2)
+      const float sing_tol_f = (float)sing_tol;
+      static_assert(kNB <= kThreads, "one thread per prefetched fresh entry");
       auto split4 = [](cd z) -> float4 {
         const float rh = (float)z.x, ih = (float)z.y;
         return make_float4(rh, (float)(z.x - (double)rh), ih, (float)(z.y - (double)ih));
       };
-      auto join4 = [](float4 w) -> cd { return mkcd((double)w.x + (double)w.y, (double)w.z + (double)w.w); };
       // entry (global row gr, fresh column jc) of H - sigma I as FP32 pairs
       auto fresh4 = [&](int gr, int jc) -> float4 {
         const size_t hidx = (size_t)gr + (size_t)jc * n;
@@ -314,34 +350,44 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
       for (int c = nbe - 1; c >= 0; --c) {
         const int fs = m + ((nbe - 1 - c) & 1);
         const int fn = (fs == m) ? m + 1 : m;
+        // the next fresh column is read from H now, its latency hidden behind
+        // this row's reflector and update (H is not written by the sweep)
+        float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c > 0 && tid < c) pre = fresh4(k - nbe + tid, j0 + c - 1);
         if (tid < 32) {
-          double rest2 = 0.0;
+          // reflector scalars in double-word arithmetic:
+          //   v = conj(x) + e^{i arg conj(x_f)} ||x|| e_f,  tau = 1 / (||x||^2 + |x_f| ||x||)
+          dw rest2{0.f, 0.f};
           for (int q = tid; q < m; q += 32) {
-            const cd x = join4(cand4[q * kNB + c]);
-            rest2 = fma(x.x, x.x, fma(x.y, x.y, rest2));
+            const float4 x = cand4[q * kNB + c];
+            df_mac(rest2.hi, rest2.lo, x.x, x.y, x.x, x.y);
+            df_mac(rest2.hi, rest2.lo, x.z, x.w, x.z, x.w);
+            vf[q] = make_float4(x.x, x.y, -x.z, -x.w);
           }
-          for (int o = 16; o > 0; o >>= 1) rest2 += __shfl_xor_sync(0xffffffffu, rest2, o);
-          const cd xf = join4(cand4[fs * kNB + c]);
-          const double af2 = fma(xf.x, xf.x, xf.y * xf.y);
-          const double af = sqrt(af2);
-          const double nrm2 = rest2 + af2;
-          const double nrm = sqrt(nrm2);
-          const cd ph = af > 0.0 ? mkcd(xf.x / af, -xf.y / af) : mkcd(1.0, 0.0);
-          const cd alpha = mkcd(-ph.x * nrm, -ph.y * nrm);
-          const bool trivial = !(rest2 > 0.0);
-          for (int q = tid; q <= m; q += 32) {
-            const int slot = q < m ? q : fs;
-            const cd x = join4(cand4[slot * kNB + c]);
-            cd v = mkcd(x.x, -x.y);
-            if (slot == fs) v = csub(v, alpha);
-            vf[slot] = split4(v);
-          }
+          rest2 = dw_fast(rest2.hi, rest2.lo);
+          for (int o = 16; o > 0; o >>= 1)
+            rest2 = dw_add(rest2, dw{__shfl_xor_sync(0xffffffffu, rest2.hi, o),
+                                     __shfl_xor_sync(0xffffffffu, rest2.lo, o)});
           if (tid == 0) {
-            const double vv = 2.0 * nrm2 + 2.0 * af * nrm;
-            const double tau = trivial ? 0.0 : 2.0 / vv;
-            const float th = (float)tau;
-            vf[MAXM + 2] = make_float4(th, (float)(tau - (double)th), 0.f, 0.f);
-            if (nrm <= sing_tol) s_sing = 1;
+            const float4 xf = cand4[fs * kNB + c];
+            const dw xr{xf.x, xf.y}, xi{xf.z, xf.w};
+            const dw af2 = dw_add(dw_mul(xr, xr), dw_mul(xi, xi));
+            const dw af = dw_sqrt(af2);
+            const dw nrm2 = dw_add(rest2, af2);
+            const dw nrm = dw_sqrt(nrm2);
+            float4 vfs;
+            if (af.hi > 0.f) {  // conj(x_f) (1 + ||x|| / |x_f|)
+              const dw g = dw_add(dw{1.f, 0.f}, dw_div(nrm, af));
+              const dw vr = dw_mul(xr, g), vi = dw_mul(xi, g);
+              vfs = make_float4(vr.hi, vr.lo, -vi.hi, -vi.lo);
+            } else {
+              vfs = make_float4(nrm.hi, nrm.lo, 0.f, 0.f);
+            }
+            vf[fs] = vfs;
+            const dw tau = rest2.hi > 0.f ? dw_div(dw{1.f, 0.f}, dw_add(nrm2, dw_mul(af, nrm)))
+                                          : dw{0.f, 0.f};
+            vf[MAXM + 2] = make_float4(tau.hi, tau.lo, 0.f, 0.f);
+            if (nrm.hi <= sing_tol_f) s_sing = 1;
           }
         }
         __syncthreads();
@@ -392,8 +438,8 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
           }
         }
         if (c > 0) {
-          const int cn = c - 1, jc = j0 + cn;
-          for (int t = tid; t <= cn; t += kThreads) cand4[fn * kNB + t] = fresh4(k - nbe + t, jc);
+          const int cn = c - 1;
+          if (tid <= cn) cand4[fn * kNB + tid] = pre;
           for (int crow = tid; crow < L::kCoefRows; crow += kThreads)
             coef4[crow * S + fn] = make_float4(crow == cn ? 1.f : 0.f, 0.f, 0.f, 0.f);
         }
