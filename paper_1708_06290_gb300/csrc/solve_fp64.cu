@@ -149,6 +149,14 @@ __device__ __forceinline__ dw dw_sqrt(dw x) {
   const float e = fmaf(-s, s, x.hi) + x.lo;
   return dw_fast(s, e / (2.f * s));
 }
+// complex128 <-> double-float (re_hi, re_lo, im_hi, im_lo)
+__device__ __forceinline__ float4 df_split(cd z) {
+  const float rh = (float)z.x, ih = (float)z.y;
+  return make_float4(rh, (float)(z.x - (double)rh), ih, (float)(z.y - (double)ih));
+}
+__device__ __forceinline__ cd df_join(float4 w) {
+  return mkcd((double)w.x + (double)w.y, (double)w.z + (double)w.w);
+}
 
 // Solve shift sh of system d with the window state in Z2 (and ZT).  With RHS,
 // the dense right-hand side d.rhs(:, sh) is carried through the sweep: each
@@ -194,6 +202,18 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   cd* ZT = Z2 + (size_t)ldz * m;  // n x m, valid when track_t
   cd* Zr = ZT + (size_t)n * m;    // RHS rows in progress (n), when RHS
   cd* Tr = Zr + n;                // T rows of the removed finalised columns (n), when RHS
+  // With double-float updates the window state Z2 is kept as FP32 pairs
+  // (one float4 per complex entry, the size of a complex128), so the bulk
+  // update reads and writes it without FP64 conversions.
+  float4* const Z2f = reinterpret_cast<float4*>(Z2);
+  auto z2ld = [&](size_t idx) -> cd {
+    if constexpr (DF) return df_join(Z2f[idx]);
+    else return Z2[idx];
+  };
+  auto z2st = [&](size_t idx, cd v) {
+    if constexpr (DF) Z2f[idx] = df_split(v);
+    else Z2[idx] = v;
+  };
   const cd sigma = shifts[sh];
   // ||H - sigma I||_F from ||H||_F^2 and trace(H); a finalized diagonal entry
   // of magnitude <= n eps ||H - sigma I||_F marks the shift singular.
@@ -208,7 +228,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     double v = i < p ? Ct[i + (size_t)j * ldct] : H[(i - p) + (size_t)j * n];
     cd z = mkcd(v, 0.0);
     if (i - p == j) z = csub(z, sigma);
-    Z2[idx] = z;
+    z2st(idx, z);
   }
   if (track_t) {
     for (long long idx = tid; idx < (long long)n * m; idx += kThreads) {
@@ -335,7 +355,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
       };
       for (int idx = tid; idx < m * nbe; idx += kThreads) {
         int t = idx % nbe, q = idx / nbe;
-        cand4[q * kNB + t] = split4(Z2[(r + t) + (size_t)q * ldz]);
+        cand4[q * kNB + t] = Z2f[(r + t) + (size_t)q * ldz];
       }
       for (int idx = tid; idx < L::kCoefRows * S; idx += kThreads) {
         int c = idx / S, slot = idx % S;
@@ -608,7 +628,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
             }
           }
           for (int qq = 0; qq < m; ++qq) {
-            const cd zz = Z2[i + (size_t)qq * ldz];
+            const cd zz = df_join(Z2f[i + (size_t)qq * ldz]);
 #pragma unroll
             for (int q = 0; q < MAXM; ++q)
               if (q < m) acc[q] = cfma(zz, coefd(LB + qq, q), acc[q]);
@@ -632,9 +652,8 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
             }
           }
           for (int qq = 0; qq < m; ++qq) {
-            const cd zz = Z2[i + (size_t)qq * ldz];
-            const float zrh = (float)zz.x, zrl = (float)(zz.x - (double)zrh);
-            const float zih = (float)zz.y, zil = (float)(zz.y - (double)zih);
+            const float4 zz = Z2f[i + (size_t)qq * ldz];
+            const float zrh = zz.x, zrl = zz.y, zih = zz.z, zil = zz.w;
             const float4* cr = cf4 + (LB + qq) * S;
 #pragma unroll
             for (int q = 0; q < MAXM; ++q) {
@@ -648,6 +667,19 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
               }
             }
           }
+          const int cd_ = i - (r - m);  // diagonal correction of fresh column cd_
+          if (!(cd_ >= 0 && cd_ < min(m, nbe))) {
+            // normalised pairs straight back into the window state
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) {
+              if (q < m) {
+                const float sr = rh[q] + rl[q], si = ih[q] + il[q];
+                Z2f[i + (size_t)q * ldz] =
+                    make_float4(sr, rl[q] - (sr - rh[q]), si, il[q] - (si - ih[q]));
+              }
+            }
+            continue;
+          }
 #pragma unroll
           for (int q = 0; q < MAXM; ++q)
             acc[q] = mkcd((double)rh[q] + (double)rl[q], (double)ih[q] + (double)il[q]);
@@ -660,7 +692,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
         }
 #pragma unroll
         for (int q = 0; q < MAXM; ++q)
-          if (q < m) Z2[i + (size_t)q * ldz] = acc[q];
+          if (q < m) z2st(i + (size_t)q * ldz, acc[q]);
       }
     } else
     for (int i = tid; i < r; i += kThreads) {
@@ -774,7 +806,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   for (int idx = tid; idx < m * w2; idx += kThreads) {
     int i = idx % m, j = idx / m;
     cd v;
-    if (j < m) v = Z2[(p + i) + (size_t)j * ldz];
+    if (j < m) v = z2ld((p + i) + (size_t)j * ldz);
     else if (RHS) {
       v = Zr[i];
     } else if (bh != nullptr) {
@@ -845,7 +877,7 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
     for (int idx = tid; idx < p * nr; idx += kThreads) {
       int i = idx % p, q = idx / p;
       cd acc = mkcd(0.0, 0.0);
-      for (int t = 0; t < m; ++t) acc = cfma(Z2[i + (size_t)t * ldz], Yb[t + q * MAXM], acc);
+      for (int t = 0; t < m; ++t) acc = cfma(z2ld(i + (size_t)t * ldz), Yb[t + q * MAXM], acc);
       if (sing) acc = mkcd(nanv, nanv);
       o[i + (size_t)q * ldo] = mkcd(sg * acc.x, sg * acc.y);
     }
