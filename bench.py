@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
     ap.add_argument("--profile-reduce", type=int, default=0,
                     help="profiling case: one reduction of an n x n system (m = p = 8)")
+    ap.add_argument("--profile-resid", action="store_true",
+                    help="one tensor-core backward-error pass of the workload (for ncu)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling case: one solve on a handle restored from an m-Hessenberg "
                          "stand-in (H = triu(A, -m), R = triu(B), Ct = C), no reduction")
@@ -276,6 +278,55 @@ def batching_measurement(ssv, dev, args):
     return res
 
 
+def tensor_residual_roofline(n, m, s, mixed):
+    """BF16 tensor work of one certification pass of the mixed path: per shift and
+    128-row block I, 36 digit-slice products of 128 x 32 x (K from column I*128-m)."""
+    npad = (n + 127) // 128 * 128
+    k_total = sum(npad - (max(0, i0 - m) // 32) * 32 for i0 in range(0, npad, 128))
+    flops = 2.0 * 36 * 128 * 32 * k_total * s
+    ms = mixed["phase_ms_per_step"].get("mixed_residual", float("nan"))
+    peak = None
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        peak = 1900.0
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "tc_residual_kernel (+ digit split of Xhat)", "bound": "tensor",
+            "unit": "TFLOP/s", "achieved": ach, "peak": peak, "frac": ach / peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; of measured)",
+            "flops_per_pass": flops, "pass_ms": ms,
+            "flops_definition": "executed BF16 products: 36 slice pairs x 2 x 128 x 32 x K per "
+                                "(shift, 128-row block); K = npad - 32 floor((128 I - m) / 32)"}
+
+
+def profile_resid(args):
+    """The tensor-core backward error of the workload's first solve: split of H, split
+    of Xhat and tc_residual_kernel, after one double-float solve in mode xhat."""
+    import torch
+
+    from paper_1708_06290_gb300 import ssv
+
+    sysr, sig = W.workload_precision()
+    if args.shifts:
+        sig = sig[np.unique(np.linspace(0, len(sig) - 1, args.shifts).astype(int))]
+    m = sysr.m
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().cuda()  # noqa
+    h = ssv.load_reduced(dev(np.triu(sysr.A, -m)), dev(np.triu(sysr.B)), dev(sysr.C))
+    sd = torch.from_numpy(sig.astype(np.complex128)).cuda()
+    X, st, _ = h.solve(sd, mode="xhat", precision="dfloat")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    eta = h.backward_error(sd, X, method="tensor")
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "resid", "n": sysr.n, "m": m, "shifts": int(len(sig)),
+                      "ms": e0.elapsed_time(e1), "max_eta": float(eta.max().item()),
+                      "nonzero_status": int((st != 0).sum())}))
+    h.close()
+    return 0
+
+
 def profile_solve(args):
     """One solve of the workload's shifts on a restored stand-in handle: the solve
     kernels run after only the handful of launches that restore the handle."""
@@ -331,6 +382,8 @@ def main():
         return profile_reduce(args)
     if args.profile_solve:
         return profile_solve(args)
+    if args.profile_resid:
+        return profile_resid(args)
 
     import torch
     import torch.distributed as dist
@@ -499,11 +552,13 @@ def main():
                for prec in ("fp64", "mixed", "dfloat")},
             "precisions": {
                 "fp64": "every step in double / complex128",
-                "mixed": "first solve with double-float bulk updates, FP64-accurate (double-float) "
-                         "residual certifies every shift at backward error <= 1e-13, complex64 "
-                         "correction sweeps, FP64 re-solve of shifts that miss",
-                "dfloat": "FP64 panels, bulk updates in double-float (FP32 pairs), no refinement"},
+                "mixed": "first solve in double-float (FP32 pairs), FP64-accurate residual on the "
+                         "tensor cores (Ozaki-split BF16 digit slices, tcgen05) certifies every "
+                         "shift at backward error <= 1e-13, complex64 correction sweeps, FP64 "
+                         "re-solve of shifts that miss",
+                "dfloat": "panels and bulk updates in double-float (FP32 pairs), no refinement"},
             "fp32_ffma_peak_tflops": fp32_peak,
+            "tensor_residual_roofline": tensor_residual_roofline(n, m, s, res["mixed"]),
         },
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -197,6 +197,30 @@ int ssv_givens_schedule(int rows, int m, int* rot, int max_rot, int* off, int ma
 int ssv_tf_norm2(ssv_handle h, int s, const double* shifts, const ssv_opts* o, double* norms,
                  int* status, void* stream);
 
+/* residual methods of ssv_backward_error */
+#define SSV_RESID_FP64 0   /* FP64 products on the FP64 pipe */
+#define SSV_RESID_TENSOR 1 /* error-free BF16 digit splitting of H and Xhat (Ozaki
+                              scheme, 7-bit digits, 36 slice products accumulated
+                              exactly in FP32 on the tensor cores, combined in
+                              double-float): about 2^-50 of ||H|| ||Xhat||; m <= 16 */
+
+/*
+ * ssv_backward_error -- normwise backward error of caller-supplied solutions
+ * Xhat of (H - sigma_j I) Xhat = R (reduced coordinates, Sec. 2):
+ *   eta_j = ||(H - sigma_j I) Xhat_j - R||_F / (||H - sigma_j I||_F ||Xhat_j||_F + ||R||_F),
+ * the certificate that the mixed path's refinement tests against its tolerance.
+ *   xhat (device): complex128, shift j at xhat + 2 j m ldx doubles, n x m,
+ *     leading dimension ldx >= n (the SSV_XHAT output layout);
+ *   method: SSV_RESID_FP64 or SSV_RESID_TENSOR;
+ *   eta (device): s doubles (NaN when Xhat_j is not finite, or, for
+ *     SSV_RESID_TENSOR, when a bounded wait for the tensor cores gave up).
+ * Stream-ordered; scratch is allocated and freed on `stream`.
+ * Errors: SSV_EINVAL, SSV_ENOTSUP (SSV_RESID_TENSOR with m > 16), SSV_ENOMEM,
+ * SSV_ECUDA.
+ */
+int ssv_backward_error(ssv_handle h, int s, const double* shifts, const double* xhat,
+                       long long ldx, int method, double* eta, void* stream);
+
 /*
  * ssv_solve_many -- many reduced systems of uneven n, m and shift counts in
  * one persistent launch (FP64 and SSV_DFLOAT: one kernel over a cost-ordered

@@ -83,7 +83,8 @@ __global__ void residual_finish_kernel(int n, int m, int s, const double* __rest
   double m2 = hn[0] - 2.0 * sg.x * hn[1] + (double)n * (sg.x * sg.x + sg.y * sg.y);
   m2 = fmax(m2, 0.0);
   double den = sqrt(m2) * sqrt(acc[2 * sh + 1]) + sqrt(r2);
-  resid[sh] = den > 0 ? sqrt(acc[2 * sh]) / den : 0.0;
+  // a NaN denominator (non-finite Xhat) must not read as a zero backward error
+  resid[sh] = den > 0 ? sqrt(acc[2 * sh]) / den : (den == den ? 0.0 : den);
 }
 
 template <int MAXM>

@@ -702,8 +702,9 @@ __global__ void mixed_check_kernel(int n, int m, const double* __restrict__ R,
                                    const int* __restrict__ count, double* __restrict__ acc,
                                    double* __restrict__ eta, int* __restrict__ flags,
                                    const double* __restrict__ hnorm, int it, int max_refine,
-                                   double tol) {
+                                   double tol, const int* __restrict__ err) {
   const int cnt = *count;
+  const bool tc_failed = *err != 0;
   double r2 = 0.0;
   for (int q = 0; q < m; ++q)
     for (int i = 0; i <= q; ++i) r2 += R[i + (size_t)q * n] * R[i + (size_t)q * n];
@@ -714,7 +715,8 @@ __global__ void mixed_check_kernel(int n, int m, const double* __restrict__ R,
     acc[2 * (size_t)sh] = 0.0;
     acc[2 * (size_t)sh + 1] = 0.0;
     const double den = mn * sqrt(x2) + sqrt(r2);
-    const double e = den > 0.0 ? sqrt(e2) / den : 0.0;
+    // NaN (non-finite Xhat) stays NaN and fails below
+    const double e = den > 0.0 ? sqrt(e2) / den : (den == den ? 0.0 : den);
     const double prev = eta[sh];
     eta[sh] = e;
     int f = flags[sh];
@@ -723,7 +725,7 @@ __global__ void mixed_check_kernel(int n, int m, const double* __restrict__ R,
     // slower shifts go to the FP64 sweep at once instead of iterating.
     // a shift flagged singular goes to the FP64 re-solve (which reports it)
     // even when its backward error is small
-    if (f & kFlagSing) f |= kFlagFail;
+    if ((f & kFlagSing) || tc_failed) f |= kFlagFail;
     else if (e <= tol) f |= kFlagOk;
     else if (!(e == e) || it >= max_refine || (it > 0 && e > 0.25 * prev)) f |= kFlagFail;
     flags[sh] = f;
@@ -827,6 +829,9 @@ struct MixedScratch {
   int* fallback; // s
   int* st0;      // s: statuses of the first (double-float) solve
   int* count;    // 1
+  int* err;      // 1: a tensor-core residual wait gave up
+  unsigned char* tch;  // digit slices of H (tensor-core residual, m <= 16), or null
+  unsigned char* tcx;  // digit slices of Xhat for s shifts, or null
   size_t bytes;
 };
 
@@ -842,7 +847,10 @@ size_t mixed_layout(int n, int m, int s, int grid, size_t slot_bytes, MixedScrat
   size_t oX = take(sizeof(cd) * nm * s), oE = take(sizeof(cf) * nm * s);
   size_t oS = take(slot_bytes * grid), oA = take(sizeof(double) * 2 * s),
          oT = take(sizeof(double) * s), oF = take(sizeof(int) * s), oL = take(sizeof(int) * s),
-         oB = take(sizeof(int) * s), oS0 = take(sizeof(int) * s), oC = take(sizeof(int));
+         oB = take(sizeof(int) * s), oS0 = take(sizeof(int) * s), oC = take(sizeof(int)),
+         oR = take(sizeof(int));
+  const bool tc = m <= kTcMaxM;
+  const size_t oH = tc ? take(resid_tc_hbytes(n)) : 0, oXs = tc ? take(resid_tc_xbytes(n, s)) : 0;
   if (ms && base) {
     ms->X = reinterpret_cast<cd*>(base + oX);
     ms->E = reinterpret_cast<cf*>(base + oE);
@@ -854,6 +862,9 @@ size_t mixed_layout(int n, int m, int s, int grid, size_t slot_bytes, MixedScrat
     ms->fallback = reinterpret_cast<int*>(base + oB);
     ms->st0 = reinterpret_cast<int*>(base + oS0);
     ms->count = reinterpret_cast<int*>(base + oC);
+    ms->err = reinterpret_cast<int*>(base + oR);
+    ms->tch = tc ? base + oH : nullptr;
+    ms->tcx = tc ? base + oXs : nullptr;
     ms->bytes = off;
   }
   return off;
@@ -901,14 +912,29 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
   }
   trace_end(tr, st);
   const int rgrid = num_sms() * kResidBlocksPerSm;
+  SSV_CUDA_TRY(cudaMemsetAsync(ms.err, 0, sizeof(int), st));
+  if (ms.tch != nullptr) {
+    tr = trace_begin("mixed_split_h", st);
+    const int rc = resid_tc_split_h(h, ms.tch, st);
+    trace_end(tr, st);
+    if (rc != SSV_OK) return rc;
+  }
   for (int it = 0; it <= max_refine; ++it) {
     tr = trace_begin("mixed_residual", st);
-    mixed_residual_kernel<MAXM><<<rgrid, kRT, 0, st>>>(n, m, h->Hhi, h->Hlo, h->R, sd, ms.list,
-                                                      ms.count, ms.X, ms.E, ms.acc);
-    count_launch();
+    if (ms.tch != nullptr) {
+      // Ozaki-split BF16 products on the tensor cores (residual_tc.cu)
+      const int rc = resid_tc_run(h, ms.tch, ms.tcx, s, shifts, ms.list, ms.count,
+                                  reinterpret_cast<const double*>(ms.X), n, ms.E, ms.acc, ms.err, st);
+      if (rc != SSV_OK) return rc;
+    } else {
+      mixed_residual_kernel<MAXM><<<rgrid, kRT, 0, st>>>(n, m, h->Hhi, h->Hlo, h->R, sd, ms.list,
+                                                        ms.count, ms.X, ms.E, ms.acc);
+      count_launch();
+    }
     trace_end(tr, st);
     mixed_check_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(
-        n, m, h->R, sd, ms.list, ms.count, ms.acc, ms.eta, ms.flags, h->hnorm2, it, max_refine, tol);
+        n, m, h->R, sd, ms.list, ms.count, ms.acc, ms.eta, ms.flags, h->hnorm2, it, max_refine, tol,
+        ms.err);
     count_launch();
     mixed_compact_kernel<<<1, 1024, 0, st>>>(s, ms.flags, ms.list, ms.count);
     count_launch();

@@ -266,6 +266,22 @@ int ssv_tf_norm2(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_i
   return rc;
 }
 
+int ssv_backward_error(ssv_handle hh, int s, const double* shifts, const double* xhat,
+                       long long ldx, int method, double* eta, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || s < 0 || ldx < h->n) return SSV_EINVAL;
+  if (method != SSV_RESID_FP64 && method != SSV_RESID_TENSOR) return SSV_EINVAL;
+  if (s == 0) return SSV_OK;
+  if (!shifts || !xhat || !eta) return SSV_EINVAL;
+  if (method == SSV_RESID_TENSOR && h->m > kTcMaxM) return SSV_ENOTSUP;
+  cudaStream_t st = (cudaStream_t)stream;
+  void* tr = trace_begin("backward_error", st);
+  const int rc = method == SSV_RESID_TENSOR ? backward_error_tc(h, s, shifts, xhat, ldx, eta, st)
+                                            : backward_error_fp64(h, s, shifts, xhat, ldx, eta, st);
+  trace_end(tr, st);
+  return rc;
+}
+
 static int check_many(int nsys, const ssv_handle* hs, const int* s, const double* const* shifts,
                       const ssv_opts& o, double* const* outs, const long long* ldos) {
   if (nsys < 0 || (nsys > 0 && (!hs || !s || !shifts || !outs || !ldos))) return SSV_EINVAL;

@@ -145,6 +145,22 @@ int backward_error_fp64(const Handle* h, int s, const double* shifts, const doub
 int backward_error_fp64_masked(const Handle* h, int s, const double* shifts, const double* Xhat,
                                long long ldx, double* resid, const int* mask, cudaStream_t st);
 
+// FP64-accurate residual on the tensor cores (residual_tc.cu): Ozaki-split
+// BF16 digit slices of H (per row) and Xhat (per real column), m <= kTcMaxM.
+constexpr int kTcMaxM = 16;
+int resid_tc_npad(int n);
+size_t resid_tc_hbytes(int n);
+size_t resid_tc_xbytes(int n, int s);
+int resid_tc_split_h(const Handle* h, void* hbuf, cudaStream_t st);
+// E (complex64, n x m per shift, may be null) and acc += (||E||_F^2, ||Xhat||_F^2)
+// for the shifts list[0 .. *count); Xhat of shift j at Xhat + 2 j m ldx doubles
+int resid_tc_run(const Handle* h, const void* hbuf, void* xbuf, int s, const double* shifts,
+                 const int* list, const int* count, const double* Xhat, long long ldx, void* E,
+                 double* acc, int* err, cudaStream_t st);
+// normwise backward error of computed Xhat with the tensor-core residual
+int backward_error_tc(const Handle* h, int s, const double* shifts, const double* Xhat,
+                      long long ldx, double* eta, cudaStream_t st);
+
 // allocation-free FP64 solve on the library's fixed scratch array (solve_fp64.cu)
 int solve_fp64_noalloc(const Handle* h, int s, const double* shifts, const ssv_opts* o,
                        double* out, long long ldo, int* status, cudaStream_t st);

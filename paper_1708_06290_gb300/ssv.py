@@ -60,7 +60,8 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_last_cuda_error", "ssv_kernel_launches", "ssv_peak_probe", "ssv_load_reduced", "ssv_solve_noalloc", "ssv_solve_many",
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
            "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
-           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2")
+           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2",
+           "ssv_backward_error")
 
 _lib = None
 
@@ -93,6 +94,7 @@ def load(build_if_missing=True):
     L.ssv_solve_trans.argtypes = [P, I, P, P, LL, ctypes.POINTER(Opts), P, LL, P, P]
     L.ssv_givens_schedule.argtypes = [I, I, P, I, P, I, ctypes.POINTER(I)]
     L.ssv_tf_norm2.argtypes = [P, I, P, ctypes.POINTER(Opts), P, P, P]
+    L.ssv_backward_error.argtypes = [P, I, P, P, LL, I, P, P]
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.ssv_solve_many.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
                                  ctypes.POINTER(LL), PP, P]
@@ -110,7 +112,8 @@ def load(build_if_missing=True):
     L.ssv_trace_read.argtypes = [I, ctypes.c_char_p, I, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(I), ctypes.POINTER(I)]
     for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
-           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2"):
+           "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2",
+           "ssv_backward_error"):
         getattr(L, f).restype = I
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
@@ -324,6 +327,23 @@ class Handle:
                             _stream_ptr(stream))
         _check(rc, "ssv_tf_norm2")
         return norms, status
+
+    def backward_error(self, shifts, xhat, method="tensor", stream=None):
+        """Normwise backward error of solutions Xhat of (H - sigma_j I) Xhat = R per shift.
+        xhat: complex128 (n, s*m) CUDA tensor, column-major blocks (the mode "xhat"
+        output layout).  method "tensor" (Ozaki-split BF16 products on the tensor
+        cores) or "fp64".  Returns eta float64 (s,)."""
+        L = load()
+        _need_cuda(shifts, torch.complex128, "shifts")
+        _need_cuda(xhat, torch.complex128, "xhat")
+        s = shifts.numel()
+        meth = {"fp64": 0, "tensor": 1}[method]
+        eta = torch.empty(s, dtype=torch.float64, device=shifts.device)
+        rc = L.ssv_backward_error(self.ptr, s, ctypes.c_void_p(shifts.data_ptr()),
+                                  ctypes.c_void_p(xhat.data_ptr()), _ld(xhat, self.n), meth,
+                                  ctypes.c_void_p(eta.data_ptr()), _stream_ptr(stream))
+        _check(rc, "ssv_backward_error")
+        return eta
 
     def apply_q(self, xhat, out=None, stream=None):
         L = load()
