@@ -246,8 +246,24 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
   if (tid == 0) s_sing = 0;
   __syncthreads();
 
+  // Deferred T rows (X-hat output without per-step T updates).  The rows of
+  // the accumulated column transform T set at block step b are P1_b, and
+  // every later step multiplies all rows set before it by its P2, so
+  //   X-hat(rows of step b) = P1_b P2_{b+1} ... P2_B Y,
+  // which a backward pass z_B = Y, X-hat_b = P1_b z_b, z_{b-1} = P2_b z_b
+  // forms in O(n m^2) instead of O(n^2 m^2 / n_b) updates.  P1_b stays in ZT;
+  // P2_b (m x m) is parked in this shift's own output rows n - b m ..
+  // n - (b - 1) m - 1, which the backward pass reaches only after reading it
+  // when n_b >= m.
+  const bool defer_t = track_t && !RHS && d.bhat == nullptr && !d.flip_out && nb >= m;
+  cd* const tout = (mode == SSV_XHAT || mode == SSV_X) ? out + (size_t)sh * m * ldo
+                                                        : (xhat_copy != nullptr ? xhat_copy + (size_t)sh * m * ldxc : nullptr);
+  const long long tld = (mode == SSV_XHAT || mode == SSV_X) ? ldo : ldxc;
+  int nsteps = 0;
+
   int k = n;
   while (k > m) {
+    ++nsteps;
     const int nbe = min(nb, k - m);
     const int r = p + k - nbe;        // rows of [Ct; M] above the block
     const int j0 = k - m - nbe;       // first fresh column
@@ -736,7 +752,17 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
       for (int q = 0; q < MAXM; ++q)
         if (q < m) Z2[i + (size_t)q * ldz] = acc[q];
     }
-    if (track_t) {
+    if (defer_t) {
+      // rows j0 .. j0+nbe-1: ZT = P1; P2 parked in the output (see above)
+      for (int idx = tid; idx < nbe * m; idx += kThreads) {
+        const int i = j0 + idx % nbe, q = idx / nbe;
+        ZT[i + (size_t)q * n] = coefd(i - j0, q);
+      }
+      for (int idx = tid; idx < m * m; idx += kThreads) {
+        const int qq = idx % m, q = idx / m;
+        tout[(n - nsteps * m + qq) + (size_t)q * tld] = coefd(LB + qq, q);
+      }
+    } else if (track_t) {
       // rows k-m .. n-1: ZT <- ZT P2 ; rows j0 .. j0+nbe-1: ZT = P1
       const int lo = k - m;
       for (int i = j0 + tid; i < n; i += kThreads) {
@@ -882,7 +908,43 @@ __device__ void fp64_shift(const FpSys& d, const int sh, cd* __restrict__ Z2,
       o[i + (size_t)q * ldo] = mkcd(sg * acc.x, sg * acc.y);
     }
   }
-  if (track_t) {
+  if (defer_t) {
+    // backward pass: z = Y; per step b = B .. 1: X-hat rows of b = P1_b z,
+    // then z = P2_b z; finally the initial live rows n-m .. n-1 take z
+    cd* zs = cand;                // m x m (ld MAXM)
+    cd* p2s = zs + MAXM * MAXM;   // P2_b
+    cd* zn = p2s + MAXM * MAXM;   // P2_b z
+    static_assert(L::cand_elems >= 3 * MAXM * MAXM, "backward-pass scratch");
+    for (int e = tid; e < m * m; e += kThreads) zs[(e % m) + (e / m) * MAXM] = Yb[(e % m) + (e / m) * MAXM];
+    __syncthreads();
+    for (int b = nsteps; b >= 1; --b) {
+      const int kb = n - (b - 1) * nb;  // every step before the last takes nb rows
+      const int nbe_b = min(nb, kb - m);
+      const int j0b = kb - m - nbe_b;
+      for (int e = tid; e < m * m; e += kThreads)
+        p2s[(e % m) + (e / m) * MAXM] = tout[(n - b * m + e % m) + (size_t)(e / m) * tld];
+      __syncthreads();
+      for (int idx = tid; idx < nbe_b * m; idx += kThreads) {
+        const int i = j0b + idx % nbe_b, q = idx / nbe_b;
+        cd acc = mkcd(0.0, 0.0);
+        for (int t = 0; t < m; ++t) acc = cfma(ZT[i + (size_t)t * n], zs[t + q * MAXM], acc);
+        tout[i + (size_t)q * tld] = sing ? mkcd(nanv, nanv) : acc;
+      }
+      for (int e = tid; e < m * m; e += kThreads) {
+        const int rr = e % m, q = e / m;
+        cd acc = mkcd(0.0, 0.0);
+        for (int t = 0; t < m; ++t) acc = cfma(p2s[rr + t * MAXM], zs[t + q * MAXM], acc);
+        zn[rr + q * MAXM] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += kThreads) zs[(e % m) + (e / m) * MAXM] = zn[(e % m) + (e / m) * MAXM];
+      __syncthreads();
+    }
+    for (int e = tid; e < m * m; e += kThreads) {
+      const int rr = e % m, q = e / m;
+      tout[(n - m + rr) + (size_t)q * tld] = sing ? mkcd(nanv, nanv) : zs[rr + q * MAXM];
+    }
+  } else if (track_t) {
     cd* o;
     long long ld;
     if (mode == SSV_XHAT || mode == SSV_X) {

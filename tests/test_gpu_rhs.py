@@ -55,7 +55,7 @@ def test_solve_rhs_matches_dense_oracle_all_modes(n, m, p, nb):
         assert relerr(tf[:, j], -(sysr.C @ xo[j])) < REL_TOL, j
 
 
-def test_unit_coefficients_reproduce_the_multi_column_solve_exactly():
+def test_unit_coefficients_reproduce_the_multi_column_solve():
     sysr = W.random_system(210, 5, 3, seed=1301)
     sig = W.imag_axis_logspace(-1, 1, 6)
     h = ssv.reduce(dev(sysr.A), dev(sysr.B), dev(sysr.C))
@@ -68,7 +68,13 @@ def test_unit_coefficients_reproduce_the_multi_column_solve_exactly():
         xv, _ = h.solve_rhs(sd, _bhat_dev(e), mode="xhat")
         gv, _ = h.solve_rhs(sd, _bhat_dev(e), mode="g")
         for l in range(len(sig)):
-            assert torch.equal(xv[:, l], full[:, l * 5 + j])
+            # G: the same arithmetic, bit for bit.  X-hat: the multi-column sweep
+            # forms it by a backward pass over the stored block transforms
+            # (P1_b (P2_{b+1} (... Y))) while the one-column sweep accumulates T
+            # forward ((P1_b P2_{b+1} ...) Y): equal up to the association of
+            # the same products
+            a, b = xv[:, l].cpu().numpy(), full[:, l * 5 + j].cpu().numpy()
+            assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(b)
             assert torch.equal(gv[:, l], gfull[:, l * 5 + j])
 
 
