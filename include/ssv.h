@@ -54,7 +54,10 @@ extern "C" {
 
 /* ---- options ----------------------------------------------------------- */
 #define SSV_FP64 0  /* every step in double / complex128 */
-#define SSV_MIXED 1 /* complex64 elimination + FP64-accurate refinement */
+#define SSV_MIXED 1 /* double-float first solve, certified per shift by an
+                       FP64-accurate residual (tensor cores for m <= 16),
+                       complex64 correction sweeps, FP64 re-solve of shifts
+                       that miss the tolerance */
 #define SSV_DFLOAT 2 /* the window panels (reflectors formed in double-word
                         scalars) and the bulk updates of the rows above each
                         block (the Z1 P1 and Z2 P2 products, most of the work) in

@@ -3,15 +3,17 @@
 // R - (H - sigma I) Xhat is computed FP64-accurately.
 //
 // Per shift:
-//   1. first solve: the FP64 sweep of Sec. 3.1 / Algorithm 8 with its bulk
-//      updates (the rows above each block) in double-float on the FP32 pipe
-//      (SSV_DFLOAT), carrying the rows of the accumulated column
-//      transformation T (the "Q*" rows of Sec. 3.3) so that Xhat0 is formed;
-//   2. refinement: E = R - (H - sigma I) Xhat with H = Hhi + Hlo (two FP32
-//      words) and Xhat split the same way, each product formed exactly by an
-//      FMA and accumulated in double-float (Dekker/Knuth two-sum), giving
-//      ~48-bit residuals at FP32 throughput (native FP64 is 60x slower on
-//      this GPU); the normwise backward error decides convergence;
+//   1. first solve: the sweep of Sec. 3.1 / Algorithm 8 with its panels and
+//      bulk updates (the rows above each block) in double-float on the FP32
+//      pipe (SSV_DFLOAT); Xhat0 comes from the stored block transforms by a
+//      backward pass (the "Q*" rows of Sec. 3.3 without per-step updates);
+//   2. refinement residual: E = R - (H - sigma I) Xhat to FP64 accuracy.  For
+//      m <= 16 on the tensor cores (residual_tc.cu: error-free BF16 digit
+//      splitting of H and Xhat, exact FP32 accumulation per level); for wider
+//      m with H = Hhi + Hlo (two FP32 words) and Xhat split the same way, each
+//      product formed exactly by an FMA and accumulated in double-float
+//      (Dekker / Knuth two-sum).  The normwise backward error decides
+//      convergence;
 //   3. a correction sweep in complex64 solves (H - sigma I) D = E for the dense
 //      right-hand side E by carrying E as extra window columns that are
 //      back-substituted on the fly with each finalised column (the technique
