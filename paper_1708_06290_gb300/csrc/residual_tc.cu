@@ -19,8 +19,9 @@
 //
 // Persistent CTAs (two per SM) take work items of 128 rows of H and one
 // shift (N = 32 real columns, 2m of them live).  Per 32-deep K stage the
-// slices are copied into shared memory (cp.async, no-swizzle K-major
-// core-matrix layout); four threads (lane 0 of each warp, each owning two of
+// sixteen slice tiles (no-swizzle K-major core-matrix layout, stored tile by
+// tile in global memory) are copied into shared memory by one thread with
+// 1-D TMA bulk copies completing on an mbarrier; four threads (lane 0 of each warp, each owning two of
 // the eight levels) issue the 72 tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
 // M = 128, N = 32, K = 16) into eight TMEM accumulators (one per level, 32
 // columns each) and commit to their own mbarriers; after every fourth stage
@@ -41,7 +42,8 @@ constexpr int kN = 32;        // real columns per shift (2m, zero-padded)
 // of threads issuing them: one CTA per SM with two TMEM windows and the next
 // stage prefetched 208; two CTAs per SM, 16-deep stages, prefetched 142; two
 // CTAs per SM, 32-deep stages, one buffer 128, with two issuers 122, with four
-// 112 (the default); without the products at all 61 (staging and readout).
+// 112, and staged by TMA bulk copies instead of cp.async 106 (the default);
+// without the products at all 61 (staging by cp.async, and readout).
 #ifndef SSV_TC_KS
 #define SSV_TC_KS 32          // K per shared-memory stage (16 or 32)
 #endif
@@ -56,6 +58,9 @@ constexpr int kN = 32;        // real columns per shift (2m, zero-padded)
 #endif
 #ifndef SSV_TC_BUFFERS
 #define SSV_TC_BUFFERS 1      // 2: the next stage streams in during the products
+#endif
+#ifndef SSV_TC_BULK
+#define SSV_TC_BULK 1         // one buffer: stage with 1-D TMA bulk copies (else cp.async)
 #endif
 constexpr int kKS = SSV_TC_KS;  // K per shared-memory stage (16 or 32)
 constexpr int kSl = 8;        // digit slices of H and of Xhat
@@ -72,6 +77,7 @@ constexpr int kCtasPerSm = kTwoWin ? 1 : 2;
 constexpr uint32_t kStageBytes = (uint32_t)kSl * (kAT + kBT) * 2;
 constexpr int kBuf = SSV_TC_BUFFERS;  // 2: the next stage streams in during the products
 constexpr int kIss = SSV_TC_ISSUERS;  // threads issuing products (lane 0 of warps 0 ..)
+constexpr bool kBulk = SSV_TC_BULK != 0 && SSV_TC_BUFFERS == 1;
 static_assert(kIss == 1 || kIss == 2 || kIss == 4, "issuers");
 constexpr size_t kSmem = kBuf * (size_t)kStageBytes + 64;
 static_assert(kCtasPerSm * kSmem <= 227 * 1024, "shared memory of the resident CTAs");
@@ -281,6 +287,12 @@ __device__ __forceinline__ void fence_before() {
 __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// 1-D bulk copy global -> shared (TMA), completing `bytes` on the mbarrier
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -330,7 +342,7 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
   extern __shared__ __align__(128) unsigned char smem[];
   // two stage buffers, each: kSl H slice tiles (kAT) then kSl Xhat slice tiles (kBT)
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + kBuf * kStageBytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIss);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIss + 1);  // mbar[kIss]: stage loads
   __shared__ double red[2][kM / 32];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int KT = npad / kKS, RB = npad / kM;
@@ -344,32 +356,47 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int q = 0; q < kIss; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
+    for (int q = 0; q <= kIss; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  uint32_t phase = 0;
+  uint32_t phase = 0, lphase = 0;
+  const uint32_t lmb = mb + 8u * kIss;
   bool failed = false;
   float ah[kN], al[kN];
   // copy the slice tiles of K stage J of (row block I, shift sh) into buffer b
   auto stage_in = [&](int I, int sh, int J, int b) {
     const uint32_t dst = sBase + (uint32_t)b * kStageBytes;
-    for (int v = tid; v < kSl * (kAT + kBT) / 8; v += kM) {
-      const uint4* src;
-      if (v < kSl * kAT / 8) {
-        const int k = v / (kAT / 8), o = v % (kAT / 8);
-        src = Hs + ((size_t)(k * RB + I) * KT + J) * (kAT / 8) + o;
-      } else {
-        const int vb = v - kSl * kAT / 8;
-        const int l = vb / (kBT / 8), o = vb % (kBT / 8);
-        src = Xs + ((size_t)(sh * kSl + l) * KT + J) * (kBT / 8) + o;
+    if constexpr (kBulk) {
+      // sixteen contiguous tiles: one thread, sixteen TMA bulk copies
+      if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lmb), "r"(kStageBytes)
+                     : "memory");
+        for (int k = 0; k < kSl; ++k)
+          bulk_copy(dst + (uint32_t)(k * kAT * 2), Hs + ((size_t)(k * RB + I) * KT + J) * (kAT / 8),
+                    (uint32_t)(kAT * 2), lmb);
+        for (int l = 0; l < kSl; ++l)
+          bulk_copy(dst + (uint32_t)(kSl * kAT * 2 + l * kBT * 2),
+                    Xs + ((size_t)(sh * kSl + l) * KT + J) * (kBT / 8), (uint32_t)(kBT * 2), lmb);
       }
-      cp16(dst + (uint32_t)v * 16u, src);
+    } else {
+      for (int v = tid; v < kSl * (kAT + kBT) / 8; v += kM) {
+        const uint4* src;
+        if (v < kSl * kAT / 8) {
+          const int k = v / (kAT / 8), o = v % (kAT / 8);
+          src = Hs + ((size_t)(k * RB + I) * KT + J) * (kAT / 8) + o;
+        } else {
+          const int vb = v - kSl * kAT / 8;
+          const int l = vb / (kBT / 8), o = vb % (kBT / 8);
+          src = Xs + ((size_t)(sh * kSl + l) * KT + J) * (kBT / 8) + o;
+        }
+        cp16(dst + (uint32_t)v * 16u, src);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
   };
   // levels of one accumulation window (TMEM half `half`) into the double-float sums
   auto read_window = [&](uint32_t half) {
@@ -402,9 +429,19 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
     for (int st = 0; st < nst; ++st) {
       const int b = kBuf == 2 ? (st & 1) : 0;
       if (kBuf == 1) stage_in(I, sh, J0 + st, 0);
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
+      if constexpr (kBulk) {
+        // the tiles land through the async proxy that the products read
+        const bool lok = mbar_wait(lmb, lphase);
+        lphase ^= 1u;
+        if (__syncthreads_or(!lok)) {
+          failed = true;
+          break;
+        }
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+      }
       const uint32_t half = kTwoWin ? (uint32_t)(((st / kWin) & 1) * kLev * kN) : 0u;
       const int iss = tid >> 5;
       if ((tid & 31) == 0 && iss < kIss) {
@@ -524,6 +561,7 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
     if (tid == 0) {
       atomicExch(err, 1);
       for (int q = 0; q < kIss; ++q) mbar_wait(mb + 8u * q, phase ^ 1u);
+      if (kBulk) mbar_wait(lmb, lphase ^ 1u);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
