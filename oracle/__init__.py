@@ -18,6 +18,8 @@ All arithmetic is IEEE double (complex128), done in ``csrc/ssv_oracle.c``:
 * :func:`reduced_solve` -- Xhat = (H - sigma I)^{-1} R (or G = Ct Xhat) by
   band-limited Gaussian elimination with row pivoting in reduced coordinates,
   plus an optional Hager/Higham estimate of kappa_1(H - sigma I).
+* :func:`backward_error` -- the normwise backward error of a given Xhat for
+  (H - sigma I) Xhat = R (numpy; optionally with a longdouble residual).
 
 :mod:`oracle.givens` holds the greedy Givens annihilation schedule of
 Algorithm 9 (plain Python), pinned by the paper's worked example in
@@ -175,10 +177,27 @@ def tf_norm2(G):
     return np.array([np.linalg.svd(g, compute_uv=False)[0] for g in G])
 
 
-def backward_error(Mfun_H, sigma, X, R):
-    """Normwise backward error ||(H - sigma I)X - R||_F / (||H - sigma I||_F ||X||_F + ||R||_F)."""
-    H = np.asarray(Mfun_H)
+def backward_error(H, sigma, X, R, extended=False):
+    """Normwise backward error of X as a solution of the reduced system
+    (H - sigma I) X = R (Sec. 2), the quantity the mixed path certifies:
+
+        ||(H - sigma I) X - R||_F / (||H - sigma I||_F ||X||_F + ||R||_F).
+
+    H real n x n, R n x m, X n x m complex.  With ``extended`` the residual is
+    formed in numpy longdouble (real and imaginary parts separately), for
+    residuals far below FP64 rounding of the products."""
+    H = np.asarray(H, dtype=np.float64)
     n = H.shape[0]
+    X = np.asarray(X, dtype=np.complex128)
+    R = np.asarray(R)
     M = H.astype(np.complex128) - sigma * np.eye(n)
-    res = M @ X - R
-    return np.linalg.norm(res) / (np.linalg.norm(M) * np.linalg.norm(X) + np.linalg.norm(R))
+    if extended:
+        Hl = H.astype(np.longdouble)
+        xr, xi = X.real.astype(np.longdouble), X.imag.astype(np.longdouble)
+        sr, si = np.longdouble(np.real(sigma)), np.longdouble(np.imag(sigma))
+        er = Hl @ xr - (sr * xr - si * xi) - np.real(R).astype(np.longdouble)
+        ei = Hl @ xi - (sr * xi + si * xr) - np.imag(R).astype(np.longdouble)
+        rn = float(np.sqrt(np.sum(er * er + ei * ei)))
+    else:
+        rn = np.linalg.norm(M @ X - R)
+    return rn / (np.linalg.norm(M) * np.linalg.norm(X) + np.linalg.norm(R))

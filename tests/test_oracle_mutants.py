@@ -149,3 +149,62 @@ def test_givens_schedule_mutant_is_caught(name):
     except Exception:
         return
     assert got != gold, "mutant %s reproduces the figure" % name
+
+
+BACKWARD_ERROR_MUTANTS = {
+    "shift_sign": ("M = H.astype(np.complex128) - sigma * np.eye(n)", "M = H.astype(np.complex128) + sigma * np.eye(n)"),
+    "rhs_dropped": ("rn = np.linalg.norm(M @ X - R)", "rn = np.linalg.norm(M @ X)"),
+    "rhs_norm_dropped": ("/ (np.linalg.norm(M) * np.linalg.norm(X) + np.linalg.norm(R))",
+                         "/ (np.linalg.norm(M) * np.linalg.norm(X))"),
+    "ext_coupling_sign": ("er = Hl @ xr - (sr * xr - si * xi)", "er = Hl @ xr - (sr * xr + si * xi)"),
+    "ext_imag_shift": ("ei = Hl @ xi - (sr * xi + si * xr)", "ei = Hl @ xi - (sr * xi)"),
+}
+
+
+def _backward_error_checks(fn):
+    """The backward-error pins of test_oracle_pins, as a list of failures."""
+    from tests import test_oracle_pins as P
+    fails = []
+    H = P._triu_band(30, 3, 1)
+    R = np.triu(np.random.default_rng(2).standard_normal((30, 3)))
+    for ext in (False, True):
+        try:
+            if abs(fn(H, 0.4j, np.zeros((30, 3), complex), R, extended=ext) - 1.0) > 1e-15:
+                fails.append("zero %s" % ext)
+        except ZeroDivisionError:
+            fails.append("zero %s raised" % ext)
+    n, m = 40, 3
+    H = P._triu_band(n, m, 4)
+    R = np.triu(np.random.default_rng(5).standard_normal((n, m)))
+    s = 0.3 - 0.8j
+    M = H - s * np.eye(n)
+    import scipy.linalg
+    X = scipy.linalg.solve(M, R.astype(complex))
+    delta = 1e-5 * (2 - 1j)
+    X[17, 2] += delta
+    den = np.linalg.norm(M) * np.linalg.norm(X) + np.linalg.norm(R)
+    want = abs(delta) * np.linalg.norm(M[:, 17]) / den
+    for ext in (False, True):
+        if abs(fn(H, s, X, R, extended=ext) - want) > 1e-9 * want:
+            fails.append("single entry %s" % ext)
+    return fails
+
+
+def _backward_error_variant(old, new):
+    import inspect
+    src = inspect.getsource(oracle.backward_error)
+    assert src.count(old) == 1, old
+    ns = {"np": np}
+    exec(compile(src.replace(old, new), "backward_error_mutant", "exec"), ns)
+    return ns["backward_error"]
+
+
+def test_real_backward_error_passes_its_checks():
+    assert _backward_error_checks(oracle.backward_error) == []
+
+
+@pytest.mark.parametrize("name", sorted(BACKWARD_ERROR_MUTANTS))
+def test_backward_error_mutant_is_caught(name):
+    fn = _backward_error_variant(*BACKWARD_ERROR_MUTANTS[name])
+    with np.errstate(divide="ignore", invalid="ignore"):  # a mutant may divide by zero
+        assert _backward_error_checks(fn) != [], "mutant %s survived every pin" % name

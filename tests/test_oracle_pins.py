@@ -439,3 +439,61 @@ def test_tf_norm2_single_input_is_the_vector_norm(ora):
     for j, zz in enumerate(z):
         g = sysd.C @ (-sysd.B[:, 0] / (zz - a))  # C (A - zI)^{-1} b
         assert abs(nrm[j] - np.sqrt(np.sum(np.abs(g) ** 2))) <= 1e-13 * nrm[j]
+
+
+# --------------------------------------------------------------------------
+# backward_error: ||(H - sigma I) X - R|| / (||H - sigma I|| ||X|| + ||R||)
+# --------------------------------------------------------------------------
+
+def _triu_band(n, m, seed):
+    rng = np.random.default_rng(seed)
+    return np.triu(rng.standard_normal((n, n)) / np.sqrt(n), -m) - 2.0 * np.eye(n)
+
+
+@pytest.mark.parametrize("extended", [False, True])
+def test_backward_error_of_zero_is_one(ora, extended):
+    """X = 0 leaves the whole right-hand side as residual: eta = ||R|| / ||R|| = 1."""
+    H = _triu_band(30, 3, 1)
+    R = np.triu(np.random.default_rng(2).standard_normal((30, 3)))
+    assert ora.backward_error(H, 0.4j, np.zeros((30, 3), complex), R, extended=extended) == pytest.approx(1.0, abs=1e-15)
+
+
+@pytest.mark.parametrize("extended", [False, True])
+def test_backward_error_diagonal_closed_form_solution(ora, extended):
+    """Diagonal H: X = R / (d - sigma) row by row solves the system; its backward
+    error is at the rounding level of the division."""
+    n, m = 50, 4
+    d = np.linspace(-3.0, -1.0, n)
+    R = np.random.default_rng(3).standard_normal((n, m))
+    s = -1.7 + 0.2j
+    X = R / (d - s)[:, None]
+    assert ora.backward_error(np.diag(d), s, X, R, extended=extended) <= 4 * EPS
+
+
+@pytest.mark.parametrize("j,q", [(0, 0), (17, 2), (39, 1)])
+def test_backward_error_single_entry_perturbation(ora, j, q):
+    """X' = X + delta e_j e_q^T for the exact-enough X: the residual is
+    -(H - sigma I) e_j delta, so eta = |delta| ||(H - sigma I) e_j|| / den."""
+    n, m = 40, 3
+    H = _triu_band(n, m, 4)
+    R = np.triu(np.random.default_rng(5).standard_normal((n, m)))
+    s = 0.3 - 0.8j
+    M = H - s * np.eye(n)
+    X = scipy.linalg.solve(M, R.astype(complex))
+    delta = 1e-5 * (2 - 1j)
+    Xp = X.copy()
+    Xp[j, q] += delta
+    den = np.linalg.norm(M) * np.linalg.norm(Xp) + np.linalg.norm(R)
+    want = abs(delta) * np.linalg.norm(M[:, j]) / den
+    for ext in (False, True):
+        assert ora.backward_error(H, s, Xp, R, extended=ext) == pytest.approx(want, rel=1e-9)
+
+
+def test_backward_error_extended_agrees_with_fp64_for_large_residuals(ora):
+    H = _triu_band(60, 5, 6)
+    rng = np.random.default_rng(7)
+    R = np.triu(rng.standard_normal((60, 5)))
+    X = rng.standard_normal((60, 5)) + 1j * rng.standard_normal((60, 5))
+    a = ora.backward_error(H, -1.1 + 0.5j, X, R)
+    b = ora.backward_error(H, -1.1 + 0.5j, X, R, extended=True)
+    assert a == pytest.approx(b, rel=1e-13)
