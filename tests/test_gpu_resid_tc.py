@@ -2,8 +2,8 @@
 36 slice products accumulated exactly in FP32 by tcgen05.mma) behind
 ssv_backward_error(SSV_RESID_TENSOR) and the mixed path's certification.
 
-References: the backward error computed on the host in extended precision
-(numpy longdouble) from the handle's own H and R; the FP64-pipe method of the
+References: the oracle's backward error with its residual in extended
+precision (numpy longdouble), from the handle's own H and R; the FP64-pipe method of the
 same entry point at the full benchmark size; and closed forms -- perturbing one
 entry of an exact-enough solution by delta changes the residual by exactly
 delta times a column of H - sigma I.
@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import workloads as W
 from paper_1708_06290_gb300 import ssv
 from tests.gpu_util import dev, shifts_dev
@@ -26,26 +27,11 @@ ETA_ABS = 5e-15
 
 
 def eta_ext(H, R, sig, X, m):
-    """Backward error per shift in numpy longdouble (extended / quad precision)."""
-    n = H.shape[0]
-    Hl = np.triu(H, -m).astype(np.longdouble)
-    Rl = R.astype(np.longdouble)
-    r2 = float(np.sum(np.triu(R[:m, :m]) ** 2))
-    fro2 = float(np.sum(np.triu(H, -m) ** 2))
-    tr = float(np.trace(H))
-    out = []
-    for j, s in enumerate(sig):
-        Xj = X[:, j * m:(j + 1) * m]
-        xr = Xj.real.astype(np.longdouble)
-        xi = Xj.imag.astype(np.longdouble)
-        sr, si = np.longdouble(s.real), np.longdouble(s.imag)
-        er = Hl @ xr - (sr * xr - si * xi) - Rl
-        ei = Hl @ xi - (sr * xi + si * xr)
-        e2 = float(np.sum(er * er + ei * ei))
-        m2 = max(fro2 - 2.0 * s.real * tr + n * abs(s) ** 2, 0.0)
-        den = np.sqrt(m2) * np.linalg.norm(Xj) + np.sqrt(r2)
-        out.append(np.sqrt(e2) / den)
-    return np.array(out)
+    """Backward error per shift from the oracle, residual in numpy longdouble,
+    on the structural part of H (rows <= column + m)."""
+    Hs = np.triu(H, -m)
+    return np.array([oracle.backward_error(Hs, s, X[:, j * m:(j + 1) * m], R, extended=True)
+                     for j, s in enumerate(sig)])
 
 
 def setup(n, m, p, seed, sig):
