@@ -94,8 +94,9 @@ typedef struct ssv_handle_s* ssv_handle;
 
 /* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 8,
  * tol = 1e-13, panel = SSV_PANEL_HOUSEHOLDER.  (The mixed path certifies each
- * shift with a double-float residual whose own error is about 1e-14 of
- * ||H - sigma I|| ||Xhat||; 1e-13 leaves a 10x margin above it.) */
+ * shift with a residual whose own error, as a backward error, is below 5e-15
+ * for m <= 16 (the tensor-core residual) and about 1e-14 for wider m (the
+ * double-float residual); 1e-13 stays above both.) */
 void ssv_default_opts(ssv_opts* o);
 
 /*
@@ -281,22 +282,29 @@ int ssv_autotune(ssv_handle h, int s, const double* shifts, const ssv_opts* o, d
  * device memory during their step, a device-memory budget fixed in advance,
  * or a latency-critical loop where an allocation may not stall or fail).
  *
- *   Same arguments and results as ssv_solve with precision SSV_FP64 and mode
- *   SSV_G, SSV_TF or SSV_XHAT; no resid output.  The handle, shifts, out and
- *   status are the caller's, allocated beforehand.
- *   Scratch: a fixed 64 MiB array inside the library, present on every GPU
- *   that loads the library until the process exits.  One shift's window needs
- *   16 * (p + n) * m bytes (plus 16 * n * m for SSV_XHAT); sizes where that
- *   exceeds 64 MiB return SSV_ESCRATCH, and smaller sizes run with as many
- *   thread blocks as fit (fewer than ssv_solve uses when n * m is large).
+ *   Same arguments and results as ssv_solve with precision SSV_FP64, the
+ *   Householder panel and mode SSV_G, SSV_TF or SSV_XHAT (the same n_b as
+ *   ssv_solve, an autotuned one included, so the results agree); there is no
+ *   resid output.  The handle, shifts, out and status are the caller's,
+ *   allocated beforehand.
+ *   Scratch: a fixed 64 MiB array inside the library.  It is part of the
+ *   module that holds the FP64 solve kernels, so it is reserved on every GPU
+ *   where any FP64 or double-float solve (not only this entry point) has run,
+ *   until the process exits.  One shift's window needs 16 * (p + n) * m bytes
+ *   (plus 16 * n * m for SSV_XHAT); sizes where that exceeds 64 MiB return
+ *   SSV_ESCRATCH, and smaller sizes run with as many thread blocks as fit
+ *   (fewer than ssv_solve uses when n * m is large; each then solves more
+ *   shifts in turn).
  *   The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) and caches it; make that first call before any
- *   stream capture.
+ *   (cudaGetSymbolAddress) and caches it; under lazy module loading that
+ *   lookup may load the module, which allocates device memory.  Make the
+ *   first call outside any region where allocation is forbidden, and before
+ *   any stream capture.
  *   Every call uses the same array and leaves its contents behind: calls
  *   whose executions overlap on the GPU (different streams, or different host
  *   threads) race on it and give wrong results; serialize them.
- * Errors: SSV_EINVAL, SSV_ENOTSUP (precision, mode, m > 32, resid requested),
- * SSV_ESCRATCH, SSV_ECUDA.
+ * Errors: SSV_EINVAL, SSV_ENOTSUP (precision, mode, panel other than
+ * SSV_PANEL_HOUSEHOLDER, m > 32), SSV_ESCRATCH, SSV_ECUDA.
  */
 int ssv_solve_noalloc(ssv_handle h, int s, const double* shifts, const ssv_opts* o, double* out,
                       long long ldo, int* status, void* stream);

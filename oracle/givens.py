@@ -12,14 +12,18 @@ Labels, as in Algorithm 9:
   ready      (r, c) in the band r <= c <= r + delta, not yet zeroed and not
              serving as a partner in the current step;
   available  may take part now: initially every entry of the bottom row and
-             every diagonal entry (r, r) (reading R6: "and" in the printed
-             initialisation read as "or"); an entry above a zeroed one becomes
+             every diagonal entry (r, r) (the printed initialisation joins the
+             two conditions with "and"; it is read as "or", the only reading
+             that reproduces the paper's 13-step worked example); an entry
+             above a zeroed one becomes
              available at the start of the step after that zeroing.
 Each step scans the rows from the bottom; in row r, for c1 ascending, the first
 ready-and-available (r, c1) is paired with the ready-and-available (r, c2)
 with the largest c2 > c1; (r, c1) is then retired, (r, c2) is busy until the
 step ends, and (r-1, c1) waits for the next step.  The loop ends with the first
-step that schedules nothing (reading R7: every step found is executed).
+step that schedules nothing, and every step found is executed (the loop of
+Algorithm 10 is read as running over all of Algorithm 9's steps; stopping one
+short would skip the last rotation of the worked example).
 """
 
 
@@ -27,7 +31,7 @@ def greedy_schedule(n_rows, n_cols, initial="bottom_or_diagonal"):
     """Return the list of steps; each step is a list of (r, c1, c2), 1-based.
 
     `initial` selects the reading of Algorithm 9's initialisation:
-    "bottom_or_diagonal" (R6) or "bottom_only" (the literal alternative, kept
+    "bottom_or_diagonal" (the "or" reading above) or "bottom_only" (the literal alternative, kept
     for the test that shows it does not reproduce the paper's figure).
     """
     delta = n_cols - n_rows

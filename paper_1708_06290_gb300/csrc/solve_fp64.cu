@@ -1374,50 +1374,47 @@ int solve_fp64_trans(const Handle* h, int s, const double* shifts, const double*
   return rc;
 }
 // ---------------------------------------------------------------------------
-// Givens panel (Sec. 3.2): greedy annihilation schedule of Algorithm 9 for a
-// block of `rows` rows and rows + m columns, computed on the host once per
-// shape and device and kept in device memory.
+// Givens panel (Sec. 3.2): the greedy annihilation schedule for a block of
+// `rows` rows and rows + m columns, computed on the host once per shape and
+// device and kept in device memory.
 //
-// Row r (0-based) of the block holds nonzeros in columns r .. rows + m - 1;
-// the entries (r, c), r <= c < r + m, are zeroed, each by a rotation with a
-// partner (r, c2), c2 <= r + m, so that (r, r + m) remains.  An entry may take
-// part in a step when it is "ready" (in the band, not zeroed, not already a
-// partner in this step) and "available": every entry of the bottom row and
-// every (r, r) from the start, the entry above a zeroed one from the step
-// after.  Each step scans rows bottom-up and, in a row, pairs each candidate
-// c1 (ascending) with the largest free partner c2 > c1.
+// Row r (0-based) of the block holds nonzeros in columns r .. r + m; every
+// entry but the last of a row is zeroed by a rotation with another entry of
+// the same row, rotations of one step touching disjoint columns.  Seen per
+// column, the entries that may be rotated form a frontier moving up: column c
+// starts at its lowest band entry (row min(c, rows - 1)), and once the
+// frontier entry of c is zeroed the entry above it joins in the next step;
+// column c never rises above row c - m, where it survives as the diagonal of
+// the triangular factor.  A step therefore looks at each row's frontier
+// columns c_1 < ... < c_k and zeroes as many as the greedy choice allows:
+// c_1 with the partner c_k, c_2 with c_(k-1), and so on, the middle one of an
+// odd count waiting.  Steps are emitted rows from the bottom, zeroed columns
+// ascending within a row, until a step finds no pair.
 // ---------------------------------------------------------------------------
 void greedy_rows(int rows, int m, std::vector<int>* rot, std::vector<int>* off) {
-  const int w = m + 1;  // band width per row
-  std::vector<char> ready((size_t)rows * w, 1), avail((size_t)rows * w, 0);
-  auto at = [w](int r, int c) { return (size_t)r * w + (c - r); };
-  for (int r = 0; r < rows; ++r)
-    for (int c = r; c <= r + m; ++c) avail[at(r, c)] = (r == rows - 1 || c == r) ? 1 : 0;
-  std::vector<std::pair<int, int>> busy, zeroed;
+  const int cols = rows + m;
+  // front[c]: row of column c's frontier entry; -1 once the column is empty
+  std::vector<int> front(cols);
+  for (int c = 0; c < cols; ++c) front[c] = std::min(c, rows - 1);
+  std::vector<std::vector<int>> at_row(rows);
+  std::vector<int> zeroed;
   rot->clear();
   off->assign(1, 0);
   for (;;) {
-    for (auto& b : busy) ready[at(b.first, b.second)] = 1;
-    for (auto& z : zeroed)
-      if (z.first > 0) avail[at(z.first - 1, z.second)] = 1;
-    busy.clear();
+    for (auto& v : at_row) v.clear();
+    for (int c = 0; c < cols; ++c)
+      if (front[c] >= 0) at_row[front[c]].push_back(c);  // ascending in c
     zeroed.clear();
     for (int r = rows - 1; r >= 0; --r) {
-      for (int c1 = r; c1 <= r + m; ++c1) {
-        if (!(ready[at(r, c1)] && avail[at(r, c1)])) continue;
-        for (int c2 = r + m; c2 > c1; --c2) {
-          if (!(ready[at(r, c2)] && avail[at(r, c2)])) continue;
-          rot->push_back(r | (c1 << 8) | (c2 << 16));
-          ready[at(r, c1)] = 0;
-          ready[at(r, c2)] = 0;
-          busy.push_back({r, c2});
-          if (r > 0) avail[at(r - 1, c1)] = 0;
-          zeroed.push_back({r, c1});
-          break;
-        }
+      const std::vector<int>& e = at_row[r];
+      const int k = (int)e.size();
+      for (int i = 0; i < k / 2; ++i) {
+        rot->push_back(r | (e[i] << 8) | (e[k - 1 - i] << 16));
+        zeroed.push_back(e[i]);
       }
     }
-    if ((int)rot->size() == off->back()) break;  // empty step: done
+    if (zeroed.empty()) break;
+    for (int c : zeroed) front[c] -= 1;  // the entry above joins next step
     off->push_back((int)rot->size());
   }
 }
@@ -1548,11 +1545,15 @@ int solve_fp64_givens(const Handle* h, int s, const double* shifts, const ssv_op
 // allocates nothing: no cudaMalloc / cudaMallocAsync / cudaFree and no
 // allocating library routine.
 //
-// The array below holds kNoAllocScratchBytes (64 MiB) on every GPU that loads
-// the library, for as long as the process lives.  In host code its name is
-// only a host-side stand-in, so the device address is looked up once per
-// device with cudaGetSymbolAddress (with that device current) and cached;
-// the first call on each device performs that lookup.
+// The array below holds kNoAllocScratchBytes (64 MiB) on every GPU where this
+// translation unit's module is loaded, for as long as the process lives: any
+// FP64 or double-float solve loads the module, so the 64 MiB is taken by
+// those callers too, not only by callers of ssv_solve_noalloc.  In host code
+// the array's name is only a host-side stand-in, so the device address is
+// looked up once per device with cudaGetSymbolAddress (with that device
+// current) and cached; the first call on each device performs that lookup,
+// which under lazy module loading may itself load the module (an implicit
+// device allocation).
 // ---------------------------------------------------------------------------
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -1620,7 +1621,9 @@ size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
 int solve_fp64_noalloc(const Handle* h, int s, const double* shifts, const ssv_opts* o,
                        double* out, long long ldo, int* status, cudaStream_t st) {
   const int m = h->m;
-  const int nb = o->nb > 0 ? o->nb : default_nb(h->n, m);
+  // the same block width as ssv_solve (an autotuned choice included), so the
+  // two entry points give the same results
+  const int nb = o->nb > 0 ? o->nb : tuned_nb(h->n, m, h->p, SSV_FP64, o->mode);
   if (nb > kNB) return SSV_ENOTSUP;
   if (s == 0) return SSV_OK;
   if (m <= 1) return launch_solve_noalloc<1>(h, s, shifts, nb, o->mode, out, ldo, status, st);

@@ -386,6 +386,7 @@ int ssv_solve_noalloc(ssv_handle hh, int s, const double* shifts, const ssv_opts
   int rc = check_opts(&o);
   if (rc != SSV_OK) return rc;
   if (o.precision != SSV_FP64 || o.mode == SSV_X) return SSV_ENOTSUP;
+  if (o.panel != SSV_PANEL_HOUSEHOLDER) return SSV_ENOTSUP;
   if (h->m > 32) return SSV_ENOTSUP;
   if (s == 0) return SSV_OK;
   if (!shifts || !out) return SSV_EINVAL;

@@ -20,3 +20,11 @@ def test_library_schedule_equals_the_oracle(rows, m):
 def test_bad_sizes_are_refused():
     with pytest.raises(ssv.SsvError):
         ssv.givens_schedule(0, 4)
+
+
+def test_library_schedule_equals_the_oracle_on_every_small_shape():
+    # the library's column-frontier formulation and the oracle's label-based
+    # one are written independently; they must agree on every block shape
+    for rows in range(1, 25):
+        for m in range(1, 13):
+            assert ssv.givens_schedule(rows, m) == greedy_schedule(rows, rows + m), (rows, m)

@@ -23,12 +23,12 @@ pytestmark = pytest.mark.gpu
 REL_TOL = 1e-10
 
 
-def _noalloc(h, shifts, mode, ldo_rows, nb=0):
+def _noalloc(h, shifts, mode, ldo_rows, nb=0, panel="householder"):
     lib = ssv.load()
     s = shifts.numel()
     out = torch.full((s * h.m, ldo_rows), float("nan"), dtype=torch.complex128, device="cuda").t()
     status = torch.full((s,), -7, dtype=torch.int32, device="cuda")
-    o = ssv.opts("fp64", mode, nb=nb)
+    o = ssv.opts("fp64", mode, nb=nb, panel=panel)
     rc = lib.ssv_solve_noalloc(h.ptr, s, ctypes.c_void_p(shifts.data_ptr()), ctypes.byref(o),
                                ctypes.c_void_p(out.data_ptr()), ldo_rows,
                                ctypes.c_void_p(status.data_ptr()),
@@ -82,5 +82,42 @@ def test_noalloc_refuses_unsupported_options():
     h = ssv.reduce(dev(sysr.A), dev(sysr.B), dev(sysr.C))
     rc, _, _ = _noalloc(h, shifts_dev([0.5j]), "x", sysr.n)
     assert rc == ssv.SSV_ENOTSUP
+    # only the Householder panel runs on the fixed scratch; the Givens panel is refused
+    rc, _, _ = _noalloc(h, shifts_dev([0.5j]), "g", sysr.p, panel="givens")
+    assert rc == ssv.SSV_ENOTSUP
     lib = ssv.load()
     assert b"64 MiB" in lib.ssv_strerror(ssv.SSV_ESCRATCH)
+
+
+@pytest.mark.parametrize("mode", ["tf", "xhat"])
+def test_noalloc_with_fewer_slots_than_blocks(mode, ora):
+    """n = 1000, m = p = 32: one shift's window takes 16 (p + n) m = 528 KB (plus
+    512 KB for X-hat), so the 64 MiB array holds 127 (or 64) windows, fewer
+    than the 300 shifts and fewer than the thread blocks ssv_solve would use;
+    each block then solves many shifts in turn through its own window.  The
+    results must equal ssv_solve's bit for bit (same kernel, same n_b), on two
+    calls in a row, and the oracle's on a few shifts."""
+    sysr = W.random_system(1000, 32, 32, seed=4321)
+    h = ssv.reduce(dev(sysr.A), dev(sysr.B), dev(sysr.C))
+    slot = 16 * (sysr.p + sysr.n) * sysr.m + (16 * sysr.n * sysr.m if mode == "xhat" else 0)
+    assert (64 << 20) // slot < 300
+    rows = sysr.p if mode == "tf" else sysr.n
+    Ct = h.reduced()[2].cpu().numpy()
+    Ho, Ro, Co, _ = ora.reduce(sysr.A, sysr.B, sysr.C)
+    pick = [0, 77, 150, 299]
+    for sig in (W.imag_axis_logspace(-2, 2, 300), W.pseudospectrum_grid(20, 15)):
+        sd = shifts_dev(sig)
+        rc, out_na, st_na = _noalloc(h, sd, mode, rows)
+        assert rc == ssv.SSV_OK, ssv.strerror(rc)
+        ref, st_ref, _ = h.solve(sd, mode=mode)
+        torch.cuda.synchronize()
+        assert torch.equal(st_na, st_ref)
+        assert torch.equal(out_na, ref)
+        a = blocks(out_na, sysr.m)
+        Go, sto, k1 = ora.reduced_solve(Ho, Ro, Co, sig[pick], want="g", cond=True)
+        for k, j in enumerate(pick):
+            if sto[k] != 0 or k1[k] > 1e6:
+                continue
+            # G = Ct X-hat is coordinate-free, so X-hat is checked through it
+            g = -a[j] if mode == "tf" else Ct @ a[j]
+            assert relerr(g, Go[k]) < REL_TOL, j
