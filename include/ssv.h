@@ -75,6 +75,15 @@ extern "C" {
 #define SSV_XHAT 2 /* out(n x m) = Xhat = (H - sigma I)^{-1} R                */
 #define SSV_X 3    /* out(n x m) = X = Q Xhat = (A - sigma I)^{-1} B          */
 
+/* first solve of the mixed path (ssv_opts.first) */
+#define SSV_FIRST_DFLOAT 0 /* double-float sweep (about 48 bits): refinement usually
+                              only certifies it (default) */
+#define SSV_FIRST_C64 1    /* complex64 sweep (the correction sweep started from
+                              Xhat = 0): refinement has to win back every digit
+                              beyond single precision, and shifts whose condition
+                              number times 2^-24 is not well below 1 stagnate and
+                              go to the FP64 re-solve */
+
 /* panel factorisation of each window block (FP64 sweeps) */
 #define SSV_PANEL_HOUSEHOLDER 0 /* one complex reflector per row (default) */
 #define SSV_PANEL_GIVENS 1      /* Givens rotations in the greedy parallel order of
@@ -88,12 +97,13 @@ typedef struct ssv_opts {
   int max_refine;          /* SSV_MIXED: maximum refinement sweeps */
   double tol;              /* SSV_MIXED: target normwise backward error */
   int panel;               /* SSV_PANEL_HOUSEHOLDER or SSV_PANEL_GIVENS (ssv_solve, FP64) */
+  int first;               /* SSV_MIXED: SSV_FIRST_DFLOAT or SSV_FIRST_C64 */
 } ssv_opts;
 
 typedef struct ssv_handle_s* ssv_handle;
 
 /* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 8,
- * tol = 1e-13, panel = SSV_PANEL_HOUSEHOLDER.  (The mixed path certifies each
+ * tol = 1e-13, panel = SSV_PANEL_HOUSEHOLDER, first = SSV_FIRST_DFLOAT.  (The mixed path certifies each
  * shift with a residual whose own error, as a backward error, is below 5e-15
  * for m <= 16 (the tensor-core residual) and about 1e-14 for wider m (the
  * double-float residual); 1e-13 stays above both.) */
@@ -366,6 +376,18 @@ int ssv_last_cuda_error(void);
  * threads); differences of two reads count the launches of the calls between
  * them.  Measurement aid; the paper has no counterpart. */
 long long ssv_kernel_launches(void);
+
+/* Refinement counters of the mixed path (measurement aid; the paper has no
+ * counterpart), kept on the current device and accumulated over every
+ * SSV_MIXED solve on it:
+ *   *corrections: shift-sweeps of correction (shifts active in a correction
+ *     sweep, summed over the sweeps; with SSV_FIRST_C64 the first solve is not
+ *     counted);
+ *   *resolves: shifts re-solved by the FP64 sweep after refinement missed the
+ *     tolerance, stagnated or met a singular first solve.
+ * Either pointer may be NULL.  reset != 0 clears the counters after reading.
+ * Synchronises the device.  Errors: SSV_ECUDA. */
+int ssv_refine_counts(long long* corrections, long long* resolves, int reset);
 
 /* Phase tracer (measurement aid; the paper has no counterpart).  When
  * enabled, the library records CUDA events on the launching stream around its

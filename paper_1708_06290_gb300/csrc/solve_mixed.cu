@@ -734,10 +734,16 @@ __global__ void mixed_check_kernel(int n, int m, const double* __restrict__ R,
   }
 }
 
-// Active list: shifts whose flags have neither kFlagOk nor kFlagFail.
+// Refinement counters on this device (ssv_refine_counts): [0] shift-sweeps of
+// correction, [1] shifts handed to the FP64 re-solve.
+__device__ unsigned long long g_refine_counts[2];
+
+// Active list: shifts whose flags have neither kFlagOk nor kFlagFail.  With
+// `tally`, the shifts listed (those the next correction sweep solves) are
+// added to the correction counter.
 __global__ void __launch_bounds__(1024) mixed_compact_kernel(int s, const int* __restrict__ flags,
                                                              int* __restrict__ list,
-                                                             int* __restrict__ count) {
+                                                             int* __restrict__ count, int tally) {
   __shared__ int part[1024];
   const int tid = threadIdx.x;
   const int chunk = (s + 1023) / 1024;
@@ -755,7 +761,10 @@ __global__ void __launch_bounds__(1024) mixed_compact_kernel(int s, const int* _
   int pos = part[tid] - c;
   for (int j = b; j < e; ++j)
     if (!(flags[j] & (kFlagOk | kFlagFail))) list[pos++] = j;
-  if (tid == 1023) *count = part[1023];
+  if (tid == 1023) {
+    *count = part[1023];
+    if (tally) atomicAdd(&g_refine_counts[0], (unsigned long long)part[1023]);
+  }
 }
 
 // Outputs of converged shifts (G = +-Ct Xhat in FP64, or Xhat); the others are
@@ -771,6 +780,7 @@ __global__ void mixed_output_kernel(int n, int m, int p, int s, int mode,
     const bool ok = (flags[sh] & kFlagOk) != 0;
     if (threadIdx.x == 0) {
       fallback[sh] = ok ? 0 : 1;
+      if (!ok) atomicAdd(&g_refine_counts[1], 1ull);
       if (ok && status) status[sh] = SSV_SHIFT_OK;
       if (ok && resid) resid[sh] = eta[sh];
     }
@@ -877,7 +887,7 @@ constexpr int kResidBlocksPerSm = 8;
 
 template <int MAXM>
 int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, double* out,
-              long long ldo, int* status, double* resid, int max_refine, double tol,
+              long long ldo, int* status, double* resid, int max_refine, double tol, int first,
               int** fallback_out, void** scratch_out, cudaStream_t st) {
   using L = LayoutM<MAXM>;
   const int n = h->n, m = h->m, p = h->p;
@@ -899,10 +909,16 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
   mixed_init_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(s, ms.flags, ms.eta, ms.acc,
                                                                      ms.list, ms.count);
   count_launch();
-  // first solve: the double-float sweep (FP64 panels, FP32-pair bulk updates)
-  // writes Xhat of every shift; its singular shifts are flagged
+  // first solve: the double-float sweep (double-word panels, FP32-pair bulk
+  // updates) writes Xhat of every shift and flags its singular shifts.  With
+  // SSV_FIRST_C64 Xhat starts at zero instead: the residual of the round
+  // numbered -1 below is then R itself, and that round's correction sweep is
+  // the complex64 first solve.
+  const bool c64 = first == SSV_FIRST_C64;
   void* tr = trace_begin("mixed_sweep0", st);
-  {
+  if (c64) {
+    SSV_CUDA_TRY(cudaMemsetAsync(ms.X, 0, sizeof(cd) * (size_t)n * m * s, st));
+  } else {
     ssv_opts od;
     ssv_default_opts(&od);
     od.precision = SSV_DFLOAT;
@@ -921,7 +937,7 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
     trace_end(tr, st);
     if (rc != SSV_OK) return rc;
   }
-  for (int it = 0; it <= max_refine; ++it) {
+  for (int it = c64 ? -1 : 0; it <= max_refine; ++it) {
     tr = trace_begin("mixed_residual", st);
     if (ms.tch != nullptr) {
       // Ozaki-split BF16 products on the tensor cores (residual_tc.cu)
@@ -938,10 +954,11 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
         n, m, h->R, sd, ms.list, ms.count, ms.acc, ms.eta, ms.flags, h->hnorm2, it, max_refine, tol,
         ms.err);
     count_launch();
-    mixed_compact_kernel<<<1, 1024, 0, st>>>(s, ms.flags, ms.list, ms.count);
+    mixed_compact_kernel<<<1, 1024, 0, st>>>(s, ms.flags, ms.list, ms.count,
+                                             (it >= 0 && it < max_refine) ? 1 : 0);
     count_launch();
     if (it == max_refine) break;
-    tr = trace_begin("mixed_correction", st);
+    tr = trace_begin(it < 0 ? "mixed_first_c64" : "mixed_correction", st);
     k1<<<grid, kThreads, L::bytes, st>>>(n, m, nb, h->Hhi, h->R, sd, ms.list, ms.count, ms.slots,
                                         slot_bytes, ms.X, ms.E, ms.flags, h->hnorm2);
     count_launch();
@@ -956,6 +973,18 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
 }
 
 }  // namespace
+
+int refine_counts(long long c[2], bool reset) {
+  unsigned long long v[2] = {0, 0};
+  SSV_CUDA_TRY(cudaMemcpyFromSymbol(v, g_refine_counts, sizeof(v)));
+  if (reset) {
+    const unsigned long long z[2] = {0, 0};
+    SSV_CUDA_TRY(cudaMemcpyToSymbol(g_refine_counts, z, sizeof(z)));
+  }
+  c[0] = (long long)v[0];
+  c[1] = (long long)v[1];
+  return SSV_OK;
+}
 
 size_t solve_mixed_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) {
   (void)p;
@@ -977,12 +1006,12 @@ int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o,
   const int mode = o->mode == SSV_X ? SSV_XHAT : o->mode;
   const int mr = o->max_refine;
   const double tol = o->tol;
-  if (m <= 1) rc = run_mixed<1>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
-  else if (m <= 2) rc = run_mixed<2>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
-  else if (m <= 4) rc = run_mixed<4>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
-  else if (m <= 8) rc = run_mixed<8>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
-  else if (m <= 16) rc = run_mixed<16>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
-  else if (m <= 32) rc = run_mixed<32>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, &fallback, &scratch, st);
+  if (m <= 1) rc = run_mixed<1>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, o->first, &fallback, &scratch, st);
+  else if (m <= 2) rc = run_mixed<2>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, o->first, &fallback, &scratch, st);
+  else if (m <= 4) rc = run_mixed<4>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, o->first, &fallback, &scratch, st);
+  else if (m <= 8) rc = run_mixed<8>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, o->first, &fallback, &scratch, st);
+  else if (m <= 16) rc = run_mixed<16>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, o->first, &fallback, &scratch, st);
+  else if (m <= 32) rc = run_mixed<32>(h, s, shifts, nb, mode, out, ldo, status, resid, mr, tol, o->first, &fallback, &scratch, st);
   else rc = SSV_ENOTSUP;
   // shifts that did not converge: FP64 sweep (status and output overwritten);
   // their backward errors come from the FP64 solution

@@ -53,6 +53,7 @@ static int check_opts(const ssv_opts* o) {
   if (o->mode < SSV_G || o->mode > SSV_X) return SSV_EINVAL;
   if (o->nb < 0 || o->tile < 0 || o->max_refine < 0 || !(o->tol >= 0.0)) return SSV_EINVAL;
   if (o->panel != SSV_PANEL_HOUSEHOLDER && o->panel != SSV_PANEL_GIVENS) return SSV_EINVAL;
+  if (o->first != SSV_FIRST_DFLOAT && o->first != SSV_FIRST_C64) return SSV_EINVAL;
   return SSV_OK;
 }
 
@@ -71,6 +72,7 @@ void ssv_default_opts(ssv_opts* o) {
   o->max_refine = 8;
   o->tol = 1e-13;
   o->panel = SSV_PANEL_HOUSEHOLDER;
+  o->first = SSV_FIRST_DFLOAT;
 }
 
 static int make_handle(int n, int m, int p, cudaStream_t st, Handle** out) {
@@ -462,6 +464,15 @@ const char* ssv_strerror(int code) {
 }
 
 int ssv_last_cuda_error(void) { return g_last_cuda; }
+
+int ssv_refine_counts(long long* corrections, long long* resolves, int reset) {
+  long long c[2] = {0, 0};
+  const int rc = refine_counts(c, reset != 0);
+  if (rc != SSV_OK) return rc;
+  if (corrections) *corrections = c[0];
+  if (resolves) *resolves = c[1];
+  return SSV_OK;
+}
 
 long long ssv_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -135,6 +135,9 @@ int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, in
 int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,
                 long long ldo, int* status, double* resid, cudaStream_t st);
 size_t solve_mixed_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o);
+// refinement counters of the mixed path on the current device: c[0] correction
+// shift-sweeps, c[1] FP64 re-solves (synchronising read, optional reset)
+int refine_counts(long long c[2], bool reset);
 // split H into the FP32 pair (Hhi, Hlo) (reduce_fp64.cu)
 int split_h(Handle* h, cudaStream_t st);
 size_t solve_fp64_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o);

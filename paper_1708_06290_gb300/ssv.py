@@ -52,7 +52,7 @@ class SsvError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("nb", ctypes.c_int),
                 ("tile", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
-                ("panel", ctypes.c_int)]
+                ("panel", ctypes.c_int), ("first", ctypes.c_int)]
 
 
 EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_get_reduced",
@@ -61,7 +61,7 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
            "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
            "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2",
-           "ssv_backward_error")
+           "ssv_backward_error", "ssv_refine_counts")
 
 _lib = None
 
@@ -95,6 +95,7 @@ def load(build_if_missing=True):
     L.ssv_givens_schedule.argtypes = [I, I, P, I, P, I, ctypes.POINTER(I)]
     L.ssv_tf_norm2.argtypes = [P, I, P, ctypes.POINTER(Opts), P, P, P]
     L.ssv_backward_error.argtypes = [P, I, P, P, LL, I, P, P]
+    L.ssv_refine_counts.argtypes = [ctypes.POINTER(LL), ctypes.POINTER(LL), I]
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.ssv_solve_many.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
                                  ctypes.POINTER(LL), PP, P]
@@ -113,7 +114,7 @@ def load(build_if_missing=True):
                                  ctypes.POINTER(I), ctypes.POINTER(I)]
     for f in ("ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
            "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2",
-           "ssv_backward_error"):
+           "ssv_backward_error", "ssv_refine_counts"):
         getattr(L, f).restype = I
     L.ssv_apply_q.argtypes = [P, I, P, LL, P, LL, P]
     L.ssv_get_reduced.argtypes = [P, P, LL, P, LL, P, LL, P]
@@ -180,7 +181,11 @@ def _need_cuda(t, dtype, name):
 _PANELS = {"householder": 0, "givens": 1}
 
 
-def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-13, panel="householder"):
+_FIRST = {"dfloat": 0, "c64": 1}
+
+
+def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-13, panel="householder",
+         first="dfloat"):
     o = Opts()
     load().ssv_default_opts(ctypes.byref(o))
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
@@ -190,7 +195,19 @@ def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-13, pane
     o.max_refine = max_refine
     o.tol = tol
     o.panel = _PANELS[panel] if isinstance(panel, str) else int(panel)
+    o.first = _FIRST[first] if isinstance(first, str) else int(first)
     return o
+
+
+def refine_counts(reset=False):
+    """(correction shift-sweeps, FP64 re-solves) of the mixed path on the current
+    device, accumulated since the last reset (synchronises the device)."""
+    L = load()
+    c = ctypes.c_longlong()
+    r = ctypes.c_longlong()
+    _check(L.ssv_refine_counts(ctypes.byref(c), ctypes.byref(r), 1 if reset else 0),
+           "ssv_refine_counts")
+    return int(c.value), int(r.value)
 
 
 def givens_schedule(rows, m):
@@ -236,7 +253,8 @@ class Handle:
         return self.p if _MODES.get(mode, mode) in (G, TF) else self.n
 
     def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=8, tol=1e-13,
-              out=None, status=None, resid=None, want_resid=False, stream=None, panel="householder"):
+              out=None, status=None, resid=None, want_resid=False, stream=None, panel="householder",
+              first="dfloat"):
         """Solve all shifts.  Returns (out, status, resid).
 
         out is a column-major complex128 (rows, s*m) tensor, rows = p for
@@ -245,7 +263,7 @@ class Handle:
         L = load()
         _need_cuda(shifts, torch.complex128, "shifts")
         s = shifts.numel()
-        o = opts(precision, mode, nb, tile, max_refine, tol, panel)
+        o = opts(precision, mode, nb, tile, max_refine, tol, panel, first)
         rows = self.out_rows(o.mode)
         dev = shifts.device
         if out is None:

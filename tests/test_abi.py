@@ -53,6 +53,9 @@ def test_strerror_and_defaults(lib):
     o = ssv.Opts()
     lib.ssv_default_opts(ctypes.byref(o))
     assert o.precision == ssv.FP64 and o.mode == ssv.G and o.max_refine == 8 and o.tol == 1e-13
+    assert o.first == 0   # SSV_FIRST_DFLOAT
+    # the C struct and the ctypes mirror agree in size (ssv_opts is passed by pointer)
+    assert ctypes.sizeof(ssv.Opts) == 40
 
 
 def test_argument_validation_needs_no_gpu(lib):
@@ -73,6 +76,9 @@ def test_argument_validation_needs_no_gpu(lib):
     lib.ssv_default_opts(ctypes.byref(bad))
     bad.mode = 9
     b = ctypes.c_size_t()
+    assert lib.ssv_footprint(10, 2, 2, 5, ctypes.byref(bad), ctypes.byref(b)) == ssv.SSV_EINVAL
+    bad.mode = 0
+    bad.first = 7
     assert lib.ssv_footprint(10, 2, 2, 5, ctypes.byref(bad), ctypes.byref(b)) == ssv.SSV_EINVAL
     assert lib.ssv_dims(None, None, None, None) == ssv.SSV_EINVAL
     lib.ssv_destroy(None)
