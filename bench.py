@@ -4,9 +4,11 @@ One step = the whole path over one synthetic system: the FP64 controller-
 Hessenberg reduction of (A, B, C) followed by the solve of every shift,
 G(sigma_j) = C (A - sigma_j I)^{-1} B.  The workload is n = 5000, m = p = 16,
 2000 shifts on the 50 x 40 grid over [-4, 0] x [-2, 2] (A = -2I + G/sqrt(n)).
-value = shifts processed by all ranks / max-over-ranks time of K steps.
+value = shifts processed by all ranks / max-over-ranks time of K steps of the
+headline precision (default: the certified mixed path); the FP64 and
+double-float steps are timed beside it for the comparison.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64|dfloat]
     python bench.py --impl reference ...   # the CPU oracle arm
 
 Under torchrun each rank solves its own copy of the workload (weak scaling;
@@ -38,7 +40,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed", "dfloat"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "dfloat"], default="mixed",
+                    help="headline precision (value, e2e, roofline); the others are timed beside it "
+                         "(--profile-solve: the precision of the profiled solve)")
+    ap.add_argument("--side-steps", type=int, default=5,
+                    help="timed steps of the comparison precisions")
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -48,7 +54,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batching and serving measurements")
     ap.add_argument("--serving-scale", type=float, default=1.0)
-    ap.add_argument("--serving-requests", type=int, default=40)
+    ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
     ap.add_argument("--profile-reduce", type=int, default=0,
                     help="profiling case: one reduction of an n x n system (m = p = 8)")
@@ -66,7 +72,8 @@ def workload_config(sysr, sig, nb, precision):
                     "A=-2I+G/sqrt(n)" % (sysr.n, sysr.m, len(sig)),
         "n": sysr.n, "m": sysr.m, "p": sysr.p, "shifts": int(len(sig)),
         "output": "G(sigma)=C X, complex128, p x (s*m)",
-        "step": "FP64 reduction + solve of all shifts",
+        "step": "FP64 reduction + %s solve of all shifts (certified: backward error <= 1e-12)"
+                % precision,
         "precision": precision, "nb": nb or (128 if sysr.n >= 1024 else 64),
         "l2": "inputs larger than L2 (A and H are 200 MB each; every step re-reads A)",
     }
@@ -132,24 +139,77 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # the oracle (CPU) arm
 # ----------------------------------------------------------------------------
-def time_oracle(sysr, sig, sample):
-    """Oracle reduction (full) + tier-2 solve of `sample` evenly spread shifts."""
+def oracle_sample(sig, k):
+    """k grid shifts: three quarters inside the spectral disc |sigma + 2| < 1 (where the
+    condition numbers are large), the rest outside, evenly spread over each set."""
+    inside = np.where(np.abs(sig + 2.0) < 1.0)[0]
+    outside = np.where(np.abs(sig + 2.0) >= 1.0)[0]
+    ki = (3 * k) // 4
+    return np.concatenate([inside[np.linspace(0, len(inside) - 1, ki).astype(int)],
+                           outside[np.linspace(0, len(outside) - 1, k - ki).astype(int)]])
+
+
+def cpu_baseline_leg(ssv, sysr, sig, dev, args):
+    """The oracle as it stands on the host cores: its reduction of the full system
+    plus tier-2 reduced GEPP on a sample of grid shifts (one call, parallel over the
+    shifts), extrapolated to all shifts.  On the same sample, the per-shift relative
+    error of the GPU's G (mixed and FP64 paths) against the oracle's G, with the
+    oracle's condition estimate kappa_1 beside it."""
+    import torch
+
     import oracle
 
     oracle._load()
+    cores = os.cpu_count()
+    pick = oracle_sample(sig, max(4, args.cpu_shifts))
     t0 = time.perf_counter()
-    H, R, Ct, _ = oracle.reduce(sysr.A, sysr.B, sysr.C)
+    Ho, Ro, Co, _ = oracle.reduce(sysr.A, sysr.B, sysr.C)
     t_red = time.perf_counter() - t0
-    idx = np.unique(np.linspace(0, len(sig) - 1, sample).astype(int))
     t0 = time.perf_counter()
-    oracle.reduced_solve(H, R, Ct, sig[idx], want="g")
-    t_solve = time.perf_counter() - t0
-    per_shift = t_solve / len(idx)
+    Go, sto, _ = oracle.reduced_solve(Ho, Ro, Co, sig[pick], want="g")
+    t_call = time.perf_counter() - t0
+    per_shift = t_call / len(pick)
     value = len(sig) / (t_red + per_shift * len(sig))
-    return value, t_red, per_shift, len(idx), (H, R, Ct, idx)
+    _, _, k1 = oracle.reduced_solve(Ho, Ro, Co, sig[pick], want="g", cond=True)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().to(dev)  # noqa
+    h = ssv.reduce(to(sysr.A), to(sysr.B), to(sysr.C))
+    sd = torch.from_numpy(sig[pick].astype(np.complex128)).to(dev)
+    errs = {}
+    for prec in ("mixed", "fp64"):
+        out, st, resid = h.solve(sd, mode="g", precision=prec, want_resid=True)
+        G = out.cpu().numpy()
+        m = sysr.m
+        errs[prec] = [float(np.linalg.norm(G[:, j * m:(j + 1) * m] - Go[j]) / np.linalg.norm(Go[j]))
+                      for j in range(len(pick))]
+        errs[prec + "_eta"] = [float(x) for x in resid.cpu().numpy()]
+    h.close()
+    gate = k1 <= 1e6
+    r3 = lambda xs: [float("%.3g" % x) for x in xs]  # noqa: E731
+    return {
+        "value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": "oracle reduction of the full n=5000 system (%.1f s) + tier-2 reduced GEPP on "
+                  "%d grid shifts (%d inside the spectral disc) in one call, %.3f s/shift, "
+                  "extrapolated to %d shifts" % (t_red, len(pick), (3 * len(pick)) // 4,
+                                                 per_shift, len(sig)),
+        "per_shift_error": {
+            "reference": "oracle: own reduction + tier-2 reduced GEPP, G = Ct Xhat; "
+                         "rel_err = ||G - G_oracle||_F / ||G_oracle||_F",
+            "sigma_re": r3(sig[pick].real), "sigma_im": r3(sig[pick].imag), "kappa1": r3(k1),
+            "rel_err_mixed": r3(errs["mixed"]), "rel_err_fp64": r3(errs["fp64"]),
+            "backward_error_mixed": r3(errs["mixed_eta"]),
+            "max_rel_err_mixed_kappa_le_1e6": float(max(np.array(errs["mixed"])[gate], default=0.0)),
+            "max_rel_err_fp64_kappa_le_1e6": float(max(np.array(errs["fp64"])[gate], default=0.0)),
+            "oracle_status_nonzero": int((sto != 0).sum()),
+        },
+    }
 
 
 def run_reference(args):
+    """The oracle arm: the plain CPU oracle on the host cores.  One step = one
+    tier-2 call on os.cpu_count() grid shifts (the call is parallel over shifts,
+    one per core) plus that many shifts' share of the oracle reduction, which is
+    timed once before the steps; value = shifts per second of that step, i.e.
+    2000 / (t_reduce + 2000 t_call / shifts_per_call)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -157,32 +217,35 @@ def run_reference(args):
     import oracle
 
     oracle._load()
+    cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     H, R, Ct, _ = oracle.reduce(sysr.A, sysr.B, sysr.C)
     t_red = time.perf_counter() - t0
-    per_step = 4
-    rng_idx = np.unique(np.linspace(0, len(sig) - 1, per_step * (args.steps + args.warmup)).astype(int))
+    per_step = cores
+    idx_all = np.unique(np.linspace(0, len(sig) - 1, per_step * (args.steps + args.warmup)).astype(int))
     times = []
     for k in range(args.warmup + args.steps):
-        idx = rng_idx[(k * per_step) % len(rng_idx):][:per_step]
+        idx = idx_all[(k * per_step) % len(idx_all):][:per_step]
+        if len(idx) < per_step:
+            idx = idx_all[:per_step]
         t0 = time.perf_counter()
         oracle.reduced_solve(H, R, Ct, sig[idx], want="g")
         if k >= args.warmup:
-            times.append((time.perf_counter() - t0) / len(idx))
-    per_shift = float(np.mean(times))
-    step_s = t_red + per_shift * len(sig)
-    value = len(sig) / step_s
-    cores = os.cpu_count()
+            times.append(time.perf_counter() - t0)
+    t_call = float(np.mean(times))
+    step_s = t_call + t_red * per_step / len(sig)
+    value = per_step / step_s
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(sysr, sig, 0, "fp64"),
+        "config": workload_config(sysr, sig, 0, args.precision),
         "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
-                         "sample": "oracle reduction of the full n=5000 system (%.1f s, once) + "
-                                   "tier-2 reduced GEPP on %d shifts per step; per-shift time x 2000"
-                                   % (t_red, per_step)},
+                         "sample": "per step: oracle tier-2 reduced GEPP on %d grid shifts in one "
+                                   "call (parallel over shifts, %.3f s) + those shifts' share of "
+                                   "the oracle reduction of the full n=5000 system (%.1f s, timed "
+                                   "once)" % (per_step, t_call, t_red)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -203,53 +266,46 @@ def combine_ranks(world, shifts_per_rank, steps, local_ms, reduce_max):
 # ----------------------------------------------------------------------------
 def serving_measurement(ssv, dev, args):
     """The serving workload: 8 preloaded reduced systems (n = 1000 .. 10000,
-    m = (1, 4, 16)[i % 3], p = m), requests of 1..256 imaginary-axis shifts.
-    Saturated throughput first (all requests at t = 0), then Poisson arrivals at
-    0.5 / 0.8 / 0.95 of it; p50 / p99 latency per load."""
+    m = (1, 4, 16)[i % 3], p = m), requests of 1..256 imaginary-axis shifts,
+    solved with the certified mixed path.  Saturated throughput first (every
+    request at t = 0), then Poisson arrivals at 0.5 / 0.8 / 0.95 of it, each
+    with --serving-requests requests; p50 / p99 latency per load."""
     import torch
 
     from paper_1708_06290_gb300.serve import Server, make_requests
 
     systems = W.workload_serving_systems(scale=args.serving_scale)
     to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().to(dev)  # noqa
-    t0 = time.perf_counter()
     handles = [ssv.reduce(to(sy.A), to(sy.B), to(sy.C)) for sy in systems]
     torch.cuda.synchronize()
-    t_reduce = time.perf_counter() - t0
     budget = int(args.serving_budget_gb * (1 << 30))
     nreq = args.serving_requests
-
-    def one(precision):
-        warm = make_requests(W.serving_requests(8, 100.0, seed=900))
-        Server(handles, slots=4, mem_budget=budget, precision=precision).run(warm, realtime=False)
-        sat = Server(handles, slots=4, mem_budget=budget, precision=precision).run(
-            make_requests(W.serving_requests(nreq, 1.0, seed=901)), realtime=False)
-        req_rate = sat["requests"] / sat["wall_s"]
-        loads = {}
-        for f in (0.5, 0.8, 0.95):
-            st = Server(handles, slots=4, mem_budget=budget, precision=precision).run(
-                make_requests(W.serving_requests(nreq, f * req_rate, seed=902 + int(100 * f))),
-                realtime=True)
-            loads["%.2f" % f] = {k: st[k] for k in ("p50_ms", "p99_ms", "shift_solves_per_s",
-                                                     "requests", "batches", "max_inflight_batches")}
-        return {"saturated": {"requests_per_s": req_rate,
-                              "shift_solves_per_s": sat["shift_solves_per_s"],
-                              "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"]},
-                "poisson": loads}
-
-    res = one("fp64")
-    res_df = one("dfloat")
+    prec = "mixed"
+    warm = make_requests(W.serving_requests(16, 100.0, seed=900))
+    Server(handles, slots=4, mem_budget=budget, precision=prec).run(warm, realtime=False)
+    sat = Server(handles, slots=4, mem_budget=budget, precision=prec).run(
+        make_requests(W.serving_requests(nreq, 1.0, seed=901)), realtime=False)
+    req_rate = sat["requests"] / sat["wall_s"]
+    loads = {}
+    for f in (0.5, 0.8, 0.95):
+        st = Server(handles, slots=4, mem_budget=budget, precision=prec).run(
+            make_requests(W.serving_requests(nreq, f * req_rate, seed=902 + int(100 * f))),
+            realtime=True)
+        loads["%.2f" % f] = {"p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
+                             "shift_solves_per_s": round(st["shift_solves_per_s"], 1),
+                             "requests": st["requests"], "overlap": st["max_inflight_batches"]}
     for h in handles:
         h.close()
-    return {"systems_n": [sy.n for sy in systems], "systems_m": [sy.m for sy in systems],
-            "reduce_s": t_reduce, "budget_bytes": budget, "precision": "fp64", **res,
-            "dfloat": res_df}
+    return {"precision": prec, "requests_per_load": nreq,
+            "saturated_shift_solves_per_s": round(sat["shift_solves_per_s"], 1),
+            "saturated_requests_per_s": round(req_rate, 2), "poisson": loads}
 
 
 def batching_measurement(ssv, dev, args):
     """The batching workload: 64 systems, n ~ U{200..3000}, m in {1,2,4,8},
-    16..512 shifts each, one ssv_solve_many launch per precision (FP64 and the
-    double-float updates); reductions untimed."""
+    16..512 shifts each; n_b autotuned per system, then one batch plan per
+    precision (FP64, double-float) captured in a CUDA graph and replayed
+    (median of 3 replays); reductions and tuning untimed."""
     import torch
 
     work = W.workload_batching()
@@ -257,22 +313,31 @@ def batching_measurement(ssv, dev, args):
     handles = [ssv.reduce(to(sy.A), to(sy.B), to(sy.C)) for sy, _ in work]
     shifts = [torch.from_numpy(sig.astype(np.complex128)).to(dev) for _, sig in work]
     total = sum(int(x.numel()) for x in shifts)
-    res = {"systems": len(work), "shifts": total, "launches_per_batch": 1}
+    res = {"systems": len(work), "shifts": total, "graph_replay": True}
+    stream = torch.cuda.Stream()
     for prec in ("fp64", "dfloat"):
-        ssv.solve_many(handles, shifts, mode="g", precision=prec)
+        tuned = [ssv.autotune(h, x, mode="g", precision=prec)[0] for h, x in zip(handles, shifts)]
+        plan = ssv.BatchPlan(handles, shifts, mode="g", precision=prec)
+        plan.run(stream)
         torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            plan.run(stream)
         ts = []
         for _ in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ssv.solve_many(handles, shifts, mode="g", precision=prec)
-            e1.record()
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                g.replay()
+            e1.record(stream)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         ms = float(np.median(ts))
-        if prec == "fp64":
-            res.update({"ms": ms, "shift_solves_per_s": total / (ms * 1e-3)})
-        res[prec] = {"ms": ms, "shift_solves_per_s": total / (ms * 1e-3)}
+        bad = int(sum(int((st != 0).sum()) for st in plan.statuses))
+        res[prec] = {"ms": round(ms, 3), "shift_solves_per_s": round(total / (ms * 1e-3), 1),
+                     "nb_tuned": sorted(set(tuned)), "nonzero_status": bad}
+        plan.close()
+        del g
     for h in handles:
         h.close()
     return res
@@ -432,7 +497,7 @@ def main():
         h.solve(sig_d, mode="g", precision=precision, nb=args.nb, out=out, status=status)
         return h
 
-    def timed(precision):
+    def timed(precision, steps, warmup):
         """W warm-up steps, then K steps bracketed by barrier + sync; phase spans
         from the library tracer (CUDA events on this stream)."""
         h = step(precision)
@@ -441,9 +506,10 @@ def main():
         torch.cuda.synchronize()
         gate = {"max_backward_error": float(resid.max()), "nonzero_status": int((st_chk != 0).sum())}
         h.close()
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step(precision).close()
         torch.cuda.synchronize()
+        ssv.refine_counts(reset=True)
         ssv.trace(True)
         launches0 = ssv.kernel_launches()
         barrier()
@@ -451,7 +517,7 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         handles = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             handles.append(step(precision))
             if len(handles) > 1:
                 handles.pop(0).close()
@@ -463,20 +529,28 @@ def main():
         launches = ssv.kernel_launches() - launches0
         phases = ssv.trace_read()
         ssv.trace(False)
-        value, total_ms = combine_ranks(world, s, args.steps, e0.elapsed_time(e1), max_over_ranks)
-        phase_ms = {k: v[0] / args.steps for k, v in phases.items()}
-        return {"value": value, "ms_per_step": total_ms / args.steps,
-                "phase_ms_per_step": phase_ms, "gpu_launches": int(launches), **gate}
+        corr, resol = ssv.refine_counts(reset=True)
+        value, total_ms = combine_ranks(world, s, steps, e0.elapsed_time(e1), max_over_ranks)
+        phase_ms = {k: round(v[0] / steps, 3) for k, v in phases.items()}
+        return {"value": value, "ms_per_step": total_ms / steps, "steps": steps,
+                "phase_ms_per_step": phase_ms, "gpu_launches": int(launches),
+                "corrections_per_step": corr / steps, "fp64_resolves_per_step": resol / steps,
+                **gate}
 
     fp64_peak = ssv.peak_probe("fp64")
     fp32_peak = ssv.peak_probe("fp32")
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
-    res = {"fp64": timed("fp64"), "mixed": timed("mixed"), "dfloat": timed("dfloat")}
+    headp = args.precision
+    res = {headp: timed(headp, args.steps, args.warmup)}
+    for prec in ("fp64", "mixed", "dfloat"):
+        if prec != headp:
+            res[prec] = timed(prec, max(1, min(args.side_steps, args.steps)), min(args.warmup, 3))
     clocks = clk.stop()
+    head = res[headp]
 
-    # ---- end to end through the public API with host buffers (FP64 path)
+    # ---- end to end through the public API with host buffers (headline precision)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     A_h = pin(sysr.A.T.copy())
     B_h = pin(sysr.B.T.copy())
@@ -497,7 +571,7 @@ def main():
         C_e.copy_(C_h, non_blocking=True)
         sig_e.copy_(sig_h, non_blocking=True)
         hh = ssv.reduce(A_e.t(), B_e.t(), C_e.t())
-        o, st2, _ = hh.solve(sig_e, mode="g", precision="fp64", nb=args.nb)
+        o, st2, _ = hh.solve(sig_e, mode="g", precision=headp, nb=args.nb)
         G_h.copy_(o.t(), non_blocking=True)
         st_h.copy_(st2, non_blocking=True)
         torch.cuda.synchronize()
@@ -515,67 +589,79 @@ def main():
         e2e_s = max_over_ranks(time.perf_counter() - t0)
         e2e_value = world * s * args.e2e_steps / e2e_s
 
-    # ---- roofline of the dominant kernel of the reported (FP64) path
-    head = res["fp64"]
-    solve_ms = head["phase_ms_per_step"].get("solve_fp64", float("nan"))
-    flops_floor = s * (2.0 * n * n * m + 4.0 * n * m * p)   # n_b-independent algorithmic floor
-    achieved = flops_floor / (solve_ms * 1e-3) / 1e12
-    roofline = {
+    # ---- rooflines: the first-solve sweep of the mixed step (its largest phase) and
+    # the FP64 sweep of the FP64 step
+    floor_macs = n * n * m + 2.0 * n * m * p      # n_b-independent multiply-adds per shift
+    fp64_ms = res["fp64"]["phase_ms_per_step"].get("solve_fp64", float("nan"))
+    fp64_ach = 2.0 * floor_macs * s / (fp64_ms * 1e-3) / 1e12
+    roof_fp64 = {
         "kernel": "solve_fp64_kernel", "bound": "alu", "unit": "TFLOP/s",
-        "achieved": achieved, "peak": fp64_peak, "frac": achieved / fp64_peak,
+        "achieved": fp64_ach, "peak": fp64_peak, "frac": fp64_ach / fp64_peak,
         "peak_source": "FP64 DFMA probe measured in this run (nominal GB300 FP64 1.25 TFLOP/s)",
-        "flops_per_launch": flops_floor, "launch_ms": solve_ms,
+        "launch_ms": fp64_ms,
         "flops_definition": "2 n^2 m + 4 n m p per shift (trailing update Z1 P1 + Ct rows)",
-        # context: the kernel executes ~1.2e9 FP64 flops per shift at n_b = 128 (Z2 P2 and the
-        # Householder panel on top of the floor); ncu measured its FP64 pipe 86 % busy
-        # (profiles/solve_fp64_kernel_n5000_m16_152shifts.md)
-        "executed_flops_per_shift": 2.0 * n * n * m + 4.0 * n * n * m * m / 128 + 16.0 * n * (m + 1) * (128 + m),
-        "fp64_pipe_busy_ncu": 0.861,
-        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one solve_fp64_kernel launch
-        # on 152 shifts of this workload (3.002227 + 3.462814 GB, profiles/
-        # solve_fp64_kernel_n5000_m16_152shifts.md), scaled by shifts to this launch: each
-        # shift streams its own Z2 state, so traffic grows in proportion to the shifts.
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 152 shifts of
+        # this workload (profiles/solve_fp64_kernel_n5000_m16_152shifts.md), scaled by shifts:
+        # each shift streams its own Z2 state
         "traffic": (3.002227e9 + 3.462814e9) * s / 152.0 if args.nb in (0, 128) else None,
-        "traffic_source": "ncu capture of 152 shifts at n_b=128, scaled to %d shifts" % s,
     }
+    sweep0_ms = res["mixed"]["phase_ms_per_step"].get("mixed_sweep0", float("nan"))
+    # each double-float multiply-add (df_mac) issues 12 FP32-pipe instructions; the FFMA
+    # probe's TFLOP/s / 2 is the pipe's instruction rate
+    instr = 12.0 * floor_macs * s
+    ach_ti = instr / (sweep0_ms * 1e-3) / 1e12
+    peak_ti = fp32_peak / 2.0
+    roof_mixed = {
+        "kernel": "solve_fp64_kernel<16, double-float> (first solve of the mixed path)",
+        "bound": "alu", "unit": "T FP32-instr/s", "achieved": ach_ti, "peak": peak_ti,
+        "frac": ach_ti / peak_ti,
+        "peak_source": "FFMA probe measured in this run / 2 (instructions/s; nominal 128 lanes x "
+                       "152 SMs x 2.07 GHz = 40.3 T/s)",
+        "launch_ms": sweep0_ms,
+        "definition": "n_b-independent floor n^2 m + 2 n m p real multiply-adds per shift, each "
+                      "12 FP32-pipe instructions in double-float",
+        "traffic": None,
+    }
+    roofline = roof_mixed if headp == "mixed" else roof_fp64
+    mx = res["mixed"]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(sysr, sig, args.nb, "fp64"),
-        "phase_ms": head["phase_ms_per_step"],
-        "max_backward_error": head["max_backward_error"], "nonzero_status": head["nonzero_status"],
-        "mixed_vs_fp64": {
-            **{prec: {**{k: res[prec][k] for k in ("value", "ms_per_step", "phase_ms_per_step",
-                                                   "max_backward_error", "nonzero_status")},
-                      "speedup_vs_fp64": res[prec]["value"] / res["fp64"]["value"]}
-               for prec in ("fp64", "mixed", "dfloat")},
-            "precisions": {
-                "fp64": "every step in double / complex128",
-                "mixed": "first solve in double-float (FP32 pairs), FP64-accurate residual on the "
-                         "tensor cores (Ozaki-split BF16 digit slices, tcgen05) certifies every "
-                         "shift at backward error <= 1e-13, complex64 correction sweeps, FP64 "
-                         "re-solve of shifts that miss",
-                "dfloat": "panels and bulk updates in double-float (FP32 pairs), no refinement"},
-            "fp32_ffma_peak_tflops": fp32_peak,
-            "tensor_residual_roofline": tensor_residual_roofline(n, m, s, res["mixed"]),
-        },
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32-pair+bf16-tc+f64", "fp64": "f64", "dfloat": "f32-pair"}[headp],
+        "data": "synthetic",
+        "config": workload_config(sysr, sig, args.nb, headp),
+        "mixed_value": mx["value"], "fp64_value": res["fp64"]["value"],
+        "dfloat_value": res["dfloat"]["value"],
+        "mixed_speedup_vs_fp64": mx["value"] / res["fp64"]["value"],
+        "mixed_max_backward_error": mx["max_backward_error"],
+        "mixed_nonzero_status": mx["nonzero_status"],
+        "mixed_corrections_per_step": mx["corrections_per_step"],
+        "mixed_fp64_resolves_per_step": mx["fp64_resolves_per_step"],
+        "fp64_max_backward_error": res["fp64"]["max_backward_error"],
+        "roofline": roofline,
+        "roofline_fp64_sweep": roof_fp64,
+        "phase_ms": {k: res[k]["phase_ms_per_step"] for k in ("mixed", "fp64", "dfloat")},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": head["gpu_launches"],
-        "roofline": roofline,
+        "fp32_ffma_peak_tflops": fp32_peak,
+        "tensor_residual_roofline": tensor_residual_roofline(n, m, s, mx),
     }
     if not args.no_extras and world == 1:
         line["batching"] = batching_measurement(ssv, dev, args)
         line["serving"] = serving_measurement(ssv, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, t_red, per_shift, cnt, _ = time_oracle(sysr, sig, args.cpu_shifts)
-        line["cpu_baseline"] = {
-            "value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle reduction of the full n=5000 system (%.1f s) + tier-2 reduced GEPP "
-                      "on %d evenly spread shifts (%.3f s/shift), extrapolated to %d shifts"
-                      % (t_red, cnt, per_shift, s)}
+        line["cpu_baseline"] = cpu_baseline_leg(ssv, sysr, sig, dev, args)
+    # the comparison once more, last on the line, so a truncated tail still has it
+    line["summary"] = ("%s step %.1f shift-solves/s; mixed %.1f = %.2fx FP64 %.1f, dfloat %.1f; "
+                       "max backward error mixed %.1e, fp64 %.1e; corrections %.0f and FP64 "
+                       "re-solves %.0f per mixed step"
+                       % (headp, head["value"], mx["value"], line["mixed_speedup_vs_fp64"],
+                          res["fp64"]["value"], res["dfloat"]["value"], mx["max_backward_error"],
+                          res["fp64"]["max_backward_error"], mx["corrections_per_step"],
+                          mx["fp64_resolves_per_step"]))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -489,16 +489,16 @@ def solve_many(handles, shifts, mode="g", precision="fp64", nb=0, stream=None):
 
 
 class BatchPlan:
-    """A fixed FP64 multi-system solve: run() is one kernel launch with constant
+    """A fixed FP64 (or double-float) multi-system solve: run() is one kernel launch with constant
     arguments (capturable in a CUDA graph).  Rewrite the shift tensors in place
     between runs; outputs land in .outs / .statuses."""
 
-    def __init__(self, handles, shifts, mode="g", nb=0):
+    def __init__(self, handles, shifts, mode="g", nb=0, precision="fp64"):
         L = load()
         self.handles = list(handles)
         self.shifts = list(shifts)
         self.outs, self.statuses = _alloc_outputs(self.handles, self.shifts, mode)
-        o = opts("fp64", mode, nb)
+        o = opts(precision, mode, nb)
         n, hs, ss, sp, op, ld, st = _many_args(self.handles, self.shifts, self.outs, self.statuses)
         b = ctypes.c_void_p()
         _check(L.ssv_batch_create(n, hs, ss, sp, ctypes.byref(o), op, ld, st, ctypes.byref(b)),
