@@ -70,6 +70,17 @@ extern "C" {
                         between about 1e-18 and 1e18).  ssv_solve, the
                         many-systems launch and batch plans. */
 
+#define SSV_SPLIT 3 /* the sweep as phases over all shifts per block step, with
+                       the trailing update Z1 P1 (the product with the shared
+                       columns of H, most of the work) on the tensor cores as
+                       error-free BF16 digit products (H and the block transforms
+                       split into seven 7-bit digits, exact FP32 accumulation per
+                       level, about 48 significant bits) and the panels and Z2 P2
+                       in double-float as in SSV_DFLOAT; no refinement.
+                       m <= 16, n > m, n_b = 128, Householder panel; ssv_solve and
+                       ssv_tf_norm2 (ssv_solve_many solves the systems one after
+                       another).  Singularity threshold as SSV_DFLOAT. */
+
 #define SSV_G 0    /* out(p x m) = C X = Ct Xhat                             */
 #define SSV_TF 1   /* out(p x m) = C (sigma I - A)^{-1} B = -Ct Xhat (Sec. 2) */
 #define SSV_XHAT 2 /* out(n x m) = Xhat = (H - sigma I)^{-1} R                */
@@ -78,6 +89,9 @@ extern "C" {
 /* first solve of the mixed path (ssv_opts.first) */
 #define SSV_FIRST_DFLOAT 0 /* double-float sweep (about 48 bits): refinement usually
                               only certifies it (default) */
+#define SSV_FIRST_TENSOR 2 /* the SSV_SPLIT sweep (tensor-core trailing update, about
+                              48 bits); where SSV_SPLIT does not apply (m > 16 or
+                              n <= m) the double-float sweep is used instead */
 #define SSV_FIRST_C64 1    /* complex64 sweep (the correction sweep started from
                               Xhat = 0): refinement has to win back every digit
                               beyond single precision, and shifts whose condition
@@ -90,14 +104,14 @@ extern "C" {
                                    Algorithm 9 (Sec. 3.2); n_b <= 32, m <= 32 */
 
 typedef struct ssv_opts {
-  int precision;           /* SSV_FP64, SSV_MIXED or SSV_DFLOAT */
+  int precision;           /* SSV_FP64, SSV_MIXED, SSV_DFLOAT or SSV_SPLIT */
   int mode;                /* SSV_G, SSV_TF, SSV_XHAT, SSV_X */
   int nb;                  /* rows per elimination block n_b; 0 = default */
   int tile;                /* shifts per thread block; 0 = default */
   int max_refine;          /* SSV_MIXED: maximum refinement sweeps */
   double tol;              /* SSV_MIXED: target normwise backward error */
   int panel;               /* SSV_PANEL_HOUSEHOLDER or SSV_PANEL_GIVENS (ssv_solve, FP64) */
-  int first;               /* SSV_MIXED: SSV_FIRST_DFLOAT or SSV_FIRST_C64 */
+  int first;               /* SSV_MIXED: SSV_FIRST_DFLOAT, SSV_FIRST_C64 or SSV_FIRST_TENSOR */
 } ssv_opts;
 
 typedef struct ssv_handle_s* ssv_handle;

@@ -915,9 +915,25 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
   // numbered -1 below is then R itself, and that round's correction sweep is
   // the complex64 first solve.
   const bool c64 = first == SSV_FIRST_C64;
+  const bool tens = first == SSV_FIRST_TENSOR && ms.tch != nullptr && solve_tc_supported(h, SSV_XHAT);
+  bool h_split = false;
+  if (tens) {
+    // the H digit tiles serve the tensor-core sweep and then the residual
+    void* trs = trace_begin("mixed_split_h", st);
+    const int rc = resid_tc_split_h(h, ms.tch, st);
+    trace_end(trs, st);
+    if (rc != SSV_OK) return rc;
+    h_split = true;
+  }
   void* tr = trace_begin("mixed_sweep0", st);
   if (c64) {
     SSV_CUDA_TRY(cudaMemsetAsync(ms.X, 0, sizeof(cd) * (size_t)n * m * s, st));
+  } else if (tens) {
+    const int rc0 = solve_tc(h, s, shifts, SSV_XHAT, reinterpret_cast<double*>(ms.X), n, ms.st0,
+                             ms.tch, st);
+    if (rc0 != SSV_OK) return rc0;
+    mixed_status_kernel<<<std::min(1024, (s + 255) / 256), 256, 0, st>>>(s, ms.st0, ms.flags);
+    count_launch();
   } else {
     ssv_opts od;
     ssv_default_opts(&od);
@@ -931,7 +947,7 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
   trace_end(tr, st);
   const int rgrid = num_sms() * kResidBlocksPerSm;
   SSV_CUDA_TRY(cudaMemsetAsync(ms.err, 0, sizeof(int), st));
-  if (ms.tch != nullptr) {
+  if (ms.tch != nullptr && !h_split) {
     tr = trace_begin("mixed_split_h", st);
     const int rc = resid_tc_split_h(h, ms.tch, st);
     trace_end(tr, st);
@@ -987,11 +1003,13 @@ int refine_counts(long long c[2], bool reset) {
 }
 
 size_t solve_mixed_scratch_bytes(int n, int m, int p, int s, const ssv_opts* o) {
-  (void)p;
-  (void)o;
   const size_t slot_bytes = (size_t)n * m * 3 * sizeof(cf);
   const int grid = std::max(1, std::min(s, num_sms() * kSweepBlocksPerSm));
-  return mixed_layout(n, m, s, grid, slot_bytes, nullptr, nullptr) + 256;
+  size_t b = mixed_layout(n, m, s, grid, slot_bytes, nullptr, nullptr) + 256;
+  // the tensor-core first solve allocates its own window state while it runs
+  if (o->first == SSV_FIRST_TENSOR && m <= kTcMaxM && n > m)
+    b += solve_tc_scratch_bytes(n, m, p, s, SSV_XHAT);
+  return b;
 }
 
 int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o, double* out,

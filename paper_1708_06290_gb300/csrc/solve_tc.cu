@@ -1,0 +1,884 @@
+// Shift-batched sweep with the trailing update on the tensor cores.
+//
+// The sweep of Sec. 3.1 / Algorithm 8 for every shift, run as the paper runs
+// it on a GPU: one phase per block step k for all shifts at once, so that the
+// update of the rows above the block ("Step 2, revisited": one GEMM with the
+// shared operand Z1 = [Ct; H](1:r, fresh columns) and every shift's block
+// transform, Z2 <- Z1 P1 + Z2 P2 - sigma E P1) multiplies a tile of H that is
+// staged once for a group of shifts.  Per block step:
+//
+//   1. panel (one thread block per shift): the n_b x (n_b + m) window block is
+//      triangularised bottom-up by one complex Householder reflector per row
+//      over the m + 1 candidate columns (double-word reflector scalars,
+//      double-float application, as in the double-float sweep), giving the
+//      coefficients P1 (n_b x m) and P2 (m x m).  The panel also updates the p
+//      rows of Ct (small), writes P1 as BF16 digit tiles, and keeps the P1
+//      rows and P2 that the X-hat back pass needs;
+//   2. update (persistent, one thread block per SM): work items of 128 rows
+//      of H x one group of shifts (N = 64 real columns: each shift's m complex
+//      columns as 2m real ones, padded to a power of two).  Z1 P1 is formed
+//      exactly as in the tensor-core residual (error-free splitting after
+//      Ozaki, Ogita, Oishi and Rump): H's rows and P1's real columns are
+//      written as seven 7-bit digits relative to a power-of-two scale, each
+//      digit exact in BF16, and the 28 digit products H_k P_l with k + l <= 6
+//      run as tcgen05.mma (BF16 x BF16 -> FP32, M = 128, N = 64, K = 16) into
+//      seven TMEM accumulators, one per level k + l, where every partial sum
+//      is an integer below 7 * 128 * 127^2 < 2^24 and therefore exact.  The
+//      digit tiles reach shared memory by 1-D TMA bulk copies on an mbarrier,
+//      two stages in flight.  The epilogue reads the levels back (tcgen05.ld),
+//      adds them scaled by 2^{-7 t} into double-float sums, scales by the row
+//      and column exponents, and adds Z2 P2 and the shifted-diagonal
+//      correction in double-float on the FP32 pipe;
+//   3. after the last block: the final m x m block, G = Ct Xhat or X-hat by the
+//      backward pass over the stored block transforms.
+//
+// Accuracy: digits beyond the seventh and the products of level > 6 are
+// dropped, below 2^-48 of the row scale times the column scale (the
+// double-float class of the SSV_DFLOAT sweep).  The first block holds
+// (n - m) mod n_b rows (n_b when that is 0), so that every later block starts
+// at a column that is a multiple of n_b and the H digit tiles (32 columns
+// deep) line up with the fresh columns.
+#include <algorithm>
+
+#include "dfloat.cuh"
+#include "ssv_internal.cuh"
+#include "tc_common.cuh"
+
+namespace ssv {
+
+namespace {
+
+using namespace tcg;
+
+constexpr int kPT = 256;             // threads of the setup, panel and final kernels
+constexpr int kNBT = 128;            // n_b of the tensor-core sweep (K of the update)
+constexpr int kMaxM = kTcMaxM;       // m <= 16
+constexpr int kSlots = kMaxM + 2;    // m live + two alternating fresh slots
+constexpr int kCoefRows = kNBT + kMaxM;
+constexpr int kUM = 128;             // H rows per update item = TMEM lanes
+constexpr int kUN = 64;              // real columns per update item (shift group)
+constexpr int kKS = 32;              // K per shared-memory stage
+constexpr int kKG = kKS / 8;         // core matrices along K in a tile
+constexpr int kSD = 7;               // digits used per operand
+constexpr int kLev = 7;              // levels k + l = 0 .. 6
+constexpr int kStages = kNBT / kKS;  // stages per block step
+constexpr int kAT = kUM * kKS;       // BF16 elements of one H digit tile
+constexpr int kBT = kUN * kKS;       // BF16 elements of one P1 digit tile
+constexpr uint32_t kStageBytes = (uint32_t)kSD * (kAT + kBT) * 2;
+constexpr int kIss = 4;              // threads issuing products (lane 0 of warps 0..3)
+constexpr uint32_t kIdescU = idesc_bf16(kUM, kUN);
+constexpr int kTmemCols = 512;       // 7 levels x 64 columns, rounded up
+// polls of one mbarrier wait before the update gives up (a stage's copies and
+// products complete within microseconds)
+constexpr long long kUpdWait = 1LL << 22;
+static_assert(kLev * kUN <= kTmemCols, "TMEM columns of the levels");
+constexpr size_t kUpdSmem = 2 * (size_t)kStageBytes + (size_t)2 * kMaxM * kMaxM * 16 * 4 + 1024;
+static_assert(kUpdSmem <= 227 * 1024, "shared memory of the update");
+
+// element offset in a K-major core-matrix tile (8 rows x 8 K per 128 bytes;
+// byte strides 128 along K, kKG * 128 along rows): the layout of the residual's
+// H digit tiles
+__host__ __device__ __forceinline__ int tile_off(int row, int k) {
+  return (((row >> 3) * kKG + (k >> 3)) * 8 + (row & 7)) * 8 + (k & 7);
+}
+
+// issuer owning level t (products per level t + 1): {6}, {5, 0}, {4, 1}, {3, 2}
+__host__ __device__ constexpr int level_owner(int t) {
+  return t == 6 ? 0 : (t == 5 || t == 0) ? 1 : (t == 4 || t == 1) ? 2 : 3;
+}
+
+// column stride of one shift in a group: 2m real columns rounded up to a power of two
+__host__ __device__ inline int shift_cols(int m) {
+  int c = 2;
+  while (c < 2 * m) c <<= 1;
+  return c;
+}
+
+struct TcsArgs {
+  int n, m, p, s, cs, S, ngroups, mode;
+  const double* H;       // n x n
+  const float* Hhi;      // double-float split of H
+  const float* Hlo;
+  const double* Ct;      // p x n (ld ldct)
+  int ldct;
+  const double* R;       // n x m
+  const cd* shifts;
+  const double* hnorm;   // ||H||_F^2, trace(H)
+  float4* Z2;            // per shift: (p + n) x m double-float window columns, ld p + n
+  cd* ZT;                // per shift: n x m rows P1 of every step (X-hat mode), or null
+  size_t z2_stride;      // float4 per shift slot
+  uint16_t* Pd;          // P1 digit tiles: [group][digit][stage][kBT]
+  int* pexp;             // per shift: 2m column exponents (stride 2 kMaxM)
+  float4* pc;            // per shift: P2 (m x m) then sigma rows P1(0:min(m,nbe), :) (m x m)
+  cd* out;
+  long long ldo;
+  int* flags;            // per shift: 1 = singular to working precision
+  int* status;
+  const uint4* Hs;       // H digit tiles (residual layout) and row exponents
+  const int* hexp;
+  int RB, KT;            // row blocks / K blocks of the H digit tiles
+  int* err;              // an update wait gave up
+};
+
+__device__ __forceinline__ double shifted_norm2(const double* hnorm, int n, cd sg) {
+  return fmax(hnorm[0] - 2.0 * sg.x * hnorm[1] + (double)n * (sg.x * sg.x + sg.y * sg.y), 0.0);
+}
+
+// ---- setup: Z2 = last m columns of [Ct; H] - sigma on the diagonal ---------
+__global__ void __launch_bounds__(kPT) tcs_setup_kernel(TcsArgs a) {
+  const int sh = blockIdx.x;
+  const int n = a.n, m = a.m, p = a.p, ldz = p + n;
+  const cd sigma = a.shifts[sh];
+  float4* Z2 = a.Z2 + (size_t)sh * a.z2_stride;
+  for (long long idx = threadIdx.x; idx < (long long)ldz * m; idx += kPT) {
+    const int i = (int)(idx % ldz), q = (int)(idx / ldz);
+    const int j = n - m + q;
+    const double v = i < p ? a.Ct[i + (size_t)j * a.ldct] : a.H[(i - p) + (size_t)j * n];
+    cd z = mkcd(v, 0.0);
+    if (i - p == j) z = csub(z, sigma);
+    Z2[idx] = df_split(z);
+  }
+  if (threadIdx.x == 0) a.flags[sh] = 0;
+}
+
+// ---- panel of block step `step` (1-based), rows k - nbe .. k - 1 ------------
+struct PanelSmem {
+  float4 cand[kSlots * kNBT];
+  float4 coef[kCoefRows * kSlots];
+  float4 vf[kMaxM + 4];
+  int fexp[2 * kMaxM];
+  int sing;
+};
+
+__global__ void __launch_bounds__(kPT, 2) tcs_panel_kernel(TcsArgs a, int k, int nbe, int step) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PanelSmem& sm = *reinterpret_cast<PanelSmem*>(smem_raw);
+  constexpr int S = kSlots;
+  const int sh = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int n = a.n, m = a.m, p = a.p, ldz = p + n;
+  const int r = p + k - nbe;       // rows of [Ct; M] above the block
+  const int j0 = k - m - nbe;      // first fresh column
+  const cd sigma = a.shifts[sh];
+  float4* Z2f = a.Z2 + (size_t)sh * a.z2_stride;
+  const double sing_tol = (double)n * 7.105427357601002e-15 * sqrt(shifted_norm2(a.hnorm, n, sigma));
+  const float sing_tol_f = (float)sing_tol;
+  const float* __restrict__ Hhi = a.Hhi;
+  const float* __restrict__ Hlo = a.Hlo;
+  auto split4 = [](cd z) -> float4 { return df_split(z); };
+  // entry (global row gr, fresh column jc) of H - sigma I as FP32 pairs
+  auto fresh4 = [&](int gr, int jc) -> float4 {
+    const size_t hidx = (size_t)gr + (size_t)jc * n;
+    if (gr == jc) return split4(csub(mkcd((double)Hhi[hidx] + (double)Hlo[hidx], 0.0), sigma));
+    return make_float4(Hhi[hidx], Hlo[hidx], 0.f, 0.f);
+  };
+  float4* cand4 = sm.cand;
+  float4* coef4 = sm.coef;
+  float4* vf = sm.vf;
+  if (tid == 0) sm.sing = 0;
+  for (int idx = tid; idx < m * nbe; idx += kPT) {
+    const int t = idx % nbe, q = idx / nbe;
+    cand4[q * kNBT + t] = Z2f[(r + t) + (size_t)q * ldz];
+  }
+  for (int idx = tid; idx < kCoefRows * S; idx += kPT) {
+    const int c = idx / S, slot = idx % S;
+    const bool one = (slot < m && c == kNBT + slot) || (slot == m && c == nbe - 1);
+    coef4[idx] = make_float4(one ? 1.f : 0.f, 0.f, 0.f, 0.f);
+  }
+  {
+    const int c = nbe - 1, jc = j0 + c;
+    for (int t = tid; t <= c; t += kPT) cand4[m * kNBT + t] = fresh4(k - nbe + t, jc);
+  }
+  __syncthreads();
+  for (int c = nbe - 1; c >= 0; --c) {
+    const int fs = m + ((nbe - 1 - c) & 1);   // slot holding the fresh column of row c
+    const int fn = (fs == m) ? m + 1 : m;     // slot for the next fresh column
+    // the next fresh column is read now, its latency hidden behind this row
+    float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c > 0 && tid < c) pre = fresh4(k - nbe + tid, j0 + c - 1);
+    if (tid < 32) {
+      // reflector scalars in double-word arithmetic:
+      //   v = conj(x) + e^{i arg conj(x_f)} ||x|| e_f,  tau = 1 / (||x||^2 + |x_f| ||x||)
+      dw rest2{0.f, 0.f};
+      for (int q = tid; q < m; q += 32) {
+        const float4 x = cand4[q * kNBT + c];
+        df_mac(rest2.hi, rest2.lo, x.x, x.y, x.x, x.y);
+        df_mac(rest2.hi, rest2.lo, x.z, x.w, x.z, x.w);
+        vf[q] = make_float4(x.x, x.y, -x.z, -x.w);
+      }
+      rest2 = dw_fast(rest2.hi, rest2.lo);
+      for (int o = 16; o > 0; o >>= 1)
+        rest2 = dw_add(rest2, dw{__shfl_xor_sync(0xffffffffu, rest2.hi, o),
+                                 __shfl_xor_sync(0xffffffffu, rest2.lo, o)});
+      if (tid == 0) {
+        const float4 xf = cand4[fs * kNBT + c];
+        const dw xr{xf.x, xf.y}, xi{xf.z, xf.w};
+        const dw af2 = dw_add(dw_mul(xr, xr), dw_mul(xi, xi));
+        const dw af = dw_sqrt(af2);
+        const dw nrm2 = dw_add(rest2, af2);
+        const dw nrm = dw_sqrt(nrm2);
+        float4 vfs;
+        if (af.hi > 0.f) {  // conj(x_f) (1 + ||x|| / |x_f|)
+          const dw g = dw_add(dw{1.f, 0.f}, dw_div(nrm, af));
+          const dw vr = dw_mul(xr, g), vi = dw_mul(xi, g);
+          vfs = make_float4(vr.hi, vr.lo, -vi.hi, -vi.lo);
+        } else {
+          vfs = make_float4(nrm.hi, nrm.lo, 0.f, 0.f);
+        }
+        vf[fs] = vfs;
+        const dw tau = rest2.hi > 0.f ? dw_div(dw{1.f, 0.f}, dw_add(nrm2, dw_mul(af, nrm)))
+                                      : dw{0.f, 0.f};
+        vf[kMaxM + 2] = make_float4(tau.hi, tau.lo, 0.f, 0.f);
+        if (nrm.hi <= sing_tol_f) sm.sing = 1;
+      }
+    }
+    __syncthreads();
+    const float4 tauf = vf[kMaxM + 2];
+    if (tauf.x != 0.0f) {
+      const int nrow = c;
+      const int ncoef = (nbe - c) + m;
+      for (int e = tid; e < nrow + ncoef; e += kPT) {
+        float4* base;
+        int stride;
+        if (e < nrow) {
+          base = cand4 + e;
+          stride = kNBT;
+        } else {
+          const int ee = e - nrow;
+          const int crow = ee < nbe - c ? c + ee : kNBT + (ee - (nbe - c));
+          base = coef4 + crow * S;
+          stride = 1;
+        }
+        // w = sum_slot base(slot) v(slot)
+        float wrh = 0.f, wrl = 0.f, wih = 0.f, wil = 0.f;
+        for (int q = 0; q <= m; ++q) {
+          const int slot = q < m ? q : fs;
+          const float4 x = base[slot * stride], v = vf[slot];
+          df_mac(wrh, wrl, x.x, x.y, v.x, v.y);
+          df_mac(wrh, wrl, -x.z, -x.w, v.z, v.w);
+          df_mac(wih, wil, x.x, x.y, v.z, v.w);
+          df_mac(wih, wil, x.z, x.w, v.x, v.y);
+        }
+        float trh = 0.f, trl = 0.f, tih = 0.f, til = 0.f;
+        df_mac(trh, trl, tauf.x, tauf.y, wrh, wrl);
+        df_mac(tih, til, tauf.x, tauf.y, wih, wil);
+        // base(slot) -= t conj(v(slot))
+        for (int q = 0; q <= m; ++q) {
+          const int slot = q < m ? q : fs;
+          float4 x = base[slot * stride];
+          const float4 v = vf[slot];
+          float xrh = x.x, xrl = x.y, xih = x.z, xil = x.w;
+          df_mac(xrh, xrl, -trh, -trl, v.x, v.y);
+          df_mac(xrh, xrl, -tih, -til, v.z, v.w);
+          df_mac(xih, xil, -tih, -til, v.x, v.y);
+          df_mac(xih, xil, trh, trl, v.z, v.w);
+          const float sr = xrh + xrl, si = xih + xil;
+          x = make_float4(sr, xrl - (sr - xrh), si, xil - (si - xih));
+          base[slot * stride] = x;
+        }
+      }
+    }
+    if (c > 0) {
+      const int cn = c - 1;
+      if (tid <= cn) cand4[fn * kNBT + tid] = pre;
+      for (int crow = tid; crow < kCoefRows; crow += kPT)
+        coef4[crow * S + fn] = make_float4(crow == cn ? 1.f : 0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+  }
+  // coef rows c < nbe hold P1(c, :), rows kNBT + qq hold P2(qq, :) (slots 0..m-1)
+
+  // ---- P1 as BF16 digit tiles: column exponents first (one warp per real column)
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int cr = warp; cr < 2 * m; cr += kPT / 32) {
+    const int q = cr >> 1;
+    double mx = 0.0;
+    bool bad = false;
+    for (int c = lane; c < nbe; c += 32) {
+      const float4 w = coef4[c * S + q];
+      const double v = fabs((cr & 1) ? (double)w.z + (double)w.w : (double)w.x + (double)w.y);
+      if (!(v <= 1.7976931348623157e308)) bad = true;
+      else mx = fmax(mx, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      bad = __shfl_xor_sync(0xffffffffu, (int)bad, o) || bad;
+    }
+    if (lane == 0) {
+      const int E = bad ? kBadExp : scale_exp(mx);
+      sm.fexp[cr] = E;
+      a.pexp[(size_t)sh * 2 * kMaxM + cr] = E;
+    }
+  }
+  __syncthreads();
+  {
+    // item = (real column cr, 8 consecutive K rows): seven uint4 stores
+    const int g = sh / a.S, slot_row = (sh % a.S) * a.cs;
+    uint16_t* Pg = a.Pd + (size_t)g * kSD * kStages * kBT;
+    for (int it = tid; it < 2 * m * (kNBT / 8); it += kPT) {
+      const int cr = it / (kNBT / 8), c8 = (it % (kNBT / 8)) * 8;
+      const int q = cr >> 1, E = sm.fexp[cr];
+      unsigned short dg[8][kDigits];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int c = c8 + e;
+        double v = 0.0;
+        if (c < nbe) {
+          const float4 w = coef4[c * S + q];
+          v = (cr & 1) ? (double)w.z + (double)w.w : (double)w.x + (double)w.y;
+        }
+        digits8(v, E, dg[e]);
+      }
+      const int J = c8 / kKS;
+      const int off = tile_off(slot_row + cr, c8 % kKS);
+#pragma unroll
+      for (int l = 0; l < kSD; ++l) {
+        uint4 u;
+        u.x = dg[0][l] | ((unsigned)dg[1][l] << 16);
+        u.y = dg[2][l] | ((unsigned)dg[3][l] << 16);
+        u.z = dg[4][l] | ((unsigned)dg[5][l] << 16);
+        u.w = dg[6][l] | ((unsigned)dg[7][l] << 16);
+        *reinterpret_cast<uint4*>(Pg + ((size_t)l * kStages + J) * kBT + off) = u;
+      }
+    }
+  }
+  // ---- P2 and the sigma rows for the update's epilogue
+  {
+    float4* pc = a.pc + (size_t)sh * 2 * kMaxM * kMaxM;
+    const int nsig = min(m, nbe);
+    for (int e = tid; e < 2 * m * m; e += kPT) {
+      const int row = e / m, q = e % m;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < m) v = coef4[(kNBT + row) * S + q];
+      else if (row - m < nsig) v = coef4[(row - m) * S + q];
+      pc[e] = v;
+    }
+  }
+  // ---- X-hat mode: P1 rows into ZT, P2 parked in this shift's output rows
+  //      n - step m .. n - (step - 1) m - 1 (read back before the back pass
+  //      writes them, since every later block is at least m rows high)
+  if (a.mode == SSV_XHAT) {
+    cd* ZT = a.ZT + (size_t)sh * (size_t)n * m;
+    for (int idx = tid; idx < nbe * m; idx += kPT) {
+      const int c = idx % nbe, q = idx / nbe;
+      ZT[(j0 + c) + (size_t)q * n] = df_join(coef4[c * S + q]);
+    }
+    cd* tout = a.out + (size_t)sh * m * a.ldo;
+    for (int idx = tid; idx < m * m; idx += kPT) {
+      const int qq = idx % m, q = idx / m;
+      tout[(n - step * m + qq) + (size_t)q * a.ldo] = df_join(coef4[(kNBT + qq) * S + q]);
+    }
+  }
+  // ---- the p rows of Ct: Z2(i, :) = Ct(i, fresh) P1 + Z2(i, :) P2, double-float,
+  //      in chunks of whole rows (each entry reads its row's old values)
+  const int rows_per_chunk = max(1, (2 * kPT) / m);
+  for (int i0 = 0; i0 < p; i0 += rows_per_chunk) {
+  const int ic = min(rows_per_chunk, p - i0);
+  float4 nv[2];
+  int nitem = 0;
+  for (int e = tid; e < ic * m && nitem < 2; e += kPT, ++nitem) {
+    const int i = i0 + e / m, q = e % m;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int c = 0; c < nbe; ++c) {
+      const double z = a.Ct[i + (size_t)(j0 + c) * a.ldct];
+      const float zh = (float)z, zl = (float)(z - (double)zh);
+      const float4 w = coef4[c * S + q];
+      df_mac(rh, rl, zh, zl, w.x, w.y);
+      df_mac(ih, il, zh, zl, w.z, w.w);
+    }
+    for (int qq = 0; qq < m; ++qq) {
+      const float4 zz = Z2f[i + (size_t)qq * ldz];
+      const float4 w = coef4[(kNBT + qq) * S + q];
+      df_mac(rh, rl, zz.x, zz.y, w.x, w.y);
+      df_mac(rh, rl, -zz.z, -zz.w, w.z, w.w);
+      df_mac(ih, il, zz.x, zz.y, w.z, w.w);
+      df_mac(ih, il, zz.z, zz.w, w.x, w.y);
+    }
+    const float sr = rh + rl, si = ih + il;
+    nv[nitem] = make_float4(sr, rl - (sr - rh), si, il - (si - ih));
+  }
+  __syncthreads();  // every old entry of these rows is read before any is written
+  nitem = 0;
+  for (int e = tid; e < ic * m && nitem < 2; e += kPT, ++nitem) {
+    const int i = i0 + e / m, q = e % m;
+    Z2f[i + (size_t)q * ldz] = nv[nitem];
+  }
+  __syncthreads();
+  }
+  if (tid == 0 && sm.sing) a.flags[sh] = 1;
+}
+
+// ---- update of the H rows above the block: Z2 <- Z1 P1 + Z2 P2 - sigma E P1 --
+constexpr int kUT = 2 * kUM;  // update threads: two per H row of the tile (one per 32 columns)
+
+__global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, int nbe) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int n = a.n, m = a.m, p = a.p, ldz = p + n;
+  const int hrows = k - nbe;              // H rows above the block
+  const int j0 = k - m - nbe;             // first fresh column (a multiple of 32)
+  const int nsig = min(m, nbe);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int S = a.S, cs = a.cs, G = a.ngroups;
+  // an earlier launch of this solve gave up a wait: its results are void, skip
+  if (*a.err != 0) return;
+  const int RT = (hrows + kUM - 1) / kUM;
+  const long long items = (long long)RT * G;
+  const int nst = (nbe + kKS - 1) / kKS;
+  const int JH0 = j0 / kKS;
+  float4* pcs = reinterpret_cast<float4*>(smem + 2 * (size_t)kStageBytes);  // S x 2 m m
+  int* fexp = reinterpret_cast<int*>(pcs + (size_t)2 * kMaxM * kMaxM * 4);  // kUN
+  cd* sig = reinterpret_cast<cd*>(fexp + kUN);                              // <= kUN shifts
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sig + kUN);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIss + 2);
+  const uint32_t mb = smem_addr(mbar);        // kIss MMA barriers, then two load barriers
+  const uint32_t lmb0 = mb + 8u * kIss;
+  const uint32_t sBase = smem_addr(smem);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tslot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < kIss + 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  uint32_t mphase = 0;
+  uint32_t lphase[2] = {0u, 0u};
+  bool pend[2] = {false, false};  // a stage copy into buffer b not yet seen complete
+  bool failed = false;
+
+  // stage st of item (I, g) into buffer b: seven H digit tiles, seven P1 digit tiles
+  auto stage_in = [&](int I, int g, int st, int b) {
+    const uint32_t dst = sBase + (uint32_t)b * kStageBytes;
+    const uint32_t lmb = lmb0 + 8u * (uint32_t)b;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lmb), "r"(kStageBytes)
+                 : "memory");
+    for (int l = 0; l < kSD; ++l)
+      bulk_copy(dst + (uint32_t)(l * kAT * 2),
+                a.Hs + ((size_t)(l * a.RB + I) * a.KT + (JH0 + st)) * (kAT / 8), (uint32_t)(kAT * 2), lmb);
+    const uint16_t* Pg = a.Pd + (size_t)g * kSD * kStages * kBT;
+    for (int l = 0; l < kSD; ++l)
+      bulk_copy(dst + (uint32_t)(kSD * kAT * 2 + l * kBT * 2), Pg + ((size_t)l * kStages + st) * kBT,
+                (uint32_t)(kBT * 2), lmb);
+  };
+
+  long long item = blockIdx.x;
+  if (item < items) {
+    pend[0] = true;
+    if (tid == 0) stage_in((int)(item / G), (int)(item % G), 0, 0);
+  }
+  int buf = 0;  // buffer holding the next stage to multiply
+  for (; item < items && !failed; item += gridDim.x) {
+    const int I = (int)(item / G), g = (int)(item % G);
+    // the group's P2 / sigma rows, column exponents and shifts
+    for (int e = tid; e < S * 2 * m * m; e += kUT) {
+      const int l = e / (2 * m * m), o = e % (2 * m * m);
+      const int sh = g * S + l;
+      pcs[e] = sh < a.s ? a.pc[(size_t)sh * 2 * kMaxM * kMaxM + o] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int e = tid; e < S * 2 * m; e += kUT) {
+      const int l = e / (2 * m), c = e % (2 * m);
+      const int sh = g * S + l;
+      fexp[l * cs + c] = sh < a.s ? a.pexp[(size_t)sh * 2 * kMaxM + c] : 0;
+    }
+    for (int l = tid; l < S; l += kUT) sig[l] = (g * S + l < a.s) ? a.shifts[g * S + l] : mkcd(0.0, 0.0);
+    for (int st = 0; st < nst; ++st) {
+      const bool lok = mbar_wait(lmb0 + 8u * (uint32_t)buf, lphase[buf], kUpdWait);
+      if (__syncthreads_or(!lok)) {
+        failed = true;
+        break;
+      }
+      lphase[buf] ^= 1u;
+      pend[buf] = false;
+      const int iss = tid >> 5;
+      if ((tid & 31) == 0 && iss < kIss) {
+        fence_after();
+        const uint32_t aBase = sBase + (uint32_t)buf * kStageBytes;
+        const uint32_t bBase = aBase + (uint32_t)(kSD * kAT * 2);
+        constexpr uint32_t kSbo = (uint32_t)kKG * 128u;
+#pragma unroll 1
+        for (int lv = 0; lv < kLev; ++lv) {
+          if (level_owner(lv) != iss) continue;
+#pragma unroll 1
+          for (int kd = 0; kd <= lv; ++kd) {
+            const int ld = lv - kd;
+#pragma unroll
+            for (int ks = 0; ks < kKS / 16; ++ks) {
+              const uint64_t ad = mat_desc(aBase + (uint32_t)(kd * kAT * 2 + ks * 256), 128u, kSbo);
+              const uint64_t bd = mat_desc(bBase + (uint32_t)(ld * kBT * 2 + ks * 256), 128u, kSbo);
+              const bool first = st == 0 && kd == 0 && ks == 0;
+              mma_bf16(tmem + (uint32_t)(lv * kUN), ad, bd, kIdescU, first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(mb + 8u * (uint32_t)iss);
+      }
+      // the next stage (of this item, or the first of the next item) streams
+      // into the other buffer, whose products finished in the previous round
+      if (st + 1 < nst) {
+        pend[buf ^ 1] = true;
+        if (tid == 0) stage_in(I, g, st + 1, buf ^ 1);
+      } else if (item + gridDim.x < items) {
+        const long long nx = item + gridDim.x;
+        pend[buf ^ 1] = true;
+        if (tid == 0) stage_in((int)(nx / G), (int)(nx % G), 0, buf ^ 1);
+      }
+      bool ok = true;
+      for (int q = 0; q < kIss; ++q) ok = mbar_wait(mb + 8u * q, mphase, kUpdWait) && ok;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      mphase ^= 1u;
+      buf ^= 1;
+    }
+    if (failed) break;
+    // ---- epilogue: thread (row, chunk) = (tid mod 128, tid / 128): one H row and
+    //      32 of the 64 columns; warps w and w + 4 read TMEM lanes 32 (w mod 4) ..
+    fence_after();
+    const int row = tid & (kUM - 1), ch = tid >> 7;
+    const int ih = I * kUM + row;
+    const bool live = ih < hrows;
+    const int Ei = live ? a.hexp[ih] : 0;
+    const int cdr = ih - j0;  // shifted-diagonal correction row of fresh column cdr
+    {
+      float ah[32], al[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) { ah[c] = 0.f; al[c] = 0.f; }
+      float sc = 0.0078125f * 0.0078125f;  // 2^{-7 (t + 2)}, t = 0
+#pragma unroll 1
+      for (int lv = 0; lv < kLev; ++lv) {
+        uint32_t rr[32];
+        tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(lv * kUN + ch * 32), rr);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const float pv = __uint_as_float(rr[c]) * sc;
+          const float s2 = ah[c] + pv;
+          const float bp = s2 - ah[c];
+          al[c] += (ah[c] - (s2 - bp)) + (pv - bp);
+          ah[c] = s2;
+        }
+        sc *= 0.0078125f;
+      }
+      // the sums go to the stage buffer whose products are done (the other one
+      // is receiving the next item's first stage), one column per 128 float2 of
+      // this chunk's half, so that the per-shift loop below indexes them at run
+      // time; each thread reads back only its own entries
+      float2* esc = reinterpret_cast<float2*>(smem + (size_t)(buf ^ 1) * kStageBytes) + ch * 32 * kUM;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) esc[c * kUM + row] = make_float2(ah[c], al[c]);
+      if (live) {
+      // shifts whose columns lie in this chunk of 32
+      for (int l0 = 0; l0 < 32 / cs && l0 < S; ++l0) {
+        const int l = ch * (32 / cs) + l0;
+        if (l >= S) break;
+        const int sh = g * S + l;
+        if (sh >= a.s) break;
+        float4* Z2f = a.Z2 + (size_t)sh * a.z2_stride;
+        const float4* P2 = pcs + (size_t)l * 2 * m * m;
+        const float4* PS = P2 + m * m;
+        const int b0 = l0 * cs;
+        float4 z2o[kMaxM];
+#pragma unroll
+        for (int qq = 0; qq < kMaxM; ++qq)
+          if (qq < m) z2o[qq] = Z2f[(p + ih) + (size_t)qq * ldz];
+        const cd sg = sig[l];
+        const float4 sgf = df_split(sg);
+#pragma unroll 1
+        for (int q = 0; q < m; ++q) {
+          float rh, rl, xh, xl;
+          {
+            const int er = fexp[l * cs + 2 * q], ei = fexp[l * cs + 2 * q + 1];
+            if (Ei == kBadExp || er == kBadExp || ei == kBadExp) {
+              rh = xh = __int_as_float(0x7fc00000);
+              rl = xl = 0.f;
+            } else {
+              const float2 vr = esc[(b0 + 2 * q) * kUM + row], vi = esc[(b0 + 2 * q + 1) * kUM + row];
+              rh = ldexpf(vr.x, Ei + er);
+              rl = ldexpf(vr.y, Ei + er);
+              xh = ldexpf(vi.x, Ei + ei);
+              xl = ldexpf(vi.y, Ei + ei);
+            }
+          }
+#pragma unroll
+          for (int qq = 0; qq < kMaxM; ++qq) {
+            if (qq < m) {
+              const float4 zz = z2o[qq];
+              const float4 w = P2[qq * m + q];
+              df_mac(rh, rl, zz.x, zz.y, w.x, w.y);
+              df_mac(rh, rl, -zz.z, -zz.w, w.z, w.w);
+              df_mac(xh, xl, zz.x, zz.y, w.z, w.w);
+              df_mac(xh, xl, zz.z, zz.w, w.x, w.y);
+            }
+          }
+          if (cdr >= 0 && cdr < nsig) {
+            // - sigma P1(cdr, q)
+            const float4 w = PS[cdr * m + q];
+            df_mac(rh, rl, -sgf.x, -sgf.y, w.x, w.y);
+            df_mac(rh, rl, sgf.z, sgf.w, w.z, w.w);
+            df_mac(xh, xl, -sgf.x, -sgf.y, w.z, w.w);
+            df_mac(xh, xl, -sgf.z, -sgf.w, w.x, w.y);
+          }
+          const float sr = rh + rl, si = xh + xl;
+          Z2f[(p + ih) + (size_t)q * ldz] = make_float4(sr, rl - (sr - rh), si, xl - (si - xh));
+        }
+      }
+      }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  if (failed) {
+    // a completion never arrived: record it, give the products and copies in
+    // flight one more bounded wait, then release TMEM
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      for (int q = 0; q < kIss; ++q) mbar_wait(mb + 8u * q, mphase, kUpdWait);
+      for (int b = 0; b < 2; ++b)
+        if (pend[b]) mbar_wait(lmb0 + 8u * (uint32_t)b, lphase[b], kUpdWait);
+    }
+    __syncthreads();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// ---- final m x m block, G or the X-hat back pass ----------------------------
+__global__ void __launch_bounds__(kPT) tcs_final_kernel(TcsArgs a, int nsteps, int nbe_first) {
+  __shared__ cd Wm[kMaxM * 2 * kMaxM];
+  __shared__ cd lmul[kMaxM];
+  __shared__ cd Yb[kMaxM * kMaxM];
+  __shared__ cd zs[kMaxM * kMaxM], p2s[kMaxM * kMaxM], zn[kMaxM * kMaxM];
+  __shared__ int s_piv, s_sing;
+  const int sh = blockIdx.x, tid = threadIdx.x;
+  const int n = a.n, m = a.m, p = a.p, ldz = p + n;
+  const cd sigma = a.shifts[sh];
+  const double sing_tol = (double)n * 7.105427357601002e-15 * sqrt(shifted_norm2(a.hnorm, n, sigma));
+  const float4* Z2f = a.Z2 + (size_t)sh * a.z2_stride;
+  const bool failed = *a.err != 0;
+  if (tid == 0) s_sing = a.flags[sh];
+  for (int idx = tid; idx < m * 2 * m; idx += kPT) {
+    const int i = idx % m, j = idx / m;
+    cd v;
+    if (j < m) v = df_join(Z2f[(p + i) + (size_t)j * ldz]);
+    else v = mkcd(i <= j - m ? a.R[i + (size_t)(j - m) * n] : 0.0, 0.0);
+    Wm[i + j * kMaxM] = v;
+  }
+  __syncthreads();
+  // Gauss-Jordan with partial pivoting on [Wm | R(0:m, 0:m)]
+  for (int kk = 0; kk < m; ++kk) {
+    if (tid < 32) {
+      double best = -1.0;
+      int brow = kk;
+      for (int i = kk + tid; i < m; i += 32) {
+        const double v = cabs1(Wm[i + kk * kMaxM]);
+        if (v > best) { best = v; brow = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+        if (ob > best || (ob == best && orow < brow)) { best = ob; brow = orow; }
+      }
+      if (tid == 0) {
+        s_piv = brow;
+        const cd pv = Wm[brow + kk * kMaxM];
+        if (best == 0.0 || sqrt(pv.x * pv.x + pv.y * pv.y) <= sing_tol) s_sing = 1;
+      }
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != kk) {
+      for (int j = tid; j < 2 * m; j += kPT) {
+        const cd t = Wm[kk + j * kMaxM];
+        Wm[kk + j * kMaxM] = Wm[pr + j * kMaxM];
+        Wm[pr + j * kMaxM] = t;
+      }
+    }
+    __syncthreads();
+    const cd d = Wm[kk + kk * kMaxM];
+    const bool dz = (d.x == 0.0 && d.y == 0.0);
+    if (tid < m) lmul[tid] = (tid == kk || dz) ? mkcd(0.0, 0.0) : cdiv(Wm[tid + kk * kMaxM], d);
+    __syncthreads();
+    for (int idx = tid; idx < m * 2 * m; idx += kPT) {
+      const int i = idx % m, j = idx / m;
+      if (i != kk && j > kk) Wm[i + j * kMaxM] = cfms(lmul[i], Wm[kk + j * kMaxM], Wm[i + j * kMaxM]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < m * m; idx += kPT) {
+    const int i = idx % m, q = idx / m;
+    const cd d = Wm[i + i * kMaxM];
+    Yb[i + q * kMaxM] = (d.x == 0.0 && d.y == 0.0) ? mkcd(0.0, 0.0) : cdiv(Wm[i + (m + q) * kMaxM], d);
+  }
+  __syncthreads();
+  const bool sing = s_sing != 0;
+  const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+  const bool bad = sing || failed;
+  cd* tout = a.out + (size_t)sh * m * a.ldo;
+  if (a.mode == SSV_G || a.mode == SSV_TF) {
+    const double sgn = a.mode == SSV_TF ? -1.0 : 1.0;
+    for (int idx = tid; idx < p * m; idx += kPT) {
+      const int i = idx % p, q = idx / p;
+      cd acc = mkcd(0.0, 0.0);
+      for (int t = 0; t < m; ++t) acc = cfma(df_join(Z2f[i + (size_t)t * ldz]), Yb[t + q * kMaxM], acc);
+      if (bad) acc = mkcd(nanv, nanv);
+      tout[i + (size_t)q * a.ldo] = mkcd(sgn * acc.x, sgn * acc.y);
+    }
+  } else {
+    // backward pass: z = Y; per step b = B .. 1: X-hat rows of b = P1_b z,
+    // then z = P2_b z; the initial live rows n - m .. n - 1 take the last z.
+    // Step b covers the fresh columns j0_b = (B - b) n_b .. + nbe_b - 1.
+    const cd* ZT = a.ZT + (size_t)sh * (size_t)n * m;
+    for (int e = tid; e < m * m; e += kPT) zs[(e % m) + (e / m) * kMaxM] = Yb[(e % m) + (e / m) * kMaxM];
+    __syncthreads();
+    for (int b = nsteps; b >= 1; --b) {
+      const int nbe_b = b == 1 ? nbe_first : kNBT;
+      const int j0b = (nsteps - b) * kNBT;
+      for (int e = tid; e < m * m; e += kPT)
+        p2s[(e % m) + (e / m) * kMaxM] = tout[(n - b * m + e % m) + (size_t)(e / m) * a.ldo];
+      __syncthreads();
+      for (int idx = tid; idx < nbe_b * m; idx += kPT) {
+        const int i = j0b + idx % nbe_b, q = idx / nbe_b;
+        cd acc = mkcd(0.0, 0.0);
+        for (int t = 0; t < m; ++t) acc = cfma(ZT[i + (size_t)t * n], zs[t + q * kMaxM], acc);
+        tout[i + (size_t)q * a.ldo] = bad ? mkcd(nanv, nanv) : acc;
+      }
+      for (int e = tid; e < m * m; e += kPT) {
+        const int rr = e % m, q = e / m;
+        cd acc = mkcd(0.0, 0.0);
+        for (int t = 0; t < m; ++t) acc = cfma(p2s[rr + t * kMaxM], zs[t + q * kMaxM], acc);
+        zn[rr + q * kMaxM] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += kPT) zs[(e % m) + (e / m) * kMaxM] = zn[(e % m) + (e / m) * kMaxM];
+      __syncthreads();
+    }
+    for (int e = tid; e < m * m; e += kPT) {
+      const int rr = e % m, q = e / m;
+      tout[(n - m + rr) + (size_t)q * a.ldo] = bad ? mkcd(nanv, nanv) : zs[rr + q * kMaxM];
+    }
+  }
+  if (a.status != nullptr && tid == 0) {
+    bool fin = true;
+    for (int e = 0; e < m * m; ++e) {
+      const cd y = Yb[(e % m) + (e / m) * kMaxM];
+      fin = fin && isfinite(y.x) && isfinite(y.y);
+    }
+    a.status[sh] = sing ? SSV_SHIFT_SINGULAR : ((fin && !failed) ? SSV_SHIFT_OK : SSV_SHIFT_NONFINITE);
+  }
+}
+
+}  // namespace
+
+bool solve_tc_supported(const Handle* h, int mode) {
+  return h->m <= kMaxM && h->n > h->m && (mode == SSV_G || mode == SSV_TF || mode == SSV_XHAT);
+}
+
+size_t solve_tc_scratch_bytes(int n, int m, int p, int s, int mode) {
+  const int cs = shift_cols(m), S = kUN / cs;
+  const size_t G = (size_t)(s + S - 1) / S;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  size_t b = al(sizeof(float4) * (size_t)s * (size_t)(p + n) * m);
+  if (mode == SSV_XHAT) b += al(sizeof(cd) * (size_t)s * (size_t)n * m);
+  b += al(G * kSD * kStages * kBT * 2) + al(sizeof(int) * (size_t)s * 2 * kMaxM) +
+       al(sizeof(float4) * (size_t)s * 2 * kMaxM * kMaxM) + al(sizeof(int) * ((size_t)s + 1));
+  return b + 256;
+}
+
+int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out, long long ldo,
+             int* status, const void* hdig, cudaStream_t st) {
+  const int n = h->n, m = h->m, p = h->p;
+  if (!solve_tc_supported(h, mode)) return SSV_ENOTSUP;
+  if (resid_tc_ktile() != kKS) return SSV_ENOTSUP;
+  if (s == 0) return SSV_OK;
+  const int cs = shift_cols(m), S = kUN / cs;
+  const int G = (s + S - 1) / S;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t bZ = al(sizeof(float4) * (size_t)s * (size_t)(p + n) * m);
+  const size_t bT = mode == SSV_XHAT ? al(sizeof(cd) * (size_t)s * (size_t)n * m) : 0;
+  const size_t bP = al((size_t)G * kSD * kStages * kBT * 2);
+  const size_t bE = al(sizeof(int) * (size_t)s * 2 * kMaxM);
+  const size_t bC = al(sizeof(float4) * (size_t)s * 2 * kMaxM * kMaxM);
+  const size_t bF = al(sizeof(int) * ((size_t)s + 1));
+  const size_t bH = hdig == nullptr ? al(resid_tc_hbytes(n)) : 0;
+  unsigned char* buf = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&buf, bZ + bT + bP + bE + bC + bF + bH, st));
+  unsigned char* o = buf;
+  TcsArgs a;
+  a.n = n; a.m = m; a.p = p; a.s = s; a.cs = cs; a.S = S; a.ngroups = G; a.mode = mode;
+  a.H = h->H; a.Hhi = h->Hhi; a.Hlo = h->Hlo; a.Ct = h->Ct; a.ldct = p > 0 ? p : 1; a.R = h->R;
+  a.shifts = reinterpret_cast<const cd*>(shifts); a.hnorm = h->hnorm2;
+  a.Z2 = reinterpret_cast<float4*>(o); o += bZ;
+  a.z2_stride = (size_t)(p + n) * m;
+  a.ZT = bT ? reinterpret_cast<cd*>(o) : nullptr; o += bT;
+  a.Pd = reinterpret_cast<uint16_t*>(o); o += bP;
+  a.pexp = reinterpret_cast<int*>(o); o += bE;
+  a.pc = reinterpret_cast<float4*>(o); o += bC;
+  a.flags = reinterpret_cast<int*>(o);
+  a.err = a.flags + s; o += bF;
+  a.out = reinterpret_cast<cd*>(out); a.ldo = ldo; a.status = status;
+  const int np = resid_tc_npad(n);
+  a.RB = np / kUM;
+  a.KT = np / kKS;
+  int rc = SSV_OK;
+  cudaError_t e = cudaMemsetAsync(a.Pd, 0, bP, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, sizeof(int), st);
+  if (e == cudaSuccess && hdig == nullptr) {
+    rc = resid_tc_split_h(h, o, st);
+    hdig = o;
+  }
+  if (e == cudaSuccess && rc == SSV_OK) {
+    const unsigned char* hb = static_cast<const unsigned char*>(hdig);
+    a.Hs = reinterpret_cast<const uint4*>(hb);
+    a.hexp = reinterpret_cast<const int*>(hb + ((size_t)kDigits * np * np * 2 + 255) / 256 * 256);
+    const size_t psm = sizeof(PanelSmem);
+    e = cudaFuncSetAttribute(tcs_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tcs_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kUpdSmem);
+    if (e == cudaSuccess) {
+      tcs_setup_kernel<<<s, kPT, 0, st>>>(a);
+      count_launch();
+      int nbe_first = (n - m) % kNBT;
+      if (nbe_first == 0) nbe_first = kNBT;
+      int k = n, step = 0;
+      while (k > m) {
+        const int nbe = step == 0 ? nbe_first : kNBT;
+        ++step;
+        tcs_panel_kernel<<<s, kPT, psm, st>>>(a, k, nbe, step);
+        count_launch();
+        const int hrows = k - nbe;
+        if (hrows > 0) {
+          const long long items = (long long)((hrows + kUM - 1) / kUM) * G;
+          const int grid = (int)std::max<long long>(1, std::min<long long>(items, num_sms()));
+          tcs_update_kernel<<<grid, kUT, kUpdSmem, st>>>(a, k, nbe);
+          count_launch();
+        }
+        k -= nbe;
+      }
+      tcs_final_kernel<<<s, kPT, 0, st>>>(a, step, nbe_first);
+      count_launch();
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    rc = SSV_ECUDA;
+  }
+  cudaError_t e2 = cudaFreeAsync(buf, st);
+  if (e2 != cudaSuccess && rc == SSV_OK) {
+    set_cuda_error(e2);
+    rc = SSV_ECUDA;
+  }
+  return rc;
+}
+
+}  // namespace ssv

@@ -48,13 +48,37 @@ static size_t handle_bytes(int n, int m, int p) {
 }
 
 static int check_opts(const ssv_opts* o) {
-  if (o->precision != SSV_FP64 && o->precision != SSV_MIXED && o->precision != SSV_DFLOAT)
+  if (o->precision != SSV_FP64 && o->precision != SSV_MIXED && o->precision != SSV_DFLOAT &&
+      o->precision != SSV_SPLIT)
     return SSV_EINVAL;
   if (o->mode < SSV_G || o->mode > SSV_X) return SSV_EINVAL;
   if (o->nb < 0 || o->tile < 0 || o->max_refine < 0 || !(o->tol >= 0.0)) return SSV_EINVAL;
   if (o->panel != SSV_PANEL_HOUSEHOLDER && o->panel != SSV_PANEL_GIVENS) return SSV_EINVAL;
-  if (o->first != SSV_FIRST_DFLOAT && o->first != SSV_FIRST_C64) return SSV_EINVAL;
+  if (o->first != SSV_FIRST_DFLOAT && o->first != SSV_FIRST_C64 && o->first != SSV_FIRST_TENSOR)
+    return SSV_EINVAL;
   return SSV_OK;
+}
+
+// SSV_SPLIT: the tensor-core sweep; with resid, the backward errors come from
+// the FP64 residual of X-hat (solved once more in X-hat mode for G / TF)
+int solve_split(const Handle* h, int s, const double* shifts, int mode, double* out, long long ldo,
+                int* status, double* resid, cudaStream_t st) {
+  if (!solve_tc_supported(h, mode)) return SSV_ENOTSUP;
+  void* tr = trace_begin("solve_split", st);
+  int rc = solve_tc(h, s, shifts, mode, out, ldo, status, nullptr, st);
+  trace_end(tr, st);
+  if (rc != SSV_OK || resid == nullptr) return rc;
+  if (mode == SSV_XHAT) return backward_error_fp64(h, s, shifts, out, ldo, resid, st);
+  double* xc = nullptr;
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&xc, sizeof(double) * 2 * (size_t)h->n * h->m * s, st));
+  rc = solve_tc(h, s, shifts, SSV_XHAT, xc, h->n, nullptr, nullptr, st);
+  if (rc == SSV_OK) rc = backward_error_fp64(h, s, shifts, xc, h->n, resid, st);
+  cudaError_t e = cudaFreeAsync(xc, st);
+  if (e != cudaSuccess && rc == SSV_OK) {
+    set_cuda_error(e);
+    rc = SSV_ECUDA;
+  }
+  return rc;
 }
 
 }  // namespace ssv
@@ -179,6 +203,8 @@ int ssv_solve(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_in, 
     trace_end(tr, st);
   } else if (o.precision == SSV_MIXED) {
     rc = solve_mixed(h, s, shifts, &o, out, ldo, status, resid, st);
+  } else if (o.precision == SSV_SPLIT) {
+    rc = solve_split(h, s, shifts, o.mode == SSV_X ? SSV_XHAT : o.mode, out, ldo, status, resid, st);
   } else {
     void* tr = trace_begin(o.precision == SSV_DFLOAT ? "solve_dfloat" : "solve_fp64", st);
     rc = solve_fp64(h, s, shifts, &o, out, ldo, status, resid, st);
@@ -312,10 +338,14 @@ int ssv_solve_many(int nsys, const ssv_handle* hs, const int* s, const double* c
   int rc = check_many(nsys, hs, s, shifts, o, outs, ldos);
   if (rc != SSV_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if (o.precision == SSV_MIXED) {
-    for (int k = 0; k < nsys && rc == SSV_OK; ++k)
-      rc = solve_mixed(reinterpret_cast<const Handle*>(hs[k]), s[k], shifts[k], &o, outs[k], ldos[k],
-                       status ? status[k] : nullptr, nullptr, st);
+  if (o.precision == SSV_MIXED || o.precision == SSV_SPLIT) {
+    for (int k = 0; k < nsys && rc == SSV_OK; ++k) {
+      const Handle* hk = reinterpret_cast<const Handle*>(hs[k]);
+      int* stk = status ? status[k] : nullptr;
+      rc = o.precision == SSV_MIXED
+               ? solve_mixed(hk, s[k], shifts[k], &o, outs[k], ldos[k], stk, nullptr, st)
+               : solve_split(hk, s[k], shifts[k], o.mode, outs[k], ldos[k], stk, nullptr, st);
+    }
     return rc;
   }
   // stream-ordered plan on a non-default stream (no device-wide synchronisation);
@@ -345,7 +375,7 @@ int ssv_batch_create(int nsys, const ssv_handle* hs, const int* s, const double*
   if (o_in) o = *o_in; else ssv_default_opts(&o);
   int rc = check_many(nsys, hs, s, shifts, o, outs, ldos);
   if (rc != SSV_OK) return rc;
-  if (o.precision == SSV_MIXED) return SSV_ENOTSUP;
+  if (o.precision == SSV_MIXED || o.precision == SSV_SPLIT) return SSV_ENOTSUP;
   BatchPlan* bp = nullptr;
   rc = batch_create(nsys, reinterpret_cast<const Handle* const*>(hs), s, shifts, &o, outs, ldos,
                     status, &bp, nullptr);
@@ -372,7 +402,7 @@ int ssv_autotune(ssv_handle hh, int s, const double* shifts, const ssv_opts* o_i
   if (o_in) o = *o_in; else ssv_default_opts(&o);
   int rc = check_opts(&o);
   if (rc != SSV_OK) return rc;
-  if (o.mode == SSV_X) return SSV_ENOTSUP;
+  if (o.mode == SSV_X || o.precision == SSV_SPLIT) return SSV_ENOTSUP;  // SSV_SPLIT: n_b = 128
   const bool gmode = (o.mode == SSV_G || o.mode == SSV_TF);
   if (gmode && ldo < (h->p > 0 ? h->p : 1)) return SSV_EINVAL;
   if (!gmode && ldo < h->n) return SSV_EINVAL;
@@ -431,8 +461,12 @@ int ssv_footprint(int n, int m, int p, int s, const ssv_opts* o_in, size_t* byte
   if (o_in) o = *o_in; else ssv_default_opts(&o);
   int rc = check_opts(&o);
   if (rc != SSV_OK) return rc;
-  *bytes = o.precision == SSV_MIXED ? solve_mixed_scratch_bytes(n, m, p, s, &o)
-                                    : solve_fp64_scratch_bytes(n, m, p, s, &o);
+  if (o.precision == SSV_SPLIT)
+    *bytes = solve_tc_scratch_bytes(n, m, p, s, o.mode == SSV_X ? SSV_XHAT : o.mode) +
+             resid_tc_hbytes(n);
+  else
+    *bytes = o.precision == SSV_MIXED ? solve_mixed_scratch_bytes(n, m, p, s, &o)
+                                      : solve_fp64_scratch_bytes(n, m, p, s, &o);
   return SSV_OK;
 }
 

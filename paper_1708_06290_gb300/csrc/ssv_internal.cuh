@@ -160,6 +160,18 @@ int resid_tc_split_h(const Handle* h, void* hbuf, cudaStream_t st);
 int resid_tc_run(const Handle* h, const void* hbuf, void* xbuf, int s, const double* shifts,
                  const int* list, const int* count, const double* Xhat, long long ldx, void* E,
                  double* acc, int* err, cudaStream_t st);
+// K depth of one H digit tile (columns per tile of the layout above)
+int resid_tc_ktile();
+// the sweep with the Z1 P1 update on the tensor cores (solve_tc.cu): m <= 16,
+// n > m, modes G / TF / XHAT; hdig = H digit tiles from resid_tc_split_h, or
+// null to split here
+bool solve_tc_supported(const Handle* h, int mode);
+size_t solve_tc_scratch_bytes(int n, int m, int p, int s, int mode);
+int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out, long long ldo,
+             int* status, const void* hdig, cudaStream_t st);
+// SSV_SPLIT solve (ssv_api.cu): the tensor-core sweep, optional FP64 backward errors
+int solve_split(const Handle* h, int s, const double* shifts, int mode, double* out, long long ldo,
+                int* status, double* resid, cudaStream_t st);
 // normwise backward error of computed Xhat with the tensor-core residual
 int backward_error_tc(const Handle* h, int s, const double* shifts, const double* Xhat,
                       long long ldx, double* eta, cudaStream_t st);

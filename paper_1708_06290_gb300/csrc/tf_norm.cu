@@ -124,6 +124,8 @@ int tf_norm2(const Handle* h, int s, const double* shifts, const ssv_opts* o, do
   SSV_CUDA_TRY(cudaMallocAsync((void**)&G, sizeof(cd) * (size_t)p * m * s, st));
   int rc = og.precision == SSV_MIXED
                ? solve_mixed(h, s, shifts, &og, reinterpret_cast<double*>(G), p, status, nullptr, st)
+           : og.precision == SSV_SPLIT
+               ? solve_split(h, s, shifts, SSV_G, reinterpret_cast<double*>(G), p, status, nullptr, st)
                : solve_fp64(h, s, shifts, &og, reinterpret_cast<double*>(G), p, status, nullptr, st);
   if (rc == SSV_OK) {
     const size_t smem = sizeof(cd) * kWarpsPerBlock * kMaxK * kLdM;

@@ -37,7 +37,8 @@ XHAT = 2
 X = 3
 
 _MODES = {"g": G, "tf": TF, "xhat": XHAT, "x": X}
-_PREC = {"fp64": FP64, "mixed": MIXED, "dfloat": DFLOAT}
+SPLIT = 3
+_PREC = {"fp64": FP64, "mixed": MIXED, "dfloat": DFLOAT, "split": SPLIT}
 
 
 class SsvError(RuntimeError):
@@ -181,7 +182,7 @@ def _need_cuda(t, dtype, name):
 _PANELS = {"householder": 0, "givens": 1}
 
 
-_FIRST = {"dfloat": 0, "c64": 1}
+_FIRST = {"dfloat": 0, "c64": 1, "tensor": 2}
 
 
 def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-13, panel="householder",
