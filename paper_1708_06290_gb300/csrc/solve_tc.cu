@@ -72,7 +72,18 @@ constexpr int kTmemCols = 512;       // 7 levels x 64 columns, rounded up
 // products complete within microseconds)
 constexpr long long kUpdWait = 1LL << 22;
 static_assert(kLev * kUN <= kTmemCols, "TMEM columns of the levels");
-constexpr size_t kUpdSmem = 2 * (size_t)kStageBytes + (size_t)2 * kMaxM * kMaxM * 16 * 4 + 1024;
+// dynamic shared memory of the update, in this order: two stage buffers; the
+// group's P2 / sigma rows (S * 2 m^2 <= 64 m float4); the group's column
+// exponents (kUN ints); its shifts (at most kUN); kIss + 2 mbarriers; the TMEM
+// address slot
+constexpr size_t kOffPc = 2 * (size_t)kStageBytes;
+constexpr size_t kPcF4 = (size_t)64 * kMaxM;
+constexpr size_t kOffExp = kOffPc + kPcF4 * 16;
+constexpr size_t kOffSig = kOffExp + (size_t)kUN * sizeof(int);
+constexpr size_t kOffBar = kOffSig + (size_t)kUN * 16;
+constexpr size_t kOffSlot = kOffBar + (size_t)(kIss + 2) * 8;
+constexpr size_t kUpdSmem = kOffSlot + 16;
+static_assert(kOffBar % 8 == 0 && kOffSig % 16 == 0, "alignment of the smem carve-up");
 static_assert(kUpdSmem <= 227 * 1024, "shared memory of the update");
 
 // element offset in a K-major core-matrix tile (8 rows x 8 K per 128 bytes;
@@ -420,16 +431,17 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
   const int tid = threadIdx.x, warp = tid >> 5;
   const int S = a.S, cs = a.cs, G = a.ngroups;
   // an earlier launch of this solve gave up a wait: its results are void, skip
-  if (*a.err != 0) return;
+  // (the flag is read by every thread and combined, so the whole block agrees)
+  if (__syncthreads_or(*(volatile int*)a.err != 0)) return;
   const int RT = (hrows + kUM - 1) / kUM;
   const long long items = (long long)RT * G;
   const int nst = (nbe + kKS - 1) / kKS;
   const int JH0 = j0 / kKS;
-  float4* pcs = reinterpret_cast<float4*>(smem + 2 * (size_t)kStageBytes);  // S x 2 m m
-  int* fexp = reinterpret_cast<int*>(pcs + (size_t)2 * kMaxM * kMaxM * 4);  // kUN
-  cd* sig = reinterpret_cast<cd*>(fexp + kUN);                              // <= kUN shifts
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sig + kUN);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIss + 2);
+  float4* pcs = reinterpret_cast<float4*>(smem + kOffPc);                   // S x 2 m m
+  int* fexp = reinterpret_cast<int*>(smem + kOffExp);                        // kUN
+  cd* sig = reinterpret_cast<cd*>(smem + kOffSig);                           // <= kUN shifts
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + kOffBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kOffSlot);
   const uint32_t mb = smem_addr(mbar);        // kIss MMA barriers, then two load barriers
   const uint32_t lmb0 = mb + 8u * kIss;
   const uint32_t sBase = smem_addr(smem);
@@ -630,6 +642,8 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
       }
       }
     }
+    // the scratch writes above precede later bulk copies into the same buffer
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     fence_before();
     __syncthreads();
   }
