@@ -40,9 +40,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed", "dfloat"], default="mixed",
+    ap.add_argument("--precision", choices=["fp64", "mixed", "dfloat", "split"], default="mixed",
                     help="headline precision (value, e2e, roofline); the others are timed beside it "
                          "(--profile-solve: the precision of the profiled solve)")
+    ap.add_argument("--first", choices=["tensor", "dfloat", "c64"], default="tensor",
+                    help="first solve of the mixed path")
     ap.add_argument("--side-steps", type=int, default=5,
                     help="timed steps of the comparison precisions")
     ap.add_argument("--nb", type=int, default=0)
@@ -410,10 +412,11 @@ def profile_solve(args):
     sd = torch.from_numpy(sig.astype(np.complex128)).cuda()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    out, st, _ = h.solve(sd, mode="g", precision=args.precision, nb=args.nb)
+    out, st, _ = h.solve(sd, mode="g", precision=args.precision, nb=args.nb, first=args.first)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"profile": "solve", "precision": args.precision, "n": sysr.n, "m": m,
+    print(json.dumps({"profile": "solve", "precision": args.precision, "first": args.first,
+                      "n": sysr.n, "m": m,
                       "shifts": int(len(sig)), "ms": e0.elapsed_time(e1),
                       "nonzero_status": int((st != 0).sum())}))
     h.close()

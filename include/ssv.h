@@ -54,10 +54,12 @@ extern "C" {
 
 /* ---- options ----------------------------------------------------------- */
 #define SSV_FP64 0  /* every step in double / complex128 */
-#define SSV_MIXED 1 /* double-float first solve, certified per shift by an
-                       FP64-accurate residual (tensor cores for m <= 16),
-                       complex64 correction sweeps, FP64 re-solve of shifts
-                       that miss the tolerance */
+#define SSV_MIXED 1 /* a first solve of about 48 bits (by default the SSV_SPLIT
+                       sweep with its tensor-core trailing update, else
+                       double-float; see ssv_opts.first), certified per shift by
+                       an FP64-accurate residual (tensor cores for m <= 16),
+                       complex64 correction sweeps, FP64 re-solve of shifts that
+                       miss the tolerance */
 #define SSV_DFLOAT 2 /* the window panels (reflectors formed in double-word
                         scalars) and the bulk updates of the rows above each
                         block (the Z1 P1 and Z2 P2 products, most of the work) in
@@ -88,10 +90,10 @@ extern "C" {
 
 /* first solve of the mixed path (ssv_opts.first) */
 #define SSV_FIRST_DFLOAT 0 /* double-float sweep (about 48 bits): refinement usually
-                              only certifies it (default) */
+                              only certifies it */
 #define SSV_FIRST_TENSOR 2 /* the SSV_SPLIT sweep (tensor-core trailing update, about
-                              48 bits); where SSV_SPLIT does not apply (m > 16 or
-                              n <= m) the double-float sweep is used instead */
+                              48 bits; default); where SSV_SPLIT does not apply
+                              (m > 16 or n <= m) the double-float sweep is used */
 #define SSV_FIRST_C64 1    /* complex64 sweep (the correction sweep started from
                               Xhat = 0): refinement has to win back every digit
                               beyond single precision, and shifts whose condition
@@ -117,7 +119,7 @@ typedef struct ssv_opts {
 typedef struct ssv_handle_s* ssv_handle;
 
 /* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 8,
- * tol = 1e-13, panel = SSV_PANEL_HOUSEHOLDER, first = SSV_FIRST_DFLOAT.  (The mixed path certifies each
+ * tol = 1e-13, panel = SSV_PANEL_HOUSEHOLDER, first = SSV_FIRST_TENSOR.  (The mixed path certifies each
  * shift with a residual whose own error, as a backward error, is below 5e-15
  * for m <= 16 (the tensor-core residual) and about 1e-14 for wider m (the
  * double-float residual); 1e-13 stays above both.) */

@@ -96,7 +96,7 @@ void ssv_default_opts(ssv_opts* o) {
   o->max_refine = 8;
   o->tol = 1e-13;
   o->panel = SSV_PANEL_HOUSEHOLDER;
-  o->first = SSV_FIRST_DFLOAT;
+  o->first = SSV_FIRST_TENSOR;
 }
 
 static int make_handle(int n, int m, int p, cudaStream_t st, Handle** out) {

@@ -186,7 +186,7 @@ _FIRST = {"dfloat": 0, "c64": 1, "tensor": 2}
 
 
 def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-13, panel="householder",
-         first="dfloat"):
+         first="tensor"):
     o = Opts()
     load().ssv_default_opts(ctypes.byref(o))
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
@@ -255,7 +255,7 @@ class Handle:
 
     def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=8, tol=1e-13,
               out=None, status=None, resid=None, want_resid=False, stream=None, panel="householder",
-              first="dfloat"):
+              first="tensor"):
         """Solve all shifts.  Returns (out, status, resid).
 
         out is a column-major complex128 (rows, s*m) tensor, rows = p for

@@ -1,6 +1,6 @@
 """The refinement route of the mixed path at the benchmark size, forced.
 
-With the default double-float first solve almost every shift of the n = 5000,
+With the default first solves (about 48 bits) almost every shift of the n = 5000,
 m = p = 16 grid workload certifies at once, so the complex64 correction sweeps
 (the unreduced right-hand side carried through the window, Sec. 3.3) and the
 FP64 re-solve of shifts that stagnate would never run.  Starting from a
@@ -73,7 +73,8 @@ def test_c64_first_solve_forces_corrections_and_resolves_on_the_grid(bench_syste
     # inside the disc), straight to the FP64 re-solve
     assert corrections >= 1 and resolves >= 1, (corrections, resolves)
     assert corrections + resolves >= len(sig), (corrections, resolves)
-    # the default double-float first solve, for comparison: fewer corrections
+    # the default first solve (about 48 bits, tensor-core sweep), for comparison:
+    # fewer corrections
     out2, st2, _ = h.solve(sd, mode="g", precision="mixed")
     torch.cuda.synchronize()
     c2, r2 = ssv.refine_counts(reset=True)
