@@ -19,11 +19,12 @@
 //      columns as 2m real ones, padded to a power of two).  Z1 P1 is formed
 //      exactly as in the tensor-core residual (error-free splitting after
 //      Ozaki, Ogita, Oishi and Rump): H's rows and P1's real columns are
-//      written as seven 7-bit digits relative to a power-of-two scale, each
-//      digit exact in BF16, and the 28 digit products H_k P_l with k + l <= 6
-//      run as tcgen05.mma (BF16 x BF16 -> FP32, M = 128, N = 64, K = 16) into
-//      seven TMEM accumulators, one per level k + l, where every partial sum
-//      is an integer below 7 * 128 * 127^2 < 2^24 and therefore exact.  The
+//      written as 7-bit digits relative to a power-of-two scale (eight for a
+//      row of H, seven for a column of P1), each digit exact in BF16, and the
+//      35 digit products H_k P_l with k + l <= 7 run as tcgen05.mma (BF16 x
+//      BF16 -> FP32, M = 128, N = 64, K = 16) into eight TMEM accumulators, one
+//      per level k + l, where every partial sum is an integer below
+//      7 * 128 * 127^2 < 2^24 and therefore exact.  The
 //      digit tiles reach shared memory by 1-D TMA bulk copies on an mbarrier,
 //      two stages in flight.  The epilogue reads the levels back (tcgen05.ld),
 //      adds them scaled by 2^{-7 t} into double-float sums, scales by the row
@@ -32,9 +33,11 @@
 //   3. after the last block: the final m x m block, G = Ct Xhat or X-hat by the
 //      backward pass over the stored block transforms.
 //
-// Accuracy: digits beyond the seventh and the products of level > 6 are
-// dropped, below 2^-48 of the row scale times the column scale (the
-// double-float class of the SSV_DFLOAT sweep).  The first block holds
+// Accuracy: the digits beyond the eighth of H and the seventh of P1 and the
+// products of level > 7 are dropped, about 2^-49 of the row scale times the
+// column scale (the double-float class of the SSV_DFLOAT sweep).  H's rows get
+// all eight digits because a dominant diagonal sets the row scale: the
+// off-diagonal entries of a row can be 2^7 below it.  The first block holds
 // (n - m) mod n_b rows (n_b when that is 0), so that every later block starts
 // at a column that is a multiple of n_b and the H digit tiles (32 columns
 // deep) line up with the fresh columns.
@@ -59,15 +62,16 @@ constexpr int kUM = 128;             // H rows per update item = TMEM lanes
 constexpr int kUN = 64;              // real columns per update item (shift group)
 constexpr int kKS = 32;              // K per shared-memory stage
 constexpr int kKG = kKS / 8;         // core matrices along K in a tile
-constexpr int kSD = 7;               // digits used per operand
-constexpr int kLev = 7;              // levels k + l = 0 .. 6
+constexpr int kSDH = 8;              // digits of H (all eight slices of its digit tiles)
+constexpr int kSD = 7;               // digits of the block transforms' columns
+constexpr int kLev = 8;              // levels k + l = 0 .. 7
 constexpr int kStages = kNBT / kKS;  // stages per block step
 constexpr int kAT = kUM * kKS;       // BF16 elements of one H digit tile
 constexpr int kBT = kUN * kKS;       // BF16 elements of one P1 digit tile
-constexpr uint32_t kStageBytes = (uint32_t)kSD * (kAT + kBT) * 2;
+constexpr uint32_t kStageBytes = (uint32_t)(kSDH * kAT + kSD * kBT) * 2;
 constexpr int kIss = 4;              // threads issuing products (lane 0 of warps 0..3)
 constexpr uint32_t kIdescU = idesc_bf16(kUM, kUN);
-constexpr int kTmemCols = 512;       // 7 levels x 64 columns, rounded up
+constexpr int kTmemCols = 512;       // 8 levels x 64 columns
 // polls of one mbarrier wait before the update gives up (a stage's copies and
 // products complete within microseconds)
 constexpr long long kUpdWait = 1LL << 22;
@@ -93,9 +97,11 @@ __host__ __device__ __forceinline__ int tile_off(int row, int k) {
   return (((row >> 3) * kKG + (k >> 3)) * 8 + (row & 7)) * 8 + (k & 7);
 }
 
-// issuer owning level t (products per level t + 1): {6}, {5, 0}, {4, 1}, {3, 2}
+// products of level t: H digit k, transform digit t - k, k in [max(0, t - 6), min(7, t)]
+// (1, 2, 3, 4, 5, 6, 7, 7 for t = 0 .. 7); issuer owning level t:
+// {7, 1}, {6, 0}, {5, 2}, {4, 3} (9, 8, 9, 9 products)
 __host__ __device__ constexpr int level_owner(int t) {
-  return t == 6 ? 0 : (t == 5 || t == 0) ? 1 : (t == 4 || t == 1) ? 2 : 3;
+  return (t == 7 || t == 1) ? 0 : (t == 6 || t == 0) ? 1 : (t == 5 || t == 2) ? 2 : 3;
 }
 
 // column stride of one shift in a group: 2m real columns rounded up to a power of two
@@ -420,7 +426,7 @@ __global__ void __launch_bounds__(kPT, 2) tcs_panel_kernel(TcsArgs a, int k, int
 }
 
 // ---- update of the H rows above the block: Z2 <- Z1 P1 + Z2 P2 - sigma E P1 --
-constexpr int kUT = 2 * kUM;  // update threads: two per H row of the tile (one per 32 columns)
+constexpr int kUT = 4 * kUM;  // update threads: four per H row of the tile (16 columns each)
 
 __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, int nbe) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -470,12 +476,12 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
     const uint32_t lmb = lmb0 + 8u * (uint32_t)b;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lmb), "r"(kStageBytes)
                  : "memory");
-    for (int l = 0; l < kSD; ++l)
+    for (int l = 0; l < kSDH; ++l)
       bulk_copy(dst + (uint32_t)(l * kAT * 2),
                 a.Hs + ((size_t)(l * a.RB + I) * a.KT + (JH0 + st)) * (kAT / 8), (uint32_t)(kAT * 2), lmb);
     const uint16_t* Pg = a.Pd + (size_t)g * kSD * kStages * kBT;
     for (int l = 0; l < kSD; ++l)
-      bulk_copy(dst + (uint32_t)(kSD * kAT * 2 + l * kBT * 2), Pg + ((size_t)l * kStages + st) * kBT,
+      bulk_copy(dst + (uint32_t)(kSDH * kAT * 2 + l * kBT * 2), Pg + ((size_t)l * kStages + st) * kBT,
                 (uint32_t)(kBT * 2), lmb);
   };
 
@@ -511,19 +517,19 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
       if ((tid & 31) == 0 && iss < kIss) {
         fence_after();
         const uint32_t aBase = sBase + (uint32_t)buf * kStageBytes;
-        const uint32_t bBase = aBase + (uint32_t)(kSD * kAT * 2);
+        const uint32_t bBase = aBase + (uint32_t)(kSDH * kAT * 2);
         constexpr uint32_t kSbo = (uint32_t)kKG * 128u;
 #pragma unroll 1
         for (int lv = 0; lv < kLev; ++lv) {
           if (level_owner(lv) != iss) continue;
 #pragma unroll 1
-          for (int kd = 0; kd <= lv; ++kd) {
+          for (int kd = max(0, lv - (kSD - 1)); kd <= min(kSDH - 1, lv); ++kd) {
             const int ld = lv - kd;
 #pragma unroll
             for (int ks = 0; ks < kKS / 16; ++ks) {
               const uint64_t ad = mat_desc(aBase + (uint32_t)(kd * kAT * 2 + ks * 256), 128u, kSbo);
               const uint64_t bd = mat_desc(bBase + (uint32_t)(ld * kBT * 2 + ks * 256), 128u, kSbo);
-              const bool first = st == 0 && kd == 0 && ks == 0;
+              const bool first = st == 0 && kd == max(0, lv - (kSD - 1)) && ks == 0;
               mma_bf16(tmem + (uint32_t)(lv * kUN), ad, bd, kIdescU, first ? 0u : 1u);
             }
           }
@@ -550,25 +556,26 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
       buf ^= 1;
     }
     if (failed) break;
-    // ---- epilogue: thread (row, chunk) = (tid mod 128, tid / 128): one H row and
-    //      32 of the 64 columns; warps w and w + 4 read TMEM lanes 32 (w mod 4) ..
+    // ---- epilogue: thread (row, quarter) = (tid mod 128, tid / 128) takes one H
+    //      row and 16 of the 64 columns; warps w, w + 4, w + 8, w + 12 read TMEM
+    //      lanes 32 (w mod 4) ..
     fence_after();
-    const int row = tid & (kUM - 1), ch = tid >> 7;
+    const int row = tid & (kUM - 1), qt = tid >> 7;
     const int ih = I * kUM + row;
     const bool live = ih < hrows;
     const int Ei = live ? a.hexp[ih] : 0;
     const int cdr = ih - j0;  // shifted-diagonal correction row of fresh column cdr
     {
-      float ah[32], al[32];
+      float ah[16], al[16];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) { ah[c] = 0.f; al[c] = 0.f; }
+      for (int c = 0; c < 16; ++c) { ah[c] = 0.f; al[c] = 0.f; }
       float sc = 0.0078125f * 0.0078125f;  // 2^{-7 (t + 2)}, t = 0
 #pragma unroll 1
       for (int lv = 0; lv < kLev; ++lv) {
-        uint32_t rr[32];
-        tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(lv * kUN + ch * 32), rr);
+        uint32_t rr[16];
+        tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(lv * kUN + qt * 16), rr);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
+        for (int c = 0; c < 16; ++c) {
           const float pv = __uint_as_float(rr[c]) * sc;
           const float s2 = ah[c] + pv;
           const float bp = s2 - ah[c];
@@ -577,73 +584,73 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
         }
         sc *= 0.0078125f;
       }
-      // the sums go to the stage buffer whose products are done (the other one
-      // is receiving the next item's first stage), one column per 128 float2 of
-      // this chunk's half, so that the per-shift loop below indexes them at run
-      // time; each thread reads back only its own entries
-      float2* esc = reinterpret_cast<float2*>(smem + (size_t)(buf ^ 1) * kStageBytes) + ch * 32 * kUM;
+      // slot j (0 .. 7) of this quarter = group columns col, col + 1 with
+      // col = 16 qt + 2 j: shift l = col / cs, complex column q = (col mod cs) / 2
+      float4 acc[8];
+      bool ok_j[8];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) esc[c * kUM + row] = make_float2(ah[c], al[c]);
-      if (live) {
-      // shifts whose columns lie in this chunk of 32
-      for (int l0 = 0; l0 < 32 / cs && l0 < S; ++l0) {
-        const int l = ch * (32 / cs) + l0;
-        if (l >= S) break;
-        const int sh = g * S + l;
-        if (sh >= a.s) break;
-        float4* Z2f = a.Z2 + (size_t)sh * a.z2_stride;
-        const float4* P2 = pcs + (size_t)l * 2 * m * m;
-        const float4* PS = P2 + m * m;
-        const int b0 = l0 * cs;
-        float4 z2o[kMaxM];
-#pragma unroll
-        for (int qq = 0; qq < kMaxM; ++qq)
-          if (qq < m) z2o[qq] = Z2f[(p + ih) + (size_t)qq * ldz];
-        const cd sg = sig[l];
-        const float4 sgf = df_split(sg);
-#pragma unroll 1
-        for (int q = 0; q < m; ++q) {
-          float rh, rl, xh, xl;
-          {
-            const int er = fexp[l * cs + 2 * q], ei = fexp[l * cs + 2 * q + 1];
-            if (Ei == kBadExp || er == kBadExp || ei == kBadExp) {
-              rh = xh = __int_as_float(0x7fc00000);
-              rl = xl = 0.f;
-            } else {
-              const float2 vr = esc[(b0 + 2 * q) * kUM + row], vi = esc[(b0 + 2 * q + 1) * kUM + row];
-              rh = ldexpf(vr.x, Ei + er);
-              rl = ldexpf(vr.y, Ei + er);
-              xh = ldexpf(vi.x, Ei + ei);
-              xl = ldexpf(vi.y, Ei + ei);
-            }
+      for (int j = 0; j < 8; ++j) {
+        const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
+        ok_j[j] = live && q < m && l < S && g * S + l < a.s;
+        acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok_j[j]) {
+          const int er = fexp[col], ei = fexp[col + 1];
+          if (Ei == kBadExp || er == kBadExp || ei == kBadExp) {
+            acc[j] = make_float4(__int_as_float(0x7fc00000), 0.f, __int_as_float(0x7fc00000), 0.f);
+          } else {
+            acc[j] = make_float4(ldexpf(ah[2 * j], Ei + er), ldexpf(al[2 * j], Ei + er),
+                                 ldexpf(ah[2 * j + 1], Ei + ei), ldexpf(al[2 * j + 1], Ei + ei));
           }
-#pragma unroll
-          for (int qq = 0; qq < kMaxM; ++qq) {
-            if (qq < m) {
-              const float4 zz = z2o[qq];
-              const float4 w = P2[qq * m + q];
-              df_mac(rh, rl, zz.x, zz.y, w.x, w.y);
-              df_mac(rh, rl, -zz.z, -zz.w, w.z, w.w);
-              df_mac(xh, xl, zz.x, zz.y, w.z, w.w);
-              df_mac(xh, xl, zz.z, zz.w, w.x, w.y);
-            }
-          }
-          if (cdr >= 0 && cdr < nsig) {
-            // - sigma P1(cdr, q)
-            const float4 w = PS[cdr * m + q];
-            df_mac(rh, rl, -sgf.x, -sgf.y, w.x, w.y);
-            df_mac(rh, rl, sgf.z, sgf.w, w.z, w.w);
-            df_mac(xh, xl, -sgf.x, -sgf.y, w.z, w.w);
-            df_mac(xh, xl, -sgf.z, -sgf.w, w.x, w.y);
-          }
-          const float sr = rh + rl, si = xh + xl;
-          Z2f[(p + ih) + (size_t)q * ldz] = make_float4(sr, rl - (sr - rh), si, xl - (si - xh));
         }
       }
+      if (live) {
+        // + Z2(row, :) P2(:, q) from the old row of each slot's shift
+#pragma unroll 1
+        for (int qq = 0; qq < m; ++qq) {
+          int lz = -1;
+          float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (!ok_j[j]) continue;
+            const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
+            if (l != lz) {
+              zz = a.Z2[(size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)qq * ldz];
+              lz = l;
+            }
+            const float4 w = pcs[(size_t)l * 2 * m * m + qq * m + q];
+            df_mac(acc[j].x, acc[j].y, zz.x, zz.y, w.x, w.y);
+            df_mac(acc[j].x, acc[j].y, -zz.z, -zz.w, w.z, w.w);
+            df_mac(acc[j].z, acc[j].w, zz.x, zz.y, w.z, w.w);
+            df_mac(acc[j].z, acc[j].w, zz.z, zz.w, w.x, w.y);
+          }
+        }
+        if (cdr >= 0 && cdr < nsig) {
+          // - sigma P1(cdr, q)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (!ok_j[j]) continue;
+            const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
+            const float4 sgf = df_split(sig[l]);
+            const float4 w = pcs[(size_t)l * 2 * m * m + m * m + cdr * m + q];
+            df_mac(acc[j].x, acc[j].y, -sgf.x, -sgf.y, w.x, w.y);
+            df_mac(acc[j].x, acc[j].y, sgf.z, sgf.w, w.z, w.w);
+            df_mac(acc[j].z, acc[j].w, -sgf.x, -sgf.y, w.z, w.w);
+            df_mac(acc[j].z, acc[j].w, -sgf.z, -sgf.w, w.x, w.y);
+          }
+        }
+      }
+      // a shift's row may be shared by two quarters (m > 8): every old entry is
+      // read before any new one is written
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (!ok_j[j]) continue;
+        const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
+        const float sr = acc[j].x + acc[j].y, si = acc[j].z + acc[j].w;
+        a.Z2[(size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)q * ldz] =
+            make_float4(sr, acc[j].y - (sr - acc[j].x), si, acc[j].w - (si - acc[j].z));
       }
     }
-    // the scratch writes above precede later bulk copies into the same buffer
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     fence_before();
     __syncthreads();
   }

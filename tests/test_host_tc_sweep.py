@@ -1,10 +1,11 @@
 """Host models (no GPU) of the tensor-core sweep (SSV_SPLIT and the mixed
 path's first solve):
 
-  * its digit arithmetic: seven 7-bit digits per operand, the 28 products with
-    k + l <= 6 summed per level over a 128-deep block, every level sum exact in
-    FP32, and the recombination 2^(E_h + E_p) sum_t 2^(-7 (t + 2)) L_t within
-    2^-48 of the row and column scales (exact integers and fractions);
+  * its digit arithmetic: eight 7-bit digits per row of H, seven per column of
+    a block transform, the 35 products with k + l <= 7 summed per level over a
+    128-deep block, every level sum exact in FP32, and the recombination
+    2^(E_h + E_p) sum_t 2^(-7 (t + 2)) L_t within about 2^-49 of the row and
+    column scales (exact integers and fractions);
   * its block schedule: the first block takes (n - m) mod n_b rows so that every
     later block starts at a multiple of n_b; the rows above each block are
     updated as Z1 P1 + Z2 P2 - sigma E P1 with the shifted-diagonal rows
@@ -22,7 +23,9 @@ import pytest
 
 import workloads as W
 
-SD = 7      # digits per operand
+SDH = 8     # digits of a row of H
+SD = 7      # digits of a column of a block transform
+LEV = 8     # levels k + l = 0 .. 7
 NB = 128    # block rows = K of one update
 
 
@@ -37,15 +40,25 @@ def digits(x, E):
     return (-1 if math.copysign(1.0, x) < 0 else 1), [(M >> (49 - 7 * l)) & 127 for l in range(8)]
 
 
+def level_pairs(t):
+    """(k, l) digit pairs of level t: H digit k < 8, transform digit l < 7."""
+    return [(k, t - k) for k in range(max(0, t - (SD - 1)), min(SDH - 1, t) + 1)]
+
+
 def test_level_sums_of_one_block_are_exact_in_fp32():
-    # level t sums t + 1 products of 127 x 127 over 128 rows of the block
-    assert max((t + 1) for t in range(7)) * NB * 127 * 127 < 2 ** 24
+    counts = [len(level_pairs(t)) for t in range(LEV)]
+    assert counts == [1, 2, 3, 4, 5, 6, 7, 7] and sum(counts) == 35
+    # the issuers' shares of the products ({7, 1}, {6, 0}, {5, 2}, {4, 3})
+    owner = {7: 0, 1: 0, 6: 1, 0: 1, 5: 2, 2: 2, 4: 3, 3: 3}
+    shares = [sum(counts[t] for t in range(LEV) if owner[t] == i) for i in range(4)]
+    assert shares == [9, 8, 9, 9]
+    assert max(counts) * NB * 127 * 127 < 2 ** 24
 
 
 def test_seven_digit_products_reproduce_the_block_product():
-    """sum_c h_c p_c over one block from the 28 digit products (k + l <= 6),
-    scaled as the update's epilogue scales them, is within K 2^(E_h + E_p - 47)
-    of the exact value: about 2^-48 relative to the row and column scales."""
+    """sum_c h_c p_c over one block from the 35 digit products (k + l <= 7),
+    scaled as the update's epilogue scales them, is within K 2^(E_h + E_p - 48)
+    of the exact value: about 2^-49 relative to the row and column scales."""
     rng = np.random.default_rng(11)
     for K in (1, 56, NB):
         h = rng.standard_normal(K) * 10.0 ** rng.integers(-2, 2, K)
@@ -55,18 +68,18 @@ def test_seven_digit_products_reproduce_the_block_product():
         dp = [digits(float(v), Ep) for v in pcol]
         exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(h, pcol))
         approx = Fraction(0)
-        for t in range(SD):
-            L = sum(sa * sb * da[k] * db[t - k] for k in range(t + 1)
+        for t in range(LEV):
+            L = sum(sa * sb * da[k] * db[l] for k, l in level_pairs(t)
                     for (sa, da), (sb, db) in zip(dh, dp))
             assert abs(L) < 2 ** 24
             approx += Fraction(L) * Fraction(2) ** (Eh + Ep - 7 * (t + 2))
-        bound = K * Fraction(2) ** (Eh + Ep - 47)
+        bound = K * Fraction(2) ** (Eh + Ep - 48)
         assert abs(approx - exact) <= bound
         # the epilogue starts its scale at 2^-14 and divides by 2^7 per level
         assert Fraction(2) ** (-7 * (0 + 2)) == Fraction(1, 2 ** 14)
 
 
-def test_dropping_the_seventh_digit_level_is_detected():
+def test_dropping_the_last_level_is_detected():
     rng = np.random.default_rng(12)
     K = NB
     h = rng.standard_normal(K)
@@ -76,10 +89,37 @@ def test_dropping_the_seventh_digit_level_is_detected():
     dp = [digits(float(v), Ep) for v in pcol]
     exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(h, pcol))
     approx = Fraction(0)
-    for t in range(SD - 1):   # level 6 left out
-        L = sum(sa * sb * da[k] * db[t - k] for k in range(t + 1) for (sa, da), (sb, db) in zip(dh, dp))
+    for t in range(LEV - 2):   # levels 6 and 7 left out
+        L = sum(sa * sb * da[k] * db[l] for k, l in level_pairs(t) for (sa, da), (sb, db) in zip(dh, dp))
         approx += Fraction(L) * Fraction(2) ** (Eh + Ep - 7 * (t + 2))
-    assert abs(approx - exact) > K * Fraction(2) ** (Eh + Ep - 47)
+    assert abs(approx - exact) > K * Fraction(2) ** (Eh + Ep - 48)
+
+
+def test_eighth_digit_of_h_matters_for_a_dominant_diagonal():
+    """A row with one entry 2 and the rest ~0.014 (H of A = -2I + G/sqrt(n)): with
+    seven digits of H the small entries keep only about 42 bits; the eighth
+    digit brings the row's dot product back within 2^-49 of its scale."""
+    rng = np.random.default_rng(13)
+    K = NB
+    h = rng.standard_normal(K) * 0.014
+    h[5] = -2.0
+    pcol = rng.standard_normal(K) * 0.1
+    Eh, Ep = scale_exp(float(np.max(np.abs(h)))), scale_exp(float(np.max(np.abs(pcol))))
+    dh = [digits(float(v), Eh) for v in h]
+    dp = [digits(float(v), Ep) for v in pcol]
+    exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(h, pcol))
+
+    def approx(ndig_h):
+        tot = Fraction(0)
+        for t in range(LEV):
+            L = sum(sa * sb * da[k] * db[l] for k, l in level_pairs(t) if k < ndig_h
+                    for (sa, da), (sb, db) in zip(dh, dp))
+            tot += Fraction(L) * Fraction(2) ** (Eh + Ep - 7 * (t + 2))
+        return tot
+
+    e8, e7 = abs(approx(8) - exact), abs(approx(7) - exact)
+    assert e8 <= K * Fraction(2) ** (Eh + Ep - 48)
+    assert e8 < e7
 
 
 def block_schedule(n, m, nb=NB):
