@@ -603,8 +603,32 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
           }
         }
       }
-      if (live) {
-        // + Z2(row, :) P2(:, q) from the old row of each slot's shift
+      if (live && cs >= 16) {
+        // one shift per quarter (m > 4): slots j are its columns q0 + j
+        const int l = (qt * 16) / cs, q0 = ((qt * 16) % cs) >> 1;
+        if (l < S && g * S + l < a.s) {
+          const float4* zr = a.Z2 + (size_t)(g * S + l) * a.z2_stride + (p + ih);
+          const float4* P2 = pcs + (size_t)l * 2 * m * m + q0;
+          float4 zn = zr[0];
+#pragma unroll 1
+          for (int qq = 0; qq < m; ++qq) {
+            const float4 zz = zn;
+            if (qq + 1 < m) zn = zr[(size_t)(qq + 1) * ldz];  // next entry in flight
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (ok_j[j]) {
+                const float4 w = P2[qq * m + j];
+                df_mac(acc[j].x, acc[j].y, zz.x, zz.y, w.x, w.y);
+                df_mac(acc[j].x, acc[j].y, -zz.z, -zz.w, w.z, w.w);
+                df_mac(acc[j].z, acc[j].w, zz.x, zz.y, w.z, w.w);
+                df_mac(acc[j].z, acc[j].w, zz.z, zz.w, w.x, w.y);
+              }
+            }
+          }
+        }
+      } else if (live) {
+        // several shifts per quarter (m <= 4): + Z2(row, :) P2(:, q) from the old
+        // row of each slot's shift
 #pragma unroll 1
         for (int qq = 0; qq < m; ++qq) {
           int lz = -1;
@@ -624,6 +648,8 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
             df_mac(acc[j].z, acc[j].w, zz.z, zz.w, w.x, w.y);
           }
         }
+      }
+      if (live) {
         if (cdr >= 0 && cdr < nsig) {
           // - sigma P1(cdr, q)
 #pragma unroll
