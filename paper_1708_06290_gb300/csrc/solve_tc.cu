@@ -7,7 +7,7 @@
 // transform, Z2 <- Z1 P1 + Z2 P2 - sigma E P1) multiplies a tile of H that is
 // staged once for a group of shifts.  Per block step:
 //
-//   1. panel (one thread block per shift): the n_b x (n_b + m) window block is
+//   1. panel (one thread block per shift, three per SM): the n_b x (n_b + m) window block is
 //      triangularised bottom-up by one complex Householder reflector per row
 //      over the m + 1 candidate columns (double-word reflector scalars,
 //      double-float application, as in the double-float sweep), giving the
@@ -56,7 +56,7 @@ using namespace tcg;
 constexpr int kPT = 256;             // threads of the setup, panel and final kernels
 constexpr int kNBT = 128;            // n_b of the tensor-core sweep (K of the update)
 constexpr int kMaxM = kTcMaxM;       // m <= 16
-constexpr int kSlots = kMaxM + 2;    // m live + two alternating fresh slots
+constexpr int kSlots = kMaxM + 1;    // m live + the fresh column
 constexpr int kCoefRows = kNBT + kMaxM;
 constexpr int kUM = 128;             // H rows per update item = TMEM lanes
 constexpr int kUN = 64;              // real columns per update item (shift group)
@@ -167,7 +167,7 @@ struct PanelSmem {
   int sing;
 };
 
-__global__ void __launch_bounds__(kPT, 2) tcs_panel_kernel(TcsArgs a, int k, int nbe, int step) {
+__global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int nbe, int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PanelSmem& sm = *reinterpret_cast<PanelSmem*>(smem_raw);
   constexpr int S = kSlots;
@@ -208,8 +208,7 @@ __global__ void __launch_bounds__(kPT, 2) tcs_panel_kernel(TcsArgs a, int k, int
   }
   __syncthreads();
   for (int c = nbe - 1; c >= 0; --c) {
-    const int fs = m + ((nbe - 1 - c) & 1);   // slot holding the fresh column of row c
-    const int fn = (fs == m) ? m + 1 : m;     // slot for the next fresh column
+    const int fs = m;                         // slot of the fresh column of row c
     // the next fresh column is read now, its latency hidden behind this row
     float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c > 0 && tid < c) pre = fresh4(k - nbe + tid, j0 + c - 1);
@@ -251,9 +250,11 @@ __global__ void __launch_bounds__(kPT, 2) tcs_panel_kernel(TcsArgs a, int k, int
     }
     __syncthreads();
     const float4 tauf = vf[kMaxM + 2];
-    if (tauf.x != 0.0f) {
+    {
       const int nrow = c;
       const int ncoef = (nbe - c) + m;
+      // nrow + ncoef <= n_b + m < kPT: each thread has at most one row e = tid,
+      // and the thread of window row e < c holds that row's next fresh entry
       for (int e = tid; e < nrow + ncoef; e += kPT) {
         float4* base;
         int stride;
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(kPT, 2) tcs_panel_kernel(TcsArgs a, int k, int
           base = coef4 + crow * S;
           stride = 1;
         }
+        if (tauf.x != 0.0f) {
         // w = sum_slot base(slot) v(slot)
         float wrh = 0.f, wrl = 0.f, wih = 0.f, wil = 0.f;
         for (int q = 0; q <= m; ++q) {
@@ -293,13 +295,13 @@ __global__ void __launch_bounds__(kPT, 2) tcs_panel_kernel(TcsArgs a, int k, int
           x = make_float4(sr, xrl - (sr - xrh), si, xil - (si - xih));
           base[slot * stride] = x;
         }
+        }
+        // the eliminated column is done with: its slot takes the next fresh
+        // column, whose coefficients are e_{c-1} (row c - 1 is set below; the
+        // rows this loop covers get zero, every other row is zero already)
+        base[fs * stride] = e < nrow ? pre : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-    }
-    if (c > 0) {
-      const int cn = c - 1;
-      if (tid <= cn) cand4[fn * kNBT + tid] = pre;
-      for (int crow = tid; crow < kCoefRows; crow += kPT)
-        coef4[crow * S + fn] = make_float4(crow == cn ? 1.f : 0.f, 0.f, 0.f, 0.f);
+      if (c > 0 && tid == 0) coef4[(c - 1) * S + fs] = make_float4(1.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
   }
@@ -888,6 +890,10 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
     a.hexp = reinterpret_cast<const int*>(hb + ((size_t)kDigits * np * np * 2 + 255) / 256 * 256);
     const size_t psm = sizeof(PanelSmem);
     e = cudaFuncSetAttribute(tcs_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    // three panels per SM (74 KB of shared memory each)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tcs_panel_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(tcs_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kUpdSmem);
