@@ -76,16 +76,19 @@ constexpr int kTmemCols = 512;       // 8 levels x 64 columns
 // products complete within microseconds)
 constexpr long long kUpdWait = 1LL << 22;
 static_assert(kLev * kUN <= kTmemCols, "TMEM columns of the levels");
-// dynamic shared memory of the update, in this order: two stage buffers; the
-// group's P2 / sigma rows (S * 2 m^2 <= 64 m float4); the group's column
-// exponents (kUN ints); its shifts (at most kUN); kIss + 2 mbarriers; the TMEM
-// address slot
+// dynamic shared memory of the update, in this order: two stage buffers (later
+// the group's Z2 and P2 digit tiles); the group's P2 / sigma rows (S * 2 m^2 <=
+// 64 m float4); the column exponents of P1 and of P2's real form (kUN ints
+// each); the row maxima of the quarters (4 x 128 floats); the shifts (at most
+// kUN); kIss + 3 mbarriers; the TMEM address slot
 constexpr size_t kOffPc = 2 * (size_t)kStageBytes;
 constexpr size_t kPcF4 = (size_t)64 * kMaxM;
 constexpr size_t kOffExp = kOffPc + kPcF4 * 16;
-constexpr size_t kOffSig = kOffExp + (size_t)kUN * sizeof(int);
+constexpr size_t kOffExp2 = kOffExp + (size_t)kUN * sizeof(int);
+constexpr size_t kOffXmax = kOffExp2 + (size_t)kUN * sizeof(int);
+constexpr size_t kOffSig = kOffXmax + (size_t)4 * kUM * sizeof(float);
 constexpr size_t kOffBar = kOffSig + (size_t)kUN * 16;
-constexpr size_t kOffSlot = kOffBar + (size_t)(kIss + 2) * 8;
+constexpr size_t kOffSlot = kOffBar + (size_t)(kIss + 3) * 8;
 constexpr size_t kUpdSmem = kOffSlot + 16;
 static_assert(kOffBar % 8 == 0 && kOffSig % 16 == 0, "alignment of the smem carve-up");
 static_assert(kUpdSmem <= 227 * 1024, "shared memory of the update");
@@ -135,7 +138,56 @@ struct TcsArgs {
   const int* hexp;
   int RB, KT;            // row blocks / K blocks of the H digit tiles
   int* err;              // an update wait gave up
+  // Z2 P2 on the tensor cores (cs >= 16, m >= 5): the H rows of every shift's
+  // window columns as digit tiles (row-scaled, K = cs real entries interleaved
+  // Re, Im) and the real form of each step's P2 (column-scaled, cs x cs)
+  int tcz;
+  int npad;
+  uint16_t* Zd;          // [shift][row block][digit][128 x cs]
+  int* zexp;             // [shift][npad] row exponents
+  uint16_t* P2d;         // [shift][digit][cs x cs]
+  int* p2exp;            // [shift][2 kMaxM] column exponents
 };
+
+// digit tiles of window row p + i (H row i) of shift sh, from the double-float
+// values Z2f(p + i, q): the row exponent over the 2m real entries, seven
+// digits of each entry at K = 2q (Re), 2q + 1 (Im), zero up to cs
+__device__ void write_z2_digits(const TcsArgs& a, int sh, int i, const float4* Z2f, int ldz) {
+  const int m = a.m, cs = a.cs, kg = cs / 8;
+  float mx = 0.f;
+  for (int q = 0; q < m; ++q) {
+    const float4 z = Z2f[(a.p + i) + (size_t)q * ldz];
+    mx = fmaxf(mx, fmaxf(fabsf(z.x), fabsf(z.z)));
+    if (!(fabsf(z.x) <= 3.4e38f) || !(fabsf(z.z) <= 3.4e38f)) mx = __int_as_float(0x7f800000);
+  }
+  const int E = scale_exp_f(mx);
+  a.zexp[(size_t)sh * a.npad + i] = E;
+  uint16_t* T = a.Zd + ((size_t)sh * a.RB + i / 128) * 7 * (128 * cs);
+  for (int k8 = 0; k8 < cs; k8 += 8) {
+    unsigned short dg[8][7];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int kk = k8 + e, q = kk >> 1;
+      float hi = 0.f, lo = 0.f;
+      if (q < m) {
+        const float4 z = Z2f[(a.p + i) + (size_t)q * ldz];
+        hi = (kk & 1) ? z.z : z.x;
+        lo = (kk & 1) ? z.w : z.y;
+      }
+      digits7_pair(hi, lo, E, dg[e]);
+    }
+    const int off = tile_off_kg(i % 128, k8, kg);
+#pragma unroll
+    for (int l = 0; l < 7; ++l) {
+      uint4 u;
+      u.x = dg[0][l] | ((unsigned)dg[1][l] << 16);
+      u.y = dg[2][l] | ((unsigned)dg[3][l] << 16);
+      u.z = dg[4][l] | ((unsigned)dg[5][l] << 16);
+      u.w = dg[6][l] | ((unsigned)dg[7][l] << 16);
+      *reinterpret_cast<uint4*>(T + (size_t)l * (128 * cs) + off) = u;
+    }
+  }
+}
 
 __device__ __forceinline__ double shifted_norm2(const double* hnorm, int n, cd sg) {
   return fmax(hnorm[0] - 2.0 * sg.x * hnorm[1] + (double)n * (sg.x * sg.x + sg.y * sg.y), 0.0);
@@ -156,6 +208,10 @@ __global__ void __launch_bounds__(kPT) tcs_setup_kernel(TcsArgs a) {
     Z2[idx] = df_split(z);
   }
   if (threadIdx.x == 0) a.flags[sh] = 0;
+  if (a.tcz) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kPT) write_z2_digits(a, sh, i, Z2, ldz);
+  }
 }
 
 // ---- panel of block step `step` (1-based), rows k - nbe .. k - 1 ------------
@@ -164,6 +220,7 @@ struct PanelSmem {
   float4 coef[kCoefRows * kSlots];
   float4 vf[kMaxM + 4];
   int fexp[2 * kMaxM];
+  int f2exp[2 * kMaxM];
   int sing;
 };
 
@@ -373,6 +430,55 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
       pc[e] = v;
     }
   }
+  // ---- Z2 P2 on the tensor cores: P2's real form (cs x cs, entry (K = 2qq + ri,
+  //      N = 2q + ro) from P2(qq, q): Re for ri = ro, -Im for (1, 0), Im for
+  //      (0, 1)) as seven-digit tiles, column-scaled
+  if (a.tcz) {
+    const int cs = a.cs, kg = cs / 8;
+    for (int c = tid; c < cs; c += kPT) {
+      const int q = c >> 1;
+      float mx = 0.f;
+      if (q < m) {
+        for (int qq = 0; qq < m; ++qq) {
+          const float4 w = coef4[(kNBT + qq) * S + q];
+          mx = fmaxf(mx, fmaxf(fabsf(w.x), fabsf(w.z)));
+          if (!(fabsf(w.x) <= 3.4e38f) || !(fabsf(w.z) <= 3.4e38f)) mx = __int_as_float(0x7f800000);
+        }
+      }
+      const int E = scale_exp_f(mx);
+      sm.f2exp[c] = E;
+      a.p2exp[(size_t)sh * 2 * kMaxM + c] = E;
+    }
+    __syncthreads();
+    uint16_t* T = a.P2d + (size_t)sh * 7 * cs * cs;
+    for (int it = tid; it < cs * (cs / 8); it += kPT) {
+      const int c = it / (cs / 8), k8 = (it % (cs / 8)) * 8;
+      const int q = c >> 1, ro = c & 1, E = sm.f2exp[c];
+      unsigned short dg[8][7];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int kk = k8 + e, qq = kk >> 1, ri = kk & 1;
+        float hi = 0.f, lo = 0.f;
+        if (q < m && qq < m) {
+          const float4 w = coef4[(kNBT + qq) * S + q];
+          if (ri == ro) { hi = w.x; lo = w.y; }
+          else if (ri == 1) { hi = -w.z; lo = -w.w; }
+          else { hi = w.z; lo = w.w; }
+        }
+        digits7_pair(hi, lo, E, dg[e]);
+      }
+      const int off = tile_off_kg(c, k8, kg);
+#pragma unroll
+      for (int l = 0; l < 7; ++l) {
+        uint4 u;
+        u.x = dg[0][l] | ((unsigned)dg[1][l] << 16);
+        u.y = dg[2][l] | ((unsigned)dg[3][l] << 16);
+        u.z = dg[4][l] | ((unsigned)dg[5][l] << 16);
+        u.w = dg[6][l] | ((unsigned)dg[7][l] << 16);
+        *reinterpret_cast<uint4*>(T + (size_t)l * cs * cs + off) = u;
+      }
+    }
+  }
   // ---- X-hat mode: P1 rows into ZT, P2 parked in this shift's output rows
   //      n - step m .. n - (step - 1) m - 1 (read back before the back pass
   //      writes them, since every later block is at least m rows high)
@@ -428,8 +534,44 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
 }
 
 // ---- update of the H rows above the block: Z2 <- Z1 P1 + Z2 P2 - sigma E P1 --
+// the level sums of one thread's 16 TMEM columns (lane = its row), each level t
+// scaled by 2^{-7 (t + 2)} and added into double-float sums
+static __device__ __forceinline__ void drain_levels(uint32_t tl, int nlev, float (&ah)[16],
+                                                    float (&al)[16]) {
+#pragma unroll
+  for (int c = 0; c < 16; ++c) { ah[c] = 0.f; al[c] = 0.f; }
+  float sc = 0.0078125f * 0.0078125f;  // 2^{-7 (t + 2)}, t = 0
+#pragma unroll 1
+  for (int lv = 0; lv < nlev; ++lv) {
+    uint32_t rr[16];
+    tmem_ld16(tl + (uint32_t)(lv * kUN), rr);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float pv = __uint_as_float(rr[c]) * sc;
+      const float s2 = ah[c] + pv;
+      const float bp = s2 - ah[c];
+      al[c] += (ah[c] - (s2 - bp)) + (pv - bp);
+      ah[c] = s2;
+    }
+    sc *= 0.0078125f;
+  }
+}
+
 constexpr int kUT = 4 * kUM;  // update threads: four per H row of the tile (16 columns each)
 
+// The update of block step (k, nbe).  TCZ: Z2 P2 as a second round of digit
+// products on the tensor cores (m >= 5); otherwise in double-float in the
+// epilogue.  Per item (row tile I, group g):
+//   1. the stages of Z1 P1 (H digit tiles x P1 digit tiles) into the eight
+//      TMEM levels, two stage buffers in flight;
+//   2. TCZ: the group's Z2 and P2 digit tiles are copied into the (then free)
+//      stage buffers while the threads drain the Z1 P1 levels into
+//      double-float sums; then the 28 products of Z2 P2 per shift go into
+//      seven TMEM levels, are drained and added;
+//   3. the next item's first stage streams in during the rest of the epilogue:
+//      the shifted-diagonal correction, the new Z2 rows in double-float and
+//      (TCZ) as digit tiles for the next block step.
+template <bool TCZ>
 __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, int nbe) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n = a.n, m = a.m, p = a.p, ldz = p + n;
@@ -447,11 +589,14 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
   const int JH0 = j0 / kKS;
   float4* pcs = reinterpret_cast<float4*>(smem + kOffPc);                   // S x 2 m m
   int* fexp = reinterpret_cast<int*>(smem + kOffExp);                        // kUN
+  int* f2exp = reinterpret_cast<int*>(smem + kOffExp2);                      // kUN
+  float* xmax = reinterpret_cast<float*>(smem + kOffXmax);                   // 4 x 128
   cd* sig = reinterpret_cast<cd*>(smem + kOffSig);                           // <= kUN shifts
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + kOffBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kOffSlot);
-  const uint32_t mb = smem_addr(mbar);        // kIss MMA barriers, then two load barriers
+  const uint32_t mb = smem_addr(mbar);        // kIss MMA barriers, two stage loads, one Z2 / P2 load
   const uint32_t lmb0 = mb + 8u * kIss;
+  const uint32_t lmb2 = mb + 8u * (kIss + 2);
   const uint32_t sBase = smem_addr(smem);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -460,19 +605,24 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int q = 0; q < kIss + 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
+    for (int q = 0; q < kIss + 3; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  uint32_t mphase = 0;
+  uint32_t mphase = 0, l2phase = 0;
   uint32_t lphase[2] = {0u, 0u};
   bool pend[2] = {false, false};  // a stage copy into buffer b not yet seen complete
+  bool pend2 = false;
   bool failed = false;
+  // Z2 / P2 digit bytes of one shift
+  const uint32_t zbytes = 7u * 128u * (uint32_t)cs * 2u;
+  const uint32_t pbytes = 7u * (uint32_t)cs * (uint32_t)cs * 2u;
+  const int kgz = cs / 8;
 
-  // stage st of item (I, g) into buffer b: seven H digit tiles, seven P1 digit tiles
+  // stage st of item (I, g) into buffer b: eight H digit tiles, seven P1 digit tiles
   auto stage_in = [&](int I, int g, int st, int b) {
     const uint32_t dst = sBase + (uint32_t)b * kStageBytes;
     const uint32_t lmb = lmb0 + 8u * (uint32_t)b;
@@ -486,28 +636,44 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
       bulk_copy(dst + (uint32_t)(kSDH * kAT * 2 + l * kBT * 2), Pg + ((size_t)l * kStages + st) * kBT,
                 (uint32_t)(kBT * 2), lmb);
   };
+  // the group's Z2 digit tiles of row tile I, then its P2 digit tiles
+  auto z2_in = [&](int I, int g, int nsh) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lmb2),
+                 "r"((uint32_t)nsh * (zbytes + pbytes))
+                 : "memory");
+    for (int l = 0; l < nsh; ++l) {
+      const int sh = g * S + l;
+      bulk_copy(sBase + (uint32_t)l * zbytes, a.Zd + ((size_t)sh * a.RB + I) * 7 * (128 * cs), zbytes, lmb2);
+      bulk_copy(sBase + (uint32_t)S * zbytes + (uint32_t)l * pbytes, a.P2d + (size_t)sh * 7 * cs * cs,
+                pbytes, lmb2);
+    }
+  };
 
   long long item = blockIdx.x;
   if (item < items) {
     pend[0] = true;
     if (tid == 0) stage_in((int)(item / G), (int)(item % G), 0, 0);
   }
-  int buf = 0;  // buffer holding the next stage to multiply
   for (; item < items && !failed; item += gridDim.x) {
     const int I = (int)(item / G), g = (int)(item % G);
-    // the group's P2 / sigma rows, column exponents and shifts
+    const int nsh = min(S, a.s - g * S);  // shifts of this group
+    // the group's sigma rows (and P2 for the double-float epilogue), column
+    // exponents and shifts
     for (int e = tid; e < S * 2 * m * m; e += kUT) {
       const int l = e / (2 * m * m), o = e % (2 * m * m);
       const int sh = g * S + l;
       pcs[e] = sh < a.s ? a.pc[(size_t)sh * 2 * kMaxM * kMaxM + o] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int e = tid; e < S * 2 * m; e += kUT) {
-      const int l = e / (2 * m), c = e % (2 * m);
+    for (int e = tid; e < S * cs; e += kUT) {
+      const int l = e / cs, c = e % cs;
       const int sh = g * S + l;
-      fexp[l * cs + c] = sh < a.s ? a.pexp[(size_t)sh * 2 * kMaxM + c] : 0;
+      fexp[e] = (sh < a.s && c < 2 * m) ? a.pexp[(size_t)sh * 2 * kMaxM + c] : 0;
+      if (TCZ) f2exp[e] = (sh < a.s) ? a.p2exp[(size_t)sh * 2 * kMaxM + c] : 0;
     }
     for (int l = tid; l < S; l += kUT) sig[l] = (g * S + l < a.s) ? a.shifts[g * S + l] : mkcd(0.0, 0.0);
+    // ---- 1. Z1 P1: stage st in buffer st & 1
     for (int st = 0; st < nst; ++st) {
+      const int buf = st & 1;
       const bool lok = mbar_wait(lmb0 + 8u * (uint32_t)buf, lphase[buf], kUpdWait);
       if (__syncthreads_or(!lok)) {
         failed = true;
@@ -538,15 +704,11 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
         }
         mma_commit(mb + 8u * (uint32_t)iss);
       }
-      // the next stage (of this item, or the first of the next item) streams
-      // into the other buffer, whose products finished in the previous round
+      // the next stage streams into the other buffer, whose products finished
+      // in the previous round
       if (st + 1 < nst) {
         pend[buf ^ 1] = true;
         if (tid == 0) stage_in(I, g, st + 1, buf ^ 1);
-      } else if (item + gridDim.x < items) {
-        const long long nx = item + gridDim.x;
-        pend[buf ^ 1] = true;
-        if (tid == 0) stage_in((int)(nx / G), (int)(nx % G), 0, buf ^ 1);
       }
       bool ok = true;
       for (int q = 0; q < kIss; ++q) ok = mbar_wait(mb + 8u * q, mphase, kUpdWait) && ok;
@@ -555,9 +717,13 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
         break;
       }
       mphase ^= 1u;
-      buf ^= 1;
     }
     if (failed) break;
+    // both stage buffers are free: TCZ fetches the group's Z2 / P2 tiles into them
+    if (TCZ) {
+      pend2 = true;
+      if (tid == 0) z2_in(I, g, nsh);
+    }
     // ---- epilogue: thread (row, quarter) = (tid mod 128, tid / 128) takes one H
     //      row and 16 of the 64 columns; warps w, w + 4, w + 8, w + 12 read TMEM
     //      lanes 32 (w mod 4) ..
@@ -567,29 +733,14 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
     const bool live = ih < hrows;
     const int Ei = live ? a.hexp[ih] : 0;
     const int cdr = ih - j0;  // shifted-diagonal correction row of fresh column cdr
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(qt * 16);
+    float4 acc[8];
+    bool ok_j[8];
     {
       float ah[16], al[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) { ah[c] = 0.f; al[c] = 0.f; }
-      float sc = 0.0078125f * 0.0078125f;  // 2^{-7 (t + 2)}, t = 0
-#pragma unroll 1
-      for (int lv = 0; lv < kLev; ++lv) {
-        uint32_t rr[16];
-        tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(lv * kUN + qt * 16), rr);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float pv = __uint_as_float(rr[c]) * sc;
-          const float s2 = ah[c] + pv;
-          const float bp = s2 - ah[c];
-          al[c] += (ah[c] - (s2 - bp)) + (pv - bp);
-          ah[c] = s2;
-        }
-        sc *= 0.0078125f;
-      }
+      drain_levels(tl, kLev, ah, al);
       // slot j (0 .. 7) of this quarter = group columns col, col + 1 with
       // col = 16 qt + 2 j: shift l = col / cs, complex column q = (col mod cs) / 2
-      float4 acc[8];
-      bool ok_j[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
@@ -605,78 +756,180 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
           }
         }
       }
-      if (live && cs >= 16) {
-        // one shift per quarter (m > 4): slots j are its columns q0 + j
-        const int l = (qt * 16) / cs, q0 = ((qt * 16) % cs) >> 1;
-        if (l < S && g * S + l < a.s) {
-          const float4* zr = a.Z2 + (size_t)(g * S + l) * a.z2_stride + (p + ih);
-          const float4* P2 = pcs + (size_t)l * 2 * m * m + q0;
-          float4 zn = zr[0];
+    }
+    if (TCZ) {
+      // ---- 2. Z2 P2: the levels of Z1 P1 are read; the same TMEM columns take
+      //      the seven levels of the group's Z2 digit tiles x P2 digit tiles
+      fence_before();
+      __syncthreads();
+      const bool lok = mbar_wait(lmb2, l2phase, kUpdWait);
+      if (__syncthreads_or(!lok)) {
+        failed = true;
+        break;
+      }
+      l2phase ^= 1u;
+      pend2 = false;
+      const int iss = tid >> 5;
+      if ((tid & 31) == 0 && iss < kIss) {
+        fence_after();
+        const uint32_t idz = idesc_bf16(kUM, cs);
+        const uint32_t sboz = (uint32_t)kgz * 128u;
 #pragma unroll 1
-          for (int qq = 0; qq < m; ++qq) {
-            const float4 zz = zn;
-            if (qq + 1 < m) zn = zr[(size_t)(qq + 1) * ldz];  // next entry in flight
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              if (ok_j[j]) {
-                const float4 w = P2[qq * m + j];
-                df_mac(acc[j].x, acc[j].y, zz.x, zz.y, w.x, w.y);
-                df_mac(acc[j].x, acc[j].y, -zz.z, -zz.w, w.z, w.w);
-                df_mac(acc[j].z, acc[j].w, zz.x, zz.y, w.z, w.w);
-                df_mac(acc[j].z, acc[j].w, zz.z, zz.w, w.x, w.y);
+        for (int lv = 0; lv < 7; ++lv) {
+          if (level_owner(lv) != iss) continue;
+#pragma unroll 1
+          for (int l = 0; l < nsh; ++l) {
+            const uint32_t zb = sBase + (uint32_t)l * zbytes;
+            const uint32_t pb = sBase + (uint32_t)S * zbytes + (uint32_t)l * pbytes;
+#pragma unroll 1
+            for (int kd = 0; kd <= lv; ++kd) {
+              const int ld = lv - kd;
+#pragma unroll 1
+              for (int ks = 0; ks < cs / 16; ++ks) {
+                const uint64_t ad = mat_desc(zb + (uint32_t)(kd * 128 * cs * 2 + ks * 256), 128u, sboz);
+                const uint64_t bd = mat_desc(pb + (uint32_t)(ld * cs * cs * 2 + ks * 256), 128u, sboz);
+                mma_bf16(tmem + (uint32_t)(lv * kUN + l * cs), ad, bd, idz, (kd == 0 && ks == 0) ? 0u : 1u);
               }
             }
           }
         }
-      } else if (live) {
-        // several shifts per quarter (m <= 4): + Z2(row, :) P2(:, q) from the old
-        // row of each slot's shift
+        mma_commit(mb + 8u * (uint32_t)iss);
+      }
+      bool ok = true;
+      for (int q = 0; q < kIss; ++q) ok = mbar_wait(mb + 8u * q, mphase, kUpdWait) && ok;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      mphase ^= 1u;
+    }
+    // ---- 3. the stage buffers are free again: the next item's first stage
+    //      streams in during the rest of the epilogue
+    if (item + gridDim.x < items) {
+      const long long nx = item + gridDim.x;
+      pend[0] = true;
+      if (tid == 0) stage_in((int)(nx / G), (int)(nx % G), 0, 0);
+    }
+    if (TCZ) {
+      fence_after();
+      float ah[16], al[16];
+      drain_levels(tl, 7, ah, al);
+      const int l = (qt * 16) / cs;  // one shift per quarter (cs >= 16)
+      const int sh = g * S + l;
+      const int Ez = (live && sh < a.s) ? a.zexp[(size_t)sh * a.npad + ih] : 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (!ok_j[j]) continue;
+        const int col = qt * 16 + 2 * j;
+        const int fr = f2exp[col], fi = f2exp[col + 1];
+        if (Ez == kBadExp || fr == kBadExp || fi == kBadExp) {
+          acc[j] = make_float4(__int_as_float(0x7fc00000), 0.f, __int_as_float(0x7fc00000), 0.f);
+          continue;
+        }
+        // acc += level sum, both double-float: two-sum of the high words
+        auto addpair = [](float& h, float& lo, float bh, float bl) {
+          const float s2 = h + bh;
+          const float bp = s2 - h;
+          lo += ((h - (s2 - bp)) + (bh - bp)) + bl;
+          h = s2;
+        };
+        addpair(acc[j].x, acc[j].y, ldexpf(ah[2 * j], Ez + fr), ldexpf(al[2 * j], Ez + fr));
+        addpair(acc[j].z, acc[j].w, ldexpf(ah[2 * j + 1], Ez + fi), ldexpf(al[2 * j + 1], Ez + fi));
+      }
+    } else if (live) {
+      // several shifts per quarter (m <= 4): + Z2(row, :) P2(:, q) in
+      // double-float from the old row of each slot's shift
 #pragma unroll 1
-        for (int qq = 0; qq < m; ++qq) {
-          int lz = -1;
-          float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int qq = 0; qq < m; ++qq) {
+        int lz = -1;
+        float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            if (!ok_j[j]) continue;
-            const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
-            if (l != lz) {
-              zz = a.Z2[(size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)qq * ldz];
-              lz = l;
-            }
-            const float4 w = pcs[(size_t)l * 2 * m * m + qq * m + q];
-            df_mac(acc[j].x, acc[j].y, zz.x, zz.y, w.x, w.y);
-            df_mac(acc[j].x, acc[j].y, -zz.z, -zz.w, w.z, w.w);
-            df_mac(acc[j].z, acc[j].w, zz.x, zz.y, w.z, w.w);
-            df_mac(acc[j].z, acc[j].w, zz.z, zz.w, w.x, w.y);
+        for (int j = 0; j < 8; ++j) {
+          if (!ok_j[j]) continue;
+          const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
+          if (l != lz) {
+            zz = a.Z2[(size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)qq * ldz];
+            lz = l;
           }
+          const float4 w = pcs[(size_t)l * 2 * m * m + qq * m + q];
+          df_mac(acc[j].x, acc[j].y, zz.x, zz.y, w.x, w.y);
+          df_mac(acc[j].x, acc[j].y, -zz.z, -zz.w, w.z, w.w);
+          df_mac(acc[j].z, acc[j].w, zz.x, zz.y, w.z, w.w);
+          df_mac(acc[j].z, acc[j].w, zz.z, zz.w, w.x, w.y);
         }
       }
-      if (live) {
-        if (cdr >= 0 && cdr < nsig) {
-          // - sigma P1(cdr, q)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            if (!ok_j[j]) continue;
-            const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
-            const float4 sgf = df_split(sig[l]);
-            const float4 w = pcs[(size_t)l * 2 * m * m + m * m + cdr * m + q];
-            df_mac(acc[j].x, acc[j].y, -sgf.x, -sgf.y, w.x, w.y);
-            df_mac(acc[j].x, acc[j].y, sgf.z, sgf.w, w.z, w.w);
-            df_mac(acc[j].z, acc[j].w, -sgf.x, -sgf.y, w.z, w.w);
-            df_mac(acc[j].z, acc[j].w, -sgf.z, -sgf.w, w.x, w.y);
-          }
-        }
-      }
-      // a shift's row may be shared by two quarters (m > 8): every old entry is
-      // read before any new one is written
-      __syncthreads();
+    }
+    if (live && cdr >= 0 && cdr < nsig) {
+      // - sigma P1(cdr, q)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         if (!ok_j[j]) continue;
         const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
-        const float sr = acc[j].x + acc[j].y, si = acc[j].z + acc[j].w;
-        a.Z2[(size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)q * ldz] =
-            make_float4(sr, acc[j].y - (sr - acc[j].x), si, acc[j].w - (si - acc[j].z));
+        const float4 sgf = df_split(sig[l]);
+        const float4 w = pcs[(size_t)l * 2 * m * m + m * m + cdr * m + q];
+        df_mac(acc[j].x, acc[j].y, -sgf.x, -sgf.y, w.x, w.y);
+        df_mac(acc[j].x, acc[j].y, sgf.z, sgf.w, w.z, w.w);
+        df_mac(acc[j].z, acc[j].w, -sgf.x, -sgf.y, w.z, w.w);
+        df_mac(acc[j].z, acc[j].w, -sgf.z, -sgf.w, w.x, w.y);
+      }
+    }
+    // normalised pairs
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float sr = acc[j].x + acc[j].y, si = acc[j].z + acc[j].w;
+      acc[j] = make_float4(sr, acc[j].y - (sr - acc[j].x), si, acc[j].w - (si - acc[j].z));
+    }
+    float mx = 0.f;
+    if (TCZ) {
+      // the new row's digit exponent: the maximum over the shift's 2m entries,
+      // which two quarters share when cs = 32
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (!ok_j[j]) continue;
+        mx = fmaxf(mx, fmaxf(fabsf(acc[j].x), fabsf(acc[j].z)));
+        if (!(fabsf(acc[j].x) <= 3.4e38f) || !(fabsf(acc[j].z) <= 3.4e38f)) mx = __int_as_float(0x7f800000);
+      }
+      xmax[qt * kUM + row] = mx;
+    }
+    // a shift's row may be shared by two quarters: every old entry (double-float
+    // path) and every maximum is read before the writes below
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (!ok_j[j]) continue;
+      const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
+      a.Z2[(size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)q * ldz] = acc[j];
+    }
+    if (TCZ && live) {
+      const int l = (qt * 16) / cs, sh = g * S + l;
+      if (sh < a.s) {
+        if (cs == 32) mx = fmaxf(mx, xmax[(qt ^ 1) * kUM + row]);
+        const int E = scale_exp_f(mx);
+        const int kb = (qt * 16) % cs;  // this quarter's first K entry of the row
+        if ((qt * 16) % cs == 0) a.zexp[(size_t)sh * a.npad + ih] = E;
+        uint16_t* T = a.Zd + ((size_t)sh * a.RB + I) * 7 * (128 * cs);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          unsigned short dg[8][7];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int j = h * 4 + (e >> 1);
+            const bool use = ok_j[j];
+            const float hi = use ? ((e & 1) ? acc[j].z : acc[j].x) : 0.f;
+            const float lo = use ? ((e & 1) ? acc[j].w : acc[j].y) : 0.f;
+            digits7_pair(hi, lo, E, dg[e]);
+          }
+          const int off = tile_off_kg(row, kb + h * 8, kgz);
+#pragma unroll
+          for (int l2 = 0; l2 < 7; ++l2) {
+            uint4 u;
+            u.x = dg[0][l2] | ((unsigned)dg[1][l2] << 16);
+            u.y = dg[2][l2] | ((unsigned)dg[3][l2] << 16);
+            u.z = dg[4][l2] | ((unsigned)dg[5][l2] << 16);
+            u.w = dg[6][l2] | ((unsigned)dg[7][l2] << 16);
+            *reinterpret_cast<uint4*>(T + (size_t)l2 * (128 * cs) + off) = u;
+          }
+        }
       }
     }
     fence_before();
@@ -690,6 +943,7 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
       for (int q = 0; q < kIss; ++q) mbar_wait(mb + 8u * q, mphase, kUpdWait);
       for (int b = 0; b < 2; ++b)
         if (pend[b]) mbar_wait(lmb0 + 8u * (uint32_t)b, lphase[b], kUpdWait);
+      if (pend2) mbar_wait(lmb2, l2phase, kUpdWait);
     }
     __syncthreads();
   }
@@ -839,6 +1093,11 @@ size_t solve_tc_scratch_bytes(int n, int m, int p, int s, int mode) {
   if (mode == SSV_XHAT) b += al(sizeof(cd) * (size_t)s * (size_t)n * m);
   b += al(G * kSD * kStages * kBT * 2) + al(sizeof(int) * (size_t)s * 2 * kMaxM) +
        al(sizeof(float4) * (size_t)s * 2 * kMaxM * kMaxM) + al(sizeof(int) * ((size_t)s + 1));
+  if (cs >= 16) {  // Z2 P2 on the tensor cores: window and P2 digit tiles
+    const size_t np = (size_t)resid_tc_npad(n);
+    b += al((size_t)s * np * 7 * cs * 2) + al(sizeof(int) * (size_t)s * np) +
+         al((size_t)s * 7 * cs * cs * 2) + al(sizeof(int) * (size_t)s * 2 * kMaxM);
+  }
   return b + 256;
 }
 
@@ -858,8 +1117,15 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
   const size_t bC = al(sizeof(float4) * (size_t)s * 2 * kMaxM * kMaxM);
   const size_t bF = al(sizeof(int) * ((size_t)s + 1));
   const size_t bH = hdig == nullptr ? al(resid_tc_hbytes(n)) : 0;
+  const int np = resid_tc_npad(n);
+  const bool tcz = cs >= 16;
+  const size_t bZd = tcz ? al((size_t)s * np * 7 * cs * 2) : 0;
+  const size_t bZe = tcz ? al(sizeof(int) * (size_t)s * np) : 0;
+  const size_t bPd2 = tcz ? al((size_t)s * 7 * cs * cs * 2) : 0;
+  const size_t bPe2 = tcz ? al(sizeof(int) * (size_t)s * 2 * kMaxM) : 0;
   unsigned char* buf = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&buf, bZ + bT + bP + bE + bC + bF + bH, st));
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&buf,
+                               bZ + bT + bP + bE + bC + bF + bZd + bZe + bPd2 + bPe2 + bH, st));
   unsigned char* o = buf;
   TcsArgs a;
   a.n = n; a.m = m; a.p = p; a.s = s; a.cs = cs; a.S = S; a.ngroups = G; a.mode = mode;
@@ -873,8 +1139,13 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
   a.pc = reinterpret_cast<float4*>(o); o += bC;
   a.flags = reinterpret_cast<int*>(o);
   a.err = a.flags + s; o += bF;
+  a.tcz = tcz ? 1 : 0;
+  a.npad = np;
+  a.Zd = tcz ? reinterpret_cast<uint16_t*>(o) : nullptr; o += bZd;
+  a.zexp = tcz ? reinterpret_cast<int*>(o) : nullptr; o += bZe;
+  a.P2d = tcz ? reinterpret_cast<uint16_t*>(o) : nullptr; o += bPd2;
+  a.p2exp = tcz ? reinterpret_cast<int*>(o) : nullptr; o += bPe2;
   a.out = reinterpret_cast<cd*>(out); a.ldo = ldo; a.status = status;
-  const int np = resid_tc_npad(n);
   a.RB = np / kUM;
   a.KT = np / kKS;
   int rc = SSV_OK;
@@ -895,7 +1166,10 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
       e = cudaFuncSetAttribute(tcs_panel_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                (int)cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tcs_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(tcs_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kUpdSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tcs_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kUpdSmem);
     if (e == cudaSuccess) {
       tcs_setup_kernel<<<s, kPT, 0, st>>>(a);
@@ -912,7 +1186,8 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
         if (hrows > 0) {
           const long long items = (long long)((hrows + kUM - 1) / kUM) * G;
           const int grid = (int)std::max<long long>(1, std::min<long long>(items, num_sms()));
-          tcs_update_kernel<<<grid, kUT, kUpdSmem, st>>>(a, k, nbe);
+          if (tcz) tcs_update_kernel<true><<<grid, kUT, kUpdSmem, st>>>(a, k, nbe);
+          else tcs_update_kernel<false><<<grid, kUT, kUpdSmem, st>>>(a, k, nbe);
           count_launch();
         }
         k -= nbe;

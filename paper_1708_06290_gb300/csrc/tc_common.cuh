@@ -47,6 +47,46 @@ static __device__ __forceinline__ void digits8(double x, int E, unsigned short (
   }
 }
 
+// 2^E > |x| for the largest |x| of a row of FP32 high words (a double-float row:
+// |hi + lo| < 2^E as well, since |lo| <= ulp(hi) / 2), from the exponent field
+static __device__ __forceinline__ int scale_exp_f(float maxabs) {
+  const unsigned b = __float_as_uint(maxabs);
+  if ((b & 0x7f800000u) == 0x7f800000u) return kBadExp;  // Inf or NaN
+  const int eb = (int)((b >> 23) & 0xffu);
+  return eb == 0 ? -126 : eb - 126;
+}
+
+// the seven 7-bit digits of x = hi + lo (a double-float value, |x| < 2^E)
+// relative to 2^E, as BF16 bit patterns: each word's 24-bit significand is
+// shifted to units of 2^{E - 56} (truncated toward zero) from its bit fields,
+// the low word with its own sign, so no FP64 arithmetic is involved
+static __device__ __forceinline__ void digits7_pair(float hi, float lo, int E, unsigned short (&d)[7]) {
+  auto part = [E](float f) -> long long {
+    const unsigned b = __float_as_uint(f);
+    const int eb = (int)((b >> 23) & 0xffu);
+    const long long mi = (long long)(b & 0x7fffffu) | (eb ? (1ll << 23) : 0ll);
+    const int sh = (eb ? eb : 1) - 94 - E;
+    const long long v = sh >= 0 ? (mi << sh) : (sh > -64 ? (mi >> (-sh)) : 0ll);
+    return (b >> 31) ? -v : v;
+  };
+  const long long M = (E == kBadExp) ? 0ll : part(hi) + part(lo);
+  const unsigned short sgn = M < 0 ? (unsigned short)0x8000u : (unsigned short)0u;
+  const unsigned long long U = (unsigned long long)(M < 0 ? -M : M);
+#pragma unroll
+  for (int l = 0; l < 7; ++l) {
+    const unsigned int dig = (unsigned int)(U >> (49 - 7 * l)) & 127u;
+    const float f = __uint_as_float(0x4B000000u | dig) - 8388608.0f;
+    d[l] = (unsigned short)(__float_as_uint(f) >> 16) | sgn;
+  }
+}
+
+// element offset in a K-major core-matrix tile with kg core matrices along K
+// (8 rows x 8 K elements per 128 bytes; byte strides 128 along K, kg * 128
+// along rows)
+__host__ __device__ __forceinline__ int tile_off_kg(int row, int k, int kg) {
+  return (((row >> 3) * kg + (k >> 3)) * 8 + (row & 7)) * 8 + (k & 7);
+}
+
 static __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }

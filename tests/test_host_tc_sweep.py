@@ -247,3 +247,63 @@ def test_schedule_model_misplaced_diagonal_correction_fails(ora):
         return X
 
     assert np.linalg.norm(bad_model() - Xo[0]) > 1e-6 * np.linalg.norm(Xo[0])
+
+
+def real_form_B(P2):
+    """The real (2m x 2m) operand of Z2 P2 with Z2's row interleaved as
+    [Re z_0, Im z_0, Re z_1, ...] and the output interleaved the same way:
+    B[2i, 2q] = Re P(i, q), B[2i + 1, 2q] = -Im P(i, q),
+    B[2i, 2q + 1] = Im P(i, q), B[2i + 1, 2q + 1] = Re P(i, q)."""
+    m = P2.shape[0]
+    B = np.zeros((2 * m, 2 * m))
+    B[0::2, 0::2] = P2.real
+    B[1::2, 0::2] = -P2.imag
+    B[0::2, 1::2] = P2.imag
+    B[1::2, 1::2] = P2.real
+    return B
+
+
+def test_real_form_of_the_z2_p2_product():
+    rng = np.random.default_rng(21)
+    for m in (1, 5, 16):
+        Z = rng.standard_normal((7, m)) + 1j * rng.standard_normal((7, m))
+        P = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+        zr = np.zeros((7, 2 * m))
+        zr[:, 0::2], zr[:, 1::2] = Z.real, Z.imag
+        out = zr @ real_form_B(P)
+        W = Z @ P
+        assert np.allclose(out[:, 0::2], W.real) and np.allclose(out[:, 1::2], W.imag)
+
+
+def float_pair_digits(hi, lo, E):
+    """The kernel's digits of x = hi + lo (two FP32 words) relative to 2^E,
+    formed from the words' bit fields without FP64: each word contributes its
+    24-bit significand shifted to 2^(56 - E) units (truncated toward zero), the
+    low word with its own sign."""
+    def part(f):
+        f = float(np.float32(f))
+        if f == 0.0:
+            return 0
+        mnt, ex = math.frexp(abs(f))          # |f| = mnt 2^ex, 0.5 <= mnt < 1
+        mi = int(mnt * 2 ** 24)               # 24-bit significand
+        sh = ex - 24 + 56 - E
+        v = mi << sh if sh >= 0 else mi >> (-sh)
+        return v if f > 0 else -v
+    M = part(hi) + part(lo)
+    s = -1 if M < 0 else 1
+    M = abs(M)
+    assert M < 2 ** 56
+    return s, [(M >> (49 - 7 * l)) & 127 for l in range(7)]
+
+
+def test_float_pair_digits_match_the_exact_value():
+    rng = np.random.default_rng(22)
+    for _ in range(300):
+        x = float(rng.standard_normal() * 10.0 ** rng.integers(-3, 3))
+        hi = float(np.float32(x))
+        lo = float(np.float32(x - hi))
+        E = scale_exp(abs(hi) * (1 + 2 ** -23))
+        s, d = float_pair_digits(hi, lo, E)
+        val = s * sum(Fraction(dl) * Fraction(2) ** (E - 7 * (l + 1)) for l, dl in enumerate(d))
+        exact = Fraction(hi) + Fraction(lo)
+        assert abs(val - exact) <= Fraction(2) ** (E - 48)
