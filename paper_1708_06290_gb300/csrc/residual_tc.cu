@@ -44,7 +44,10 @@ constexpr int kN = 32;        // real columns per shift (2m, zero-padded)
 // stage prefetched 208; two CTAs per SM, 16-deep stages, prefetched 142; two
 // CTAs per SM, 32-deep stages, one buffer 128, with two issuers 122, with four
 // 112, and staged by TMA bulk copies instead of cp.async 106 (the default);
-// without the products at all 61 (staging by cp.async, and readout).
+// without the products at all 61 (staging by cp.async, and readout).  TMA bulk
+// copies into two buffers: 16-deep stages, two CTAs per SM 136; 32-deep
+// stages, one CTA per SM with two TMEM windows 152 (the N = 32 products, not
+// the copies, set the pace).
 #ifndef SSV_TC_KS
 #define SSV_TC_KS 32          // K per shared-memory stage (16 or 32)
 #endif
@@ -78,7 +81,7 @@ constexpr int kCtasPerSm = kTwoWin ? 1 : 2;
 constexpr uint32_t kStageBytes = (uint32_t)kSl * (kAT + kBT) * 2;
 constexpr int kBuf = SSV_TC_BUFFERS;  // 2: the next stage streams in during the products
 constexpr int kIss = SSV_TC_ISSUERS;  // threads issuing products (lane 0 of warps 0 ..)
-constexpr bool kBulk = SSV_TC_BULK != 0 && SSV_TC_BUFFERS == 1;
+constexpr bool kBulk = SSV_TC_BULK != 0;
 static_assert(kIss == 1 || kIss == 2 || kIss == 4, "issuers");
 constexpr size_t kSmem = kBuf * (size_t)kStageBytes + 64;
 static_assert(kCtasPerSm * kSmem <= 227 * 1024, "shared memory of the resident CTAs");
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
   extern __shared__ __align__(128) unsigned char smem[];
   // two stage buffers, each: kSl H slice tiles (kAT) then kSl Xhat slice tiles (kBT)
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + kBuf * kStageBytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIss + 1);  // mbar[kIss]: stage loads
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIss + kBuf);  // mbar[kIss + b]: loads of buffer b
   __shared__ double red[2][kM / 32];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int KT = npad / kKS, RB = npad / kM;
@@ -258,14 +261,16 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int q = 0; q <= kIss; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
+    for (int q = 0; q < kIss + kBuf; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  uint32_t phase = 0, lphase = 0;
+  uint32_t phase = 0;
+  uint32_t lphase[2] = {0u, 0u};
+  bool pend[2] = {false, false};  // a bulk copy into buffer b not yet seen complete
   const uint32_t lmb = mb + 8u * kIss;
   bool failed = false;
   float ah[kN], al[kN];
@@ -274,15 +279,17 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
     const uint32_t dst = sBase + (uint32_t)b * kStageBytes;
     if constexpr (kBulk) {
       // sixteen contiguous tiles: one thread, sixteen TMA bulk copies
+      pend[b] = true;
       if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lmb), "r"(kStageBytes)
+        const uint32_t lb = lmb + 8u * (uint32_t)b;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lb), "r"(kStageBytes)
                      : "memory");
         for (int k = 0; k < kSl; ++k)
           bulk_copy(dst + (uint32_t)(k * kAT * 2), Hs + ((size_t)(k * RB + I) * KT + J) * (kAT / 8),
-                    (uint32_t)(kAT * 2), lmb);
+                    (uint32_t)(kAT * 2), lb);
         for (int l = 0; l < kSl; ++l)
           bulk_copy(dst + (uint32_t)(kSl * kAT * 2 + l * kBT * 2),
-                    Xs + ((size_t)(sh * kSl + l) * KT + J) * (kBT / 8), (uint32_t)(kBT * 2), lmb);
+                    Xs + ((size_t)(sh * kSl + l) * KT + J) * (kBT / 8), (uint32_t)(kBT * 2), lb);
       }
     } else {
       for (int v = tid; v < kSl * (kAT + kBT) / 8; v += kM) {
@@ -333,12 +340,13 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
       if (kBuf == 1) stage_in(I, sh, J0 + st, 0);
       if constexpr (kBulk) {
         // the tiles land through the async proxy that the products read
-        const bool lok = mbar_wait(lmb, lphase);
-        lphase ^= 1u;
+        const bool lok = mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
         if (__syncthreads_or(!lok)) {
           failed = true;
           break;
         }
+        lphase[b] ^= 1u;
+        pend[b] = false;
       } else {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -463,7 +471,9 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
     if (tid == 0) {
       atomicExch(err, 1);
       for (int q = 0; q < kIss; ++q) mbar_wait(mb + 8u * q, phase ^ 1u);
-      if (kBulk) mbar_wait(lmb, lphase ^ 1u);
+      if (kBulk)
+        for (int b = 0; b < kBuf; ++b)
+          if (pend[b]) mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
