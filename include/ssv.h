@@ -109,7 +109,6 @@ typedef struct ssv_opts {
   int precision;           /* SSV_FP64, SSV_MIXED, SSV_DFLOAT or SSV_SPLIT */
   int mode;                /* SSV_G, SSV_TF, SSV_XHAT, SSV_X */
   int nb;                  /* rows per elimination block n_b; 0 = default */
-  int tile;                /* shifts per thread block; 0 = default */
   int max_refine;          /* SSV_MIXED: maximum refinement sweeps */
   double tol;              /* SSV_MIXED: target normwise backward error */
   int panel;               /* SSV_PANEL_HOUSEHOLDER or SSV_PANEL_GIVENS (ssv_solve, FP64) */
@@ -118,7 +117,7 @@ typedef struct ssv_opts {
 
 typedef struct ssv_handle_s* ssv_handle;
 
-/* Fill *o with the defaults: FP64, SSV_G, nb = 0, tile = 0, max_refine = 8,
+/* Fill *o with the defaults: FP64, SSV_G, nb = 0, max_refine = 8,
  * tol = 1e-13, panel = SSV_PANEL_HOUSEHOLDER, first = SSV_FIRST_TENSOR.  (The mixed path certifies each
  * shift with a residual whose own error, as a backward error, is below 5e-15
  * for m <= 16 (the tensor-core residual) and about 1e-14 for wider m (the

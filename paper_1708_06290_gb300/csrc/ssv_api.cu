@@ -52,7 +52,7 @@ static int check_opts(const ssv_opts* o) {
       o->precision != SSV_SPLIT)
     return SSV_EINVAL;
   if (o->mode < SSV_G || o->mode > SSV_X) return SSV_EINVAL;
-  if (o->nb < 0 || o->tile < 0 || o->max_refine < 0 || !(o->tol >= 0.0)) return SSV_EINVAL;
+  if (o->nb < 0 || o->max_refine < 0 || !(o->tol >= 0.0)) return SSV_EINVAL;
   if (o->panel != SSV_PANEL_HOUSEHOLDER && o->panel != SSV_PANEL_GIVENS) return SSV_EINVAL;
   if (o->first != SSV_FIRST_DFLOAT && o->first != SSV_FIRST_C64 && o->first != SSV_FIRST_TENSOR)
     return SSV_EINVAL;
@@ -92,7 +92,6 @@ void ssv_default_opts(ssv_opts* o) {
   o->precision = SSV_FP64;
   o->mode = SSV_G;
   o->nb = 0;
-  o->tile = 0;
   o->max_refine = 8;
   o->tol = 1e-13;
   o->panel = SSV_PANEL_HOUSEHOLDER;

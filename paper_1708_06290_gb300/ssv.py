@@ -52,7 +52,7 @@ class SsvError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("mode", ctypes.c_int), ("nb", ctypes.c_int),
-                ("tile", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
                 ("panel", ctypes.c_int), ("first", ctypes.c_int)]
 
 
@@ -185,14 +185,13 @@ _PANELS = {"householder": 0, "givens": 1}
 _FIRST = {"dfloat": 0, "c64": 1, "tensor": 2}
 
 
-def opts(precision="fp64", mode="g", nb=0, tile=0, max_refine=8, tol=1e-13, panel="householder",
+def opts(precision="fp64", mode="g", nb=0, max_refine=8, tol=1e-13, panel="householder",
          first="tensor"):
     o = Opts()
     load().ssv_default_opts(ctypes.byref(o))
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
     o.mode = _MODES[mode] if isinstance(mode, str) else int(mode)
     o.nb = nb
-    o.tile = tile
     o.max_refine = max_refine
     o.tol = tol
     o.panel = _PANELS[panel] if isinstance(panel, str) else int(panel)
@@ -253,7 +252,7 @@ class Handle:
     def out_rows(self, mode):
         return self.p if _MODES.get(mode, mode) in (G, TF) else self.n
 
-    def solve(self, shifts, mode="g", precision="fp64", nb=0, tile=0, max_refine=8, tol=1e-13,
+    def solve(self, shifts, mode="g", precision="fp64", nb=0, max_refine=8, tol=1e-13,
               out=None, status=None, resid=None, want_resid=False, stream=None, panel="householder",
               first="tensor"):
         """Solve all shifts.  Returns (out, status, resid).
@@ -264,7 +263,7 @@ class Handle:
         L = load()
         _need_cuda(shifts, torch.complex128, "shifts")
         s = shifts.numel()
-        o = opts(precision, mode, nb, tile, max_refine, tol, panel, first)
+        o = opts(precision, mode, nb, max_refine, tol, panel, first)
         rows = self.out_rows(o.mode)
         dev = shifts.device
         if out is None:
@@ -293,7 +292,7 @@ class Handle:
         s = shifts.numel()
         if tuple(bhat.shape) != (self.m, s):
             raise ValueError("bhat must be (m, s) = (%d, %d)" % (self.m, s))
-        o = opts("fp64", mode, nb, 0, 0, 0.0)
+        o = opts("fp64", mode, nb, 0, 0.0)
         rows = self.out_rows(o.mode)
         dev = shifts.device
         if out is None:
@@ -318,7 +317,7 @@ class Handle:
         s = shifts.numel()
         if tuple(chat.shape) != (self.p, s):
             raise ValueError("chat must be (p, s) = (%d, %d)" % (self.p, s))
-        o = opts("fp64", mode, nb, 0, 0, 0.0)
+        o = opts("fp64", mode, nb, 0, 0.0)
         dev = shifts.device
         if out is None:
             out = torch.empty((s, self.n), dtype=torch.complex128, device=dev).t()

@@ -55,7 +55,7 @@ def test_strerror_and_defaults(lib):
     assert o.precision == ssv.FP64 and o.mode == ssv.G and o.max_refine == 8 and o.tol == 1e-13
     assert o.first == 2   # SSV_FIRST_TENSOR
     # the C struct and the ctypes mirror agree in size (ssv_opts is passed by pointer)
-    assert ctypes.sizeof(ssv.Opts) == 40
+    assert ctypes.sizeof(ssv.Opts) == 32
 
 
 def test_argument_validation_needs_no_gpu(lib):

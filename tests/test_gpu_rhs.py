@@ -115,7 +115,7 @@ def test_mixed_precision_is_refused():
     sysr = W.random_system(20, 2, 1, seed=3)
     h = ssv.reduce(dev(sysr.A), dev(sysr.B), dev(sysr.C))
     L = ssv.load()
-    o = ssv.opts("mixed", "x", 0, 0, 8, 1e-14)
+    o = ssv.opts("mixed", "x", 0, 8, 1e-14)
     sd = shifts_dev([0.5j])
     b = _bhat_dev(np.ones((2, 1), dtype=complex))
     out = torch.empty((1, 20), dtype=torch.complex128, device="cuda").t()
