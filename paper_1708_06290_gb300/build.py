@@ -35,22 +35,34 @@ def _deps():
     return _sources() + glob.glob(os.path.join(SRC_DIR, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+# debug variant: device-side index checks of the tensor-core sweep that record an
+# error word instead of trapping, NaN-poisoned scratch and a canary after it
+CHECK_DIR = os.path.join(PKG, "_build_check")
+CHECK_LIB = os.path.join(CHECK_DIR, "libssv.so")
+CHECK_FLAGS = ["-DSSV_BOUNDS_CHECK"]
+
+
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, extra_flags=(), variant="release"):
+    """Build the library; variant "check" builds the bounds-checked debug copy
+    into _build_check/ (its own file, loaded only when SSV_LIBRARY names it)."""
+    out_dir, lib = (CHECK_DIR, CHECK_LIB) if variant == "check" else (OUT_DIR, LIB)
+    if variant == "check":
+        extra_flags = list(extra_flags) + CHECK_FLAGS
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -64,13 +76,13 @@ def build(force=False, verbose=False, extra_flags=()):
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -53,6 +53,24 @@ namespace {
 
 using namespace tcg;
 
+// Debug builds (-DSSV_BOUNDS_CHECK): every global index of the sweep's kernels
+// is checked against its buffer; an index out of range sets bit 1 of the
+// solve's error word (every shift of the solve then reports a non-finite
+// result) and is replaced by 0, so the access stays inside the buffer.  In
+// normal builds BCK(i, n) is i.
+#ifdef SSV_BOUNDS_CHECK
+__device__ __forceinline__ size_t bck(long long i, size_t n, int* err) {
+  if (i < 0 || (size_t)i >= n) {
+    atomicOr(err, 2);
+    return 0;
+  }
+  return (size_t)i;
+}
+#define BCK(i, n) bck((long long)(i), (size_t)(n), a.err)
+#else
+#define BCK(i, n) ((size_t)(i))
+#endif
+
 constexpr int kPT = 256;             // threads of the setup, panel and final kernels
 constexpr int kNBT = 128;            // n_b of the tensor-core sweep (K of the update)
 constexpr int kMaxM = kTcMaxM;       // m <= 16
@@ -147,6 +165,8 @@ struct TcsArgs {
   int* zexp;             // [shift][npad] row exponents
   uint16_t* P2d;         // [shift][digit][cs x cs]
   int* p2exp;            // [shift][2 kMaxM] column exponents
+  // buffer sizes (elements) for the debug build's index checks
+  size_t n_z2, n_zt, n_pd, n_zd, n_p2d, n_pc, n_hs, n_out;
 };
 
 // digit tiles of window row p + i (H row i) of shift sh, from the double-float
@@ -156,13 +176,13 @@ __device__ void write_z2_digits(const TcsArgs& a, int sh, int i, const float4* Z
   const int m = a.m, cs = a.cs, kg = cs / 8;
   float mx = 0.f;
   for (int q = 0; q < m; ++q) {
-    const float4 z = Z2f[(a.p + i) + (size_t)q * ldz];
+    const float4 z = Z2f[BCK((a.p + i) + (size_t)q * ldz, a.z2_stride)];
     mx = fmaxf(mx, fmaxf(fabsf(z.x), fabsf(z.z)));
     if (!(fabsf(z.x) <= 3.4e38f) || !(fabsf(z.z) <= 3.4e38f)) mx = __int_as_float(0x7f800000);
   }
   const int E = scale_exp_f(mx);
-  a.zexp[(size_t)sh * a.npad + i] = E;
-  uint16_t* T = a.Zd + ((size_t)sh * a.RB + i / 128) * 7 * (128 * cs);
+  a.zexp[BCK((size_t)sh * a.npad + i, (size_t)a.s * a.npad)] = E;
+  const size_t T0 = ((size_t)sh * a.RB + i / 128) * 7 * (128 * cs);
   for (int k8 = 0; k8 < cs; k8 += 8) {
     unsigned short dg[8][7];
 #pragma unroll
@@ -170,7 +190,7 @@ __device__ void write_z2_digits(const TcsArgs& a, int sh, int i, const float4* Z
       const int kk = k8 + e, q = kk >> 1;
       float hi = 0.f, lo = 0.f;
       if (q < m) {
-        const float4 z = Z2f[(a.p + i) + (size_t)q * ldz];
+        const float4 z = Z2f[BCK((a.p + i) + (size_t)q * ldz, a.z2_stride)];
         hi = (kk & 1) ? z.z : z.x;
         lo = (kk & 1) ? z.w : z.y;
       }
@@ -184,7 +204,7 @@ __device__ void write_z2_digits(const TcsArgs& a, int sh, int i, const float4* Z
       u.y = dg[2][l] | ((unsigned)dg[3][l] << 16);
       u.z = dg[4][l] | ((unsigned)dg[5][l] << 16);
       u.w = dg[6][l] | ((unsigned)dg[7][l] << 16);
-      *reinterpret_cast<uint4*>(T + (size_t)l * (128 * cs) + off) = u;
+      *reinterpret_cast<uint4*>(a.Zd + BCK(T0 + (size_t)l * (128 * cs) + off, a.n_zd)) = u;
     }
   }
 }
@@ -205,7 +225,7 @@ __global__ void __launch_bounds__(kPT) tcs_setup_kernel(TcsArgs a) {
     const double v = i < p ? a.Ct[i + (size_t)j * a.ldct] : a.H[(i - p) + (size_t)j * n];
     cd z = mkcd(v, 0.0);
     if (i - p == j) z = csub(z, sigma);
-    Z2[idx] = df_split(z);
+    Z2[BCK(idx, a.z2_stride)] = df_split(z);
   }
   if (threadIdx.x == 0) a.flags[sh] = 0;
   if (a.tcz) {
@@ -252,7 +272,7 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
   if (tid == 0) sm.sing = 0;
   for (int idx = tid; idx < m * nbe; idx += kPT) {
     const int t = idx % nbe, q = idx / nbe;
-    cand4[q * kNBT + t] = Z2f[(r + t) + (size_t)q * ldz];
+    cand4[q * kNBT + t] = Z2f[BCK((r + t) + (size_t)q * ldz, a.z2_stride)];
   }
   for (int idx = tid; idx < kCoefRows * S; idx += kPT) {
     const int c = idx / S, slot = idx % S;
@@ -383,14 +403,14 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
     if (lane == 0) {
       const int E = bad ? kBadExp : scale_exp(mx);
       sm.fexp[cr] = E;
-      a.pexp[(size_t)sh * 2 * kMaxM + cr] = E;
+      a.pexp[BCK((size_t)sh * 2 * kMaxM + cr, (size_t)a.s * 2 * kMaxM)] = E;
     }
   }
   __syncthreads();
   {
     // item = (real column cr, 8 consecutive K rows): seven uint4 stores
     const int g = sh / a.S, slot_row = (sh % a.S) * a.cs;
-    uint16_t* Pg = a.Pd + (size_t)g * kSD * kStages * kBT;
+    const size_t Pg0 = (size_t)g * kSD * kStages * kBT;
     for (int it = tid; it < 2 * m * (kNBT / 8); it += kPT) {
       const int cr = it / (kNBT / 8), c8 = (it % (kNBT / 8)) * 8;
       const int q = cr >> 1, E = sm.fexp[cr];
@@ -414,7 +434,7 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
         u.y = dg[2][l] | ((unsigned)dg[3][l] << 16);
         u.z = dg[4][l] | ((unsigned)dg[5][l] << 16);
         u.w = dg[6][l] | ((unsigned)dg[7][l] << 16);
-        *reinterpret_cast<uint4*>(Pg + ((size_t)l * kStages + J) * kBT + off) = u;
+        *reinterpret_cast<uint4*>(a.Pd + BCK(Pg0 + ((size_t)l * kStages + J) * kBT + off, a.n_pd)) = u;
       }
     }
   }
@@ -447,10 +467,10 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
       }
       const int E = scale_exp_f(mx);
       sm.f2exp[c] = E;
-      a.p2exp[(size_t)sh * 2 * kMaxM + c] = E;
+      a.p2exp[BCK((size_t)sh * 2 * kMaxM + c, (size_t)a.s * 2 * kMaxM)] = E;
     }
     __syncthreads();
-    uint16_t* T = a.P2d + (size_t)sh * 7 * cs * cs;
+    const size_t T0 = (size_t)sh * 7 * cs * cs;
     for (int it = tid; it < cs * (cs / 8); it += kPT) {
       const int c = it / (cs / 8), k8 = (it % (cs / 8)) * 8;
       const int q = c >> 1, ro = c & 1, E = sm.f2exp[c];
@@ -475,7 +495,7 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
         u.y = dg[2][l] | ((unsigned)dg[3][l] << 16);
         u.z = dg[4][l] | ((unsigned)dg[5][l] << 16);
         u.w = dg[6][l] | ((unsigned)dg[7][l] << 16);
-        *reinterpret_cast<uint4*>(T + (size_t)l * cs * cs + off) = u;
+        *reinterpret_cast<uint4*>(a.P2d + BCK(T0 + (size_t)l * cs * cs + off, a.n_p2d)) = u;
       }
     }
   }
@@ -486,12 +506,12 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
     cd* ZT = a.ZT + (size_t)sh * (size_t)n * m;
     for (int idx = tid; idx < nbe * m; idx += kPT) {
       const int c = idx % nbe, q = idx / nbe;
-      ZT[(j0 + c) + (size_t)q * n] = df_join(coef4[c * S + q]);
+      ZT[BCK((j0 + c) + (size_t)q * n, (size_t)n * m)] = df_join(coef4[c * S + q]);
     }
     cd* tout = a.out + (size_t)sh * m * a.ldo;
     for (int idx = tid; idx < m * m; idx += kPT) {
       const int qq = idx % m, q = idx / m;
-      tout[(n - step * m + qq) + (size_t)q * a.ldo] = df_join(coef4[(kNBT + qq) * S + q]);
+      tout[BCK(n - step * m + qq, n) + (size_t)q * a.ldo] = df_join(coef4[(kNBT + qq) * S + q]);
     }
   }
   // ---- the p rows of Ct: Z2(i, :) = Ct(i, fresh) P1 + Z2(i, :) P2, double-float,
@@ -512,7 +532,7 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
       df_mac(ih, il, zh, zl, w.z, w.w);
     }
     for (int qq = 0; qq < m; ++qq) {
-      const float4 zz = Z2f[i + (size_t)qq * ldz];
+      const float4 zz = Z2f[BCK(i + (size_t)qq * ldz, a.z2_stride)];
       const float4 w = coef4[(kNBT + qq) * S + q];
       df_mac(rh, rl, zz.x, zz.y, w.x, w.y);
       df_mac(rh, rl, -zz.z, -zz.w, w.z, w.w);
@@ -526,7 +546,7 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
   nitem = 0;
   for (int e = tid; e < ic * m && nitem < 2; e += kPT, ++nitem) {
     const int i = i0 + e / m, q = e % m;
-    Z2f[i + (size_t)q * ldz] = nv[nitem];
+    Z2f[BCK(i + (size_t)q * ldz, a.z2_stride)] = nv[nitem];
   }
   __syncthreads();
   }
@@ -630,11 +650,12 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
                  : "memory");
     for (int l = 0; l < kSDH; ++l)
       bulk_copy(dst + (uint32_t)(l * kAT * 2),
-                a.Hs + ((size_t)(l * a.RB + I) * a.KT + (JH0 + st)) * (kAT / 8), (uint32_t)(kAT * 2), lmb);
-    const uint16_t* Pg = a.Pd + (size_t)g * kSD * kStages * kBT;
+                a.Hs + BCK(((size_t)(l * a.RB + I) * a.KT + (JH0 + st)) * (kAT / 8), a.n_hs),
+                (uint32_t)(kAT * 2), lmb);
+    const size_t Pg0 = (size_t)g * kSD * kStages * kBT;
     for (int l = 0; l < kSD; ++l)
-      bulk_copy(dst + (uint32_t)(kSDH * kAT * 2 + l * kBT * 2), Pg + ((size_t)l * kStages + st) * kBT,
-                (uint32_t)(kBT * 2), lmb);
+      bulk_copy(dst + (uint32_t)(kSDH * kAT * 2 + l * kBT * 2),
+                a.Pd + BCK(Pg0 + ((size_t)l * kStages + st) * kBT, a.n_pd), (uint32_t)(kBT * 2), lmb);
   };
   // the group's Z2 digit tiles of row tile I, then its P2 digit tiles
   auto z2_in = [&](int I, int g, int nsh) {
@@ -643,9 +664,10 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
                  : "memory");
     for (int l = 0; l < nsh; ++l) {
       const int sh = g * S + l;
-      bulk_copy(sBase + (uint32_t)l * zbytes, a.Zd + ((size_t)sh * a.RB + I) * 7 * (128 * cs), zbytes, lmb2);
-      bulk_copy(sBase + (uint32_t)S * zbytes + (uint32_t)l * pbytes, a.P2d + (size_t)sh * 7 * cs * cs,
-                pbytes, lmb2);
+      bulk_copy(sBase + (uint32_t)l * zbytes, a.Zd + BCK(((size_t)sh * a.RB + I) * 7 * (128 * cs), a.n_zd),
+                zbytes, lmb2);
+      bulk_copy(sBase + (uint32_t)S * zbytes + (uint32_t)l * pbytes,
+                a.P2d + BCK((size_t)sh * 7 * cs * cs, a.n_p2d), pbytes, lmb2);
     }
   };
 
@@ -662,7 +684,7 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
     for (int e = tid; e < S * 2 * m * m; e += kUT) {
       const int l = e / (2 * m * m), o = e % (2 * m * m);
       const int sh = g * S + l;
-      pcs[e] = sh < a.s ? a.pc[(size_t)sh * 2 * kMaxM * kMaxM + o] : make_float4(0.f, 0.f, 0.f, 0.f);
+      pcs[e] = sh < a.s ? a.pc[BCK((size_t)sh * 2 * kMaxM * kMaxM + o, a.n_pc)] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int e = tid; e < S * cs; e += kUT) {
       const int l = e / cs, c = e % cs;
@@ -731,7 +753,7 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
     const int row = tid & (kUM - 1), qt = tid >> 7;
     const int ih = I * kUM + row;
     const bool live = ih < hrows;
-    const int Ei = live ? a.hexp[ih] : 0;
+    const int Ei = live ? a.hexp[BCK(ih, a.npad)] : 0;
     const int cdr = ih - j0;  // shifted-diagonal correction row of fresh column cdr
     const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(qt * 16);
     float4 acc[8];
@@ -816,7 +838,7 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
       drain_levels(tl, 7, ah, al);
       const int l = (qt * 16) / cs;  // one shift per quarter (cs >= 16)
       const int sh = g * S + l;
-      const int Ez = (live && sh < a.s) ? a.zexp[(size_t)sh * a.npad + ih] : 0;
+      const int Ez = (live && sh < a.s) ? a.zexp[BCK((size_t)sh * a.npad + ih, (size_t)a.s * a.npad)] : 0;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         if (!ok_j[j]) continue;
@@ -848,7 +870,7 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
           if (!ok_j[j]) continue;
           const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
           if (l != lz) {
-            zz = a.Z2[(size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)qq * ldz];
+            zz = a.Z2[BCK((size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)qq * ldz, a.n_z2)];
             lz = l;
           }
           const float4 w = pcs[(size_t)l * 2 * m * m + qq * m + q];
@@ -898,7 +920,7 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
     for (int j = 0; j < 8; ++j) {
       if (!ok_j[j]) continue;
       const int col = qt * 16 + 2 * j, l = col / cs, q = (col % cs) >> 1;
-      a.Z2[(size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)q * ldz] = acc[j];
+      a.Z2[BCK((size_t)(g * S + l) * a.z2_stride + (p + ih) + (size_t)q * ldz, a.n_z2)] = acc[j];
     }
     if (TCZ && live) {
       const int l = (qt * 16) / cs, sh = g * S + l;
@@ -906,8 +928,8 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
         if (cs == 32) mx = fmaxf(mx, xmax[(qt ^ 1) * kUM + row]);
         const int E = scale_exp_f(mx);
         const int kb = (qt * 16) % cs;  // this quarter's first K entry of the row
-        if ((qt * 16) % cs == 0) a.zexp[(size_t)sh * a.npad + ih] = E;
-        uint16_t* T = a.Zd + ((size_t)sh * a.RB + I) * 7 * (128 * cs);
+        if ((qt * 16) % cs == 0) a.zexp[BCK((size_t)sh * a.npad + ih, (size_t)a.s * a.npad)] = E;
+        const size_t T0 = ((size_t)sh * a.RB + I) * 7 * (128 * cs);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           unsigned short dg[8][7];
@@ -927,7 +949,7 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
             u.y = dg[2][l2] | ((unsigned)dg[3][l2] << 16);
             u.z = dg[4][l2] | ((unsigned)dg[5][l2] << 16);
             u.w = dg[6][l2] | ((unsigned)dg[7][l2] << 16);
-            *reinterpret_cast<uint4*>(T + (size_t)l2 * (128 * cs) + off) = u;
+            *reinterpret_cast<uint4*>(a.Zd + BCK(T0 + (size_t)l2 * (128 * cs) + off, a.n_zd)) = u;
           }
         }
       }
@@ -954,6 +976,14 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+#ifdef SSV_BOUNDS_CHECK
+// bit 2 of the error word when a byte of the canary after the scratch changed
+__global__ void tcs_canary_kernel(const unsigned char* c, size_t nbytes, int* err) {
+  for (size_t i = threadIdx.x; i < nbytes; i += blockDim.x)
+    if (c[i] != 0xA5) atomicOr(err, 4);
+}
+#endif
+
 // ---- final m x m block, G or the X-hat back pass ----------------------------
 __global__ void __launch_bounds__(kPT) tcs_final_kernel(TcsArgs a, int nsteps, int nbe_first) {
   __shared__ cd Wm[kMaxM * 2 * kMaxM];
@@ -971,7 +1001,7 @@ __global__ void __launch_bounds__(kPT) tcs_final_kernel(TcsArgs a, int nsteps, i
   for (int idx = tid; idx < m * 2 * m; idx += kPT) {
     const int i = idx % m, j = idx / m;
     cd v;
-    if (j < m) v = df_join(Z2f[(p + i) + (size_t)j * ldz]);
+    if (j < m) v = df_join(Z2f[BCK((p + i) + (size_t)j * ldz, a.z2_stride)]);
     else v = mkcd(i <= j - m ? a.R[i + (size_t)(j - m) * n] : 0.0, 0.0);
     Wm[i + j * kMaxM] = v;
   }
@@ -1031,9 +1061,10 @@ __global__ void __launch_bounds__(kPT) tcs_final_kernel(TcsArgs a, int nsteps, i
     for (int idx = tid; idx < p * m; idx += kPT) {
       const int i = idx % p, q = idx / p;
       cd acc = mkcd(0.0, 0.0);
-      for (int t = 0; t < m; ++t) acc = cfma(df_join(Z2f[i + (size_t)t * ldz]), Yb[t + q * kMaxM], acc);
+      for (int t = 0; t < m; ++t)
+        acc = cfma(df_join(Z2f[BCK(i + (size_t)t * ldz, a.z2_stride)]), Yb[t + q * kMaxM], acc);
       if (bad) acc = mkcd(nanv, nanv);
-      tout[i + (size_t)q * a.ldo] = mkcd(sgn * acc.x, sgn * acc.y);
+      tout[BCK(i, p) + (size_t)q * a.ldo] = mkcd(sgn * acc.x, sgn * acc.y);
     }
   } else {
     // backward pass: z = Y; per step b = B .. 1: X-hat rows of b = P1_b z,
@@ -1046,13 +1077,13 @@ __global__ void __launch_bounds__(kPT) tcs_final_kernel(TcsArgs a, int nsteps, i
       const int nbe_b = b == 1 ? nbe_first : kNBT;
       const int j0b = (nsteps - b) * kNBT;
       for (int e = tid; e < m * m; e += kPT)
-        p2s[(e % m) + (e / m) * kMaxM] = tout[(n - b * m + e % m) + (size_t)(e / m) * a.ldo];
+        p2s[(e % m) + (e / m) * kMaxM] = tout[BCK(n - b * m + e % m, n) + (size_t)(e / m) * a.ldo];
       __syncthreads();
       for (int idx = tid; idx < nbe_b * m; idx += kPT) {
         const int i = j0b + idx % nbe_b, q = idx / nbe_b;
         cd acc = mkcd(0.0, 0.0);
-        for (int t = 0; t < m; ++t) acc = cfma(ZT[i + (size_t)t * n], zs[t + q * kMaxM], acc);
-        tout[i + (size_t)q * a.ldo] = bad ? mkcd(nanv, nanv) : acc;
+        for (int t = 0; t < m; ++t) acc = cfma(ZT[BCK(i + (size_t)t * n, (size_t)n * m)], zs[t + q * kMaxM], acc);
+        tout[BCK(i, n) + (size_t)q * a.ldo] = bad ? mkcd(nanv, nanv) : acc;
       }
       for (int e = tid; e < m * m; e += kPT) {
         const int rr = e % m, q = e / m;
@@ -1123,9 +1154,14 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
   const size_t bZe = tcz ? al(sizeof(int) * (size_t)s * np) : 0;
   const size_t bPd2 = tcz ? al((size_t)s * 7 * cs * cs * 2) : 0;
   const size_t bPe2 = tcz ? al(sizeof(int) * (size_t)s * 2 * kMaxM) : 0;
+  const size_t total = bZ + bT + bP + bE + bC + bF + bZd + bZe + bPd2 + bPe2 + bH;
+#ifdef SSV_BOUNDS_CHECK
+  constexpr size_t kCanary = 256;  // checked after the last block step
+#else
+  constexpr size_t kCanary = 0;
+#endif
   unsigned char* buf = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&buf,
-                               bZ + bT + bP + bE + bC + bF + bZd + bZe + bPd2 + bPe2 + bH, st));
+  SSV_CUDA_TRY(cudaMallocAsync((void**)&buf, total + kCanary, st));
   unsigned char* o = buf;
   TcsArgs a;
   a.n = n; a.m = m; a.p = p; a.s = s; a.cs = cs; a.S = S; a.ngroups = G; a.mode = mode;
@@ -1148,8 +1184,23 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
   a.out = reinterpret_cast<cd*>(out); a.ldo = ldo; a.status = status;
   a.RB = np / kUM;
   a.KT = np / kKS;
+  a.n_z2 = (size_t)s * a.z2_stride;
+  a.n_zt = bT ? (size_t)s * n * m : 0;
+  a.n_pd = (size_t)G * kSD * kStages * kBT;
+  a.n_zd = tcz ? (size_t)s * np * 7 * cs : 0;
+  a.n_p2d = tcz ? (size_t)s * 7 * cs * cs : 0;
+  a.n_pc = (size_t)s * 2 * kMaxM * kMaxM;
+  a.n_hs = (size_t)np * np;  // uint4 of the eight H digit slices
+  a.n_out = 0;
   int rc = SSV_OK;
-  cudaError_t e = cudaMemsetAsync(a.Pd, 0, bP, st);
+  cudaError_t e = cudaSuccess;
+#ifdef SSV_BOUNDS_CHECK
+  // scratch read before it is written shows up as NaN (0xFF bytes), and the
+  // canary after the scratch as a changed byte
+  e = cudaMemsetAsync(buf, 0xFF, total, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf + total, 0xA5, kCanary, st);
+#endif
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.Pd, 0, bP, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, sizeof(int), st);
   if (e == cudaSuccess && hdig == nullptr) {
     rc = resid_tc_split_h(h, o, st);
@@ -1192,6 +1243,10 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
         }
         k -= nbe;
       }
+#ifdef SSV_BOUNDS_CHECK
+      tcs_canary_kernel<<<1, 256, 0, st>>>(buf + total, kCanary, a.err);
+      count_launch();
+#endif
       tcs_final_kernel<<<s, kPT, 0, st>>>(a, step, nbe_first);
       count_launch();
       e = cudaGetLastError();

@@ -76,8 +76,10 @@ def load(build_if_missing=True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if build_if_missing and not _build.up_to_date():
+    # SSV_LIBRARY may name another build of the same library (the bounds-checked
+    # debug copy); it is used as is, never built here
+    path = os.environ.get("SSV_LIBRARY") or _build.LIB
+    if path == _build.LIB and build_if_missing and not _build.up_to_date():
         _build.build()
     if not os.path.exists(path):
         raise RuntimeError("libssv.so is not built (%s); run paper_1708_06290_gb300/build.py" % path)
