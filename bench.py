@@ -31,6 +31,8 @@ if ROOT not in sys.path:
 import workloads as W  # noqa: E402
 
 METRIC = "shift-solves/s at n=5000,m=16 (mixed vs FP64, resid<=1e-12); p50/p99 latency"
+# DRAM bytes of one reduce_blocked_kernel launch at n = 5000, m = p = 16 (ncu), or None
+REDUCE_TRAFFIC_N5000_M16 = 130381078528 + 90573036032
 UNIT = "shift-solves/s"
 
 
@@ -59,7 +61,8 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
     ap.add_argument("--profile-reduce", type=int, default=0,
-                    help="profiling case: one reduction of an n x n system (m = p = 8)")
+                    help="profiling case: one reduction of an n x n system (m = p = --profile-m)")
+    ap.add_argument("--profile-m", type=int, default=16)
     ap.add_argument("--profile-resid", action="store_true",
                     help="one tensor-core backward-error pass of the workload (for ncu)")
     ap.add_argument("--profile-solve", action="store_true",
@@ -430,14 +433,14 @@ def profile_reduce(args):
     from paper_1708_06290_gb300 import ssv
 
     n = args.profile_reduce
-    sysr = W.random_system(n, 8, 8, seed=77)
+    sysr = W.random_system(n, args.profile_m, args.profile_m, seed=77)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).t().contiguous().t().cuda()  # noqa
     A, B, C = dev(sysr.A), dev(sysr.B), dev(sysr.C)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = ssv.reduce(A, B, C)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": "reduce", "n": n, "m": 8, "s": time.perf_counter() - t0}))
+    print(json.dumps({"profile": "reduce", "n": n, "m": args.profile_m, "s": time.perf_counter() - t0}))
     h.close()
     return 0
 
@@ -609,23 +612,42 @@ def main():
         "traffic": (3.002227e9 + 3.462814e9) * s / 152.0 if args.nb in (0, 128) else None,
     }
     sweep0_ms = res["mixed"]["phase_ms_per_step"].get("mixed_sweep0", float("nan"))
-    # each double-float multiply-add (df_mac) issues 12 FP32-pipe instructions; the FFMA
-    # probe's TFLOP/s / 2 is the pipe's instruction rate
+    # the double-float equivalent of the first solve: each double-float multiply-add issues
+    # 12 FP32-pipe instructions; the FFMA probe's TFLOP/s / 2 is the pipe's instruction rate
     instr = 12.0 * floor_macs * s
     ach_ti = instr / (sweep0_ms * 1e-3) / 1e12
     peak_ti = fp32_peak / 2.0
-    roof_mixed = {
-        "kernel": "solve_fp64_kernel<16, double-float> (first solve of the mixed path)",
-        "bound": "alu", "unit": "T FP32-instr/s", "achieved": ach_ti, "peak": peak_ti,
-        "frac": ach_ti / peak_ti,
+    roof_first = {
+        "kernel": "tcs_panel_kernel + tcs_update_kernel<true> (tensor-core sweep, first solve of "
+                  "the mixed path; %d launches each)" % (len(range(0, n - m, 128)) or 1),
+        "bound": "alu", "unit": "T FP32-instr/s (double-float equivalent)", "achieved": ach_ti,
+        "peak": peak_ti, "frac": ach_ti / peak_ti,
         "peak_source": "FFMA probe measured in this run / 2 (instructions/s; nominal 128 lanes x "
                        "152 SMs x 2.07 GHz = 40.3 T/s)",
         "launch_ms": sweep0_ms,
-        "definition": "n_b-independent floor n^2 m + 2 n m p real multiply-adds per shift, each "
-                      "12 FP32-pipe instructions in double-float",
+        "definition": "n_b-independent floor n^2 m + 2 n m p real multiply-adds per shift counted "
+                      "at the 12 FP32 instructions a double-float multiply-add takes; the sweep "
+                      "runs the Z1 P1 and Z2 P2 products as exact BF16 digit products on the "
+                      "tensor cores instead, so this is the rate a double-float sweep would need",
         "traffic": None,
     }
-    roofline = roof_mixed if headp == "mixed" else roof_fp64
+    # the largest single kernel of the mixed step: the FP64 reduction
+    red_ms = res["mixed"]["phase_ms_per_step"].get("reduce", float("nan"))
+    red_flops = 10.0 / 3.0 * n ** 3 - 4.5 * n * n * m
+    red_ach = red_flops / (red_ms * 1e-3) / 1e12
+    roof_reduce = {
+        "kernel": "reduce_blocked_kernel (FP64 controller-Hessenberg reduction, one launch)",
+        "bound": "alu", "unit": "TFLOP/s", "achieved": red_ach, "peak": fp64_peak,
+        "frac": red_ach / fp64_peak,
+        "peak_source": "FP64 DFMA probe measured in this run (nominal GB300 FP64 1.25 TFLOP/s)",
+        "launch_ms": red_ms,
+        "flops_definition": "10/3 n^3 - 9/2 n^2 m (the blocking-independent terms of the "
+                            "paper's reduction count)",
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one reduction launch at
+        # n = 5000, m = p = 16 (profiles/reduce_blocked_kernel_n5000_m16.md)
+        "traffic": REDUCE_TRAFFIC_N5000_M16 if (n, m, p) == (5000, 16, 16) else None,
+    }
+    roofline = roof_reduce if headp == "mixed" else roof_fp64
     mx = res["mixed"]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -643,6 +665,7 @@ def main():
         "mixed_fp64_resolves_per_step": mx["fp64_resolves_per_step"],
         "fp64_max_backward_error": res["fp64"]["max_backward_error"],
         "roofline": roofline,
+        "roofline_first_solve": roof_first,
         "roofline_fp64_sweep": roof_fp64,
         "phase_ms": {k: res[k]["phase_ms_per_step"] for k in ("mixed", "fp64", "dfloat")},
         "clocks": clocks,
