@@ -384,6 +384,15 @@ void ssv_destroy(ssv_handle h);
 /* Static string naming a return code. */
 const char* ssv_strerror(int code);
 
+/* Scratch memory.  Every call that allocates scratch (all but
+ * ssv_solve_noalloc) takes it stream-ordered from a memory pool the library
+ * keeps per device; freed scratch stays mapped in the pool for the next call
+ * (so repeated solves do not map their scratch anew after each
+ * synchronisation), up to the largest amount used at once.  ssv_pool_trim
+ * returns the current device's pool memory beyond keep_bytes to the system
+ * (memory of calls still in flight is kept).  Errors: SSV_ECUDA. */
+int ssv_pool_trim(size_t keep_bytes);
+
 /* The last CUDA error code seen by this thread's calls (0 if none). */
 int ssv_last_cuda_error(void);
 

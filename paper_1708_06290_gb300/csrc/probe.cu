@@ -27,7 +27,7 @@ template <typename T>
 int run(int iters, cudaStream_t st, double* tflops) {
   const int blocks = num_sms() * 8, threads = 256;
   T* buf = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&buf, sizeof(T) * blocks * threads, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&buf, sizeof(T) * blocks * threads, st));
   cudaEvent_t e0, e1;
   SSV_CUDA_TRY(cudaEventCreate(&e0));
   SSV_CUDA_TRY(cudaEventCreate(&e1));

@@ -631,7 +631,7 @@ int reduce_persistent(Handle* h, cudaStream_t st) {
                       (size_t)np * kW;
   const size_t bytes = sizeof(double) * ndbl + 4 * sizeof(unsigned) + 16;
   unsigned char* wsp = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&wsp, bytes, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&wsp, bytes, st));
   RedArgs a;
   a.H = h->H; a.R = h->R; a.Ct = h->Ct; a.tauA = h->tauA; a.tauB = h->tauB;
   a.n = n; a.m = m; a.p = p; a.ldct = p > 0 ? p : 1; a.kb = kb; a.ka = h->ka;
@@ -680,7 +680,7 @@ int reduce_persistent(Handle* h, cudaStream_t st) {
 
 int barrier_selftest(long long limit, cudaStream_t st) {
   unsigned char* wsp = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&wsp, 16, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&wsp, 16, st));
   unsigned* bar = reinterpret_cast<unsigned*>(wsp);
   int* err = reinterpret_cast<int*>(bar + 2);
   int herr = 0;

@@ -110,7 +110,7 @@ int backward_error_fp64_masked(const Handle* h, int s, const double* shifts, con
                                long long ldx, double* resid, const int* mask, cudaStream_t st) {
   if (s == 0) return SSV_OK;
   double* acc = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&acc, sizeof(double) * 2 * s, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&acc, sizeof(double) * 2 * s, st));
   int rc = SSV_OK;
   cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 2 * s, st);
   if (e != cudaSuccess) { set_cuda_error(e); rc = SSV_ECUDA; }

@@ -580,7 +580,7 @@ int backward_error_tc(const Handle* h, int s, const double* shifts, const double
   const size_t lb = ((size_t)s * sizeof(int) + 255) / 256 * 256;
   const size_t ab = ((size_t)2 * s * sizeof(double) + 255) / 256 * 256;
   unsigned char* buf = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&buf, hb + xb + lb + ab + 256, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&buf, hb + xb + lb + ab + 256, st));
   int* list = reinterpret_cast<int*>(buf + hb + xb);
   double* acc = reinterpret_cast<double*>(buf + hb + xb + lb);
   int* misc = reinterpret_cast<int*>(buf + hb + xb + lb + ab);  // count, err

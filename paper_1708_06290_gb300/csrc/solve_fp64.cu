@@ -1084,7 +1084,7 @@ int launch_solve(const Handle* h, int s, const double* shifts, int nb, int mode,
   per_sm = std::max(1, std::min(per_sm, 2));
   int grid = std::min(s, num_sms() * per_sm);
   cd* scratch = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(cd) * slot * grid, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&scratch, sizeof(cd) * slot * grid, st));
   kern<<<grid, kThreads, L::bytes, st>>>(n, m, p, nb, h->H, h->Ct, p > 0 ? p : 1, h->R, s,
                                          reinterpret_cast<const cd*>(shifts), mode, scratch, slot,
                                          reinterpret_cast<cd*>(out), ldo, status, xhat_copy, ldxc,
@@ -1151,7 +1151,7 @@ int solve_fp64_masked(const Handle* h, int s, const double* shifts, int mode, in
   if (nb > kNB) return SSV_ENOTSUP;
   if (s == 0) return SSV_OK;
   int* list = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&list, sizeof(int) * ((size_t)s + 1), st));
+  SSV_CUDA_TRY(pool_alloc((void**)&list, sizeof(int) * ((size_t)s + 1), st));
   int* count = list + s;
   mask_to_list_kernel<<<1, 1024, 0, st>>>(s, mask, list, count);
   count_launch();
@@ -1189,7 +1189,7 @@ int solve_fp64(const Handle* h, int s, const double* shifts, const ssv_opts* o, 
   long long ldxc = 0;
   if (resid != nullptr && (o->mode == SSV_G || o->mode == SSV_TF)) {
     ldxc = h->n;
-    SSV_CUDA_TRY(cudaMallocAsync((void**)&xcopy, sizeof(cd) * (size_t)h->n * m * s, st));
+    SSV_CUDA_TRY(pool_alloc((void**)&xcopy, sizeof(cd) * (size_t)h->n * m * s, st));
   }
   int rc;
   if (o->precision == SSV_DFLOAT) {
@@ -1256,7 +1256,7 @@ int launch_rhs(const FpSys& d, int s, cudaStream_t st) {
   per_sm = std::max(1, std::min(per_sm, 2));
   const int grid = std::min(s, num_sms() * per_sm);
   cd* scratch = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(cd) * slot * grid, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&scratch, sizeof(cd) * slot * grid, st));
   kern<<<grid, kThreads, L::bytes, st>>>(d, s, scratch, slot);
   count_launch();
   cudaError_t e = cudaGetLastError();
@@ -1284,8 +1284,8 @@ int solve_fp64_trans(const Handle* h, int s, const double* shifts, const double*
   if (s == 0) return SSV_OK;
   double* Ht = nullptr;
   cd* dvec = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&Ht, sizeof(double) * (size_t)n * n, st));
-  cudaError_t e = cudaMallocAsync((void**)&dvec, sizeof(cd) * (size_t)n * s, st);
+  SSV_CUDA_TRY(pool_alloc((void**)&Ht, sizeof(double) * (size_t)n * n, st));
+  cudaError_t e = pool_alloc((void**)&dvec, sizeof(cd) * (size_t)n * s, st);
   int rc = SSV_OK;
   if (e == cudaSuccess) {
     const dim3 tg((n + 31) / 32, (n + 31) / 32);
@@ -1420,7 +1420,7 @@ int launch_givens(const FpSys& d, int s, cudaStream_t st) {
   per_sm = std::max(1, std::min(per_sm, 2));
   const int grid = std::min(s, num_sms() * per_sm);
   cd* scratch = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(cd) * slot * grid, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&scratch, sizeof(cd) * slot * grid, st));
   kern<<<grid, kThreads, GL::bytes, st>>>(d, s, scratch, slot);
   count_launch();
   cudaError_t e = cudaGetLastError();
@@ -1460,7 +1460,7 @@ int solve_fp64_givens(const Handle* h, int s, const double* shifts, const ssv_op
   if (rc != SSV_OK) return rc;
   cd* xcopy = nullptr;
   if (resid != nullptr && (mode == SSV_G || mode == SSV_TF)) {
-    SSV_CUDA_TRY(cudaMallocAsync((void**)&xcopy, sizeof(cd) * (size_t)n * m * s, st));
+    SSV_CUDA_TRY(pool_alloc((void**)&xcopy, sizeof(cd) * (size_t)n * m * s, st));
     d.xhat_copy = xcopy;
     d.ldxc = n;
   }
@@ -1606,7 +1606,7 @@ namespace ssv {
 
 struct BatchPlan {
   int dev = 0;
-  bool stream_ordered = false;  // buffers from cudaMallocAsync on `stream`
+  bool stream_ordered = false;  // buffers from the library pool, ordered on `stream`
   cudaStream_t stream = nullptr;
   int maxm = 1;
   bool dfloat = false;  // SSV_DFLOAT: double-float bulk updates
@@ -1704,11 +1704,11 @@ int batch_create(int nsys, const Handle* const* hs, const int* s, const double* 
       // stream-ordered: no device-wide synchronisation, so concurrent batches on
       // other streams keep running; pageable sources are consumed before return
       cudaStream_t st = bp->stream;
-      e = cudaMallocAsync((void**)&bp->systems, sizeof(FpSys) * nsys, st);
+      e = pool_alloc((void**)&bp->systems, sizeof(FpSys) * nsys, st);
       if (e == cudaSuccess)
-        e = cudaMallocAsync((void**)&bp->items, sizeof(unsigned long long) * items.size(), st);
+        e = pool_alloc((void**)&bp->items, sizeof(unsigned long long) * items.size(), st);
       if (e == cudaSuccess)
-        e = cudaMallocAsync((void**)&bp->scratch, sizeof(cd) * bp->slot * bp->grid, st);
+        e = pool_alloc((void**)&bp->scratch, sizeof(cd) * bp->slot * bp->grid, st);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(bp->systems, sys.data(), sizeof(FpSys) * nsys, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess)

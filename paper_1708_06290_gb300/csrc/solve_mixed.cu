@@ -900,7 +900,7 @@ int run_mixed(const Handle* h, int s, const double* shifts, int nb, int mode, do
   const int grid = std::max(1, std::min(s, num_sms() * per_sm));
   const size_t total = mixed_layout(n, m, s, grid, slot_bytes, nullptr, nullptr);
   unsigned char* base = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&base, total, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&base, total, st));
   *scratch_out = base;
   MixedScratch ms;
   mixed_layout(n, m, s, grid, slot_bytes, &ms, base);
@@ -1042,7 +1042,7 @@ int solve_mixed(const Handle* h, int s, const double* shifts, const ssv_opts* o,
     cd* xcopy = nullptr;
     const bool gm = (mode == SSV_G || mode == SSV_TF);
     if (gm) {
-      cudaError_t e = cudaMallocAsync((void**)&xcopy, sizeof(cd) * (size_t)h->n * m * s, st);
+      cudaError_t e = pool_alloc((void**)&xcopy, sizeof(cd) * (size_t)h->n * m * s, st);
       if (e != cudaSuccess) { set_cuda_error(e); rc = SSV_ENOMEM; }
     }
     if (rc == SSV_OK)

@@ -77,7 +77,16 @@ constexpr int kMaxM = kTcMaxM;       // m <= 16
 constexpr int kSlots = kMaxM + 1;    // m live + the fresh column
 constexpr int kCoefRows = kNBT + kMaxM;
 constexpr int kUM = 128;             // H rows per update item = TMEM lanes
-constexpr int kUN = 64;              // real columns per update item (shift group)
+// real columns per update item (shift group): 64 = one update block per SM with
+// two stage buffers; 32 = two blocks per SM with one stage buffer each, so that
+// one block's epilogue runs under the other's products
+#ifndef SSV_TCS_N
+#define SSV_TCS_N 64
+#endif
+constexpr int kUN = SSV_TCS_N;
+static_assert(kUN == 32 || kUN == 64, "update item width");
+constexpr int kBufU = kUN == 64 ? 2 : 1;   // stage buffers of an update block
+constexpr int kCtasU = kUN == 64 ? 1 : 2;  // update blocks per SM
 constexpr int kKS = 32;              // K per shared-memory stage
 constexpr int kKG = kKS / 8;         // core matrices along K in a tile
 constexpr int kSDH = 8;              // digits of H (all eight slices of its digit tiles)
@@ -89,7 +98,7 @@ constexpr int kBT = kUN * kKS;       // BF16 elements of one P1 digit tile
 constexpr uint32_t kStageBytes = (uint32_t)(kSDH * kAT + kSD * kBT) * 2;
 constexpr int kIss = 4;              // threads issuing products (lane 0 of warps 0..3)
 constexpr uint32_t kIdescU = idesc_bf16(kUM, kUN);
-constexpr int kTmemCols = 512;       // 8 levels x 64 columns
+constexpr int kTmemCols = 8 * kUN;   // 8 levels x kUN columns
 // polls of one mbarrier wait before the update gives up (a stage's copies and
 // products complete within microseconds)
 constexpr long long kUpdWait = 1LL << 22;
@@ -99,8 +108,8 @@ static_assert(kLev * kUN <= kTmemCols, "TMEM columns of the levels");
 // 64 m float4); the column exponents of P1 and of P2's real form (kUN ints
 // each); the row maxima of the quarters (4 x 128 floats); the shifts (at most
 // kUN); kIss + 3 mbarriers; the TMEM address slot
-constexpr size_t kOffPc = 2 * (size_t)kStageBytes;
-constexpr size_t kPcF4 = (size_t)64 * kMaxM;
+constexpr size_t kOffPc = (size_t)kBufU * kStageBytes;
+constexpr size_t kPcF4 = (size_t)kUN * kMaxM;
 constexpr size_t kOffExp = kOffPc + kPcF4 * 16;
 constexpr size_t kOffExp2 = kOffExp + (size_t)kUN * sizeof(int);
 constexpr size_t kOffXmax = kOffExp2 + (size_t)kUN * sizeof(int);
@@ -109,7 +118,10 @@ constexpr size_t kOffBar = kOffSig + (size_t)kUN * 16;
 constexpr size_t kOffSlot = kOffBar + (size_t)(kIss + 3) * 8;
 constexpr size_t kUpdSmem = kOffSlot + 16;
 static_assert(kOffBar % 8 == 0 && kOffSig % 16 == 0, "alignment of the smem carve-up");
-static_assert(kUpdSmem <= 227 * 1024, "shared memory of the update");
+static_assert(kCtasU * (kUpdSmem + 1024) <= 228 * 1024, "shared memory of the update blocks");
+// the Z2 / P2 digit tiles of a group (S shifts, 7 digits, 128 x cs and cs x cs) reuse the stage buffers
+static_assert(7 * (128 * 32 + 32 * 32) * 2 * (kUN / 32) <= kBufU * (size_t)kStageBytes, "Z2 P2 tiles");
+static_assert(7 * (128 * 16 + 16 * 16) * 2 * (kUN / 16) <= kBufU * (size_t)kStageBytes, "Z2 P2 tiles");
 
 // element offset in a K-major core-matrix tile (8 rows x 8 K per 128 bytes;
 // byte strides 128 along K, kKG * 128 along rows): the layout of the residual's
@@ -577,7 +589,7 @@ static __device__ __forceinline__ void drain_levels(uint32_t tl, int nlev, float
   }
 }
 
-constexpr int kUT = 4 * kUM;  // update threads: four per H row of the tile (16 columns each)
+constexpr int kUT = (kUN / 16) * kUM;  // update threads: one per H row of the tile and 16 columns
 
 // The update of block step (k, nbe).  TCZ: Z2 P2 as a second round of digit
 // products on the tensor cores (m >= 5); otherwise in double-float in the
@@ -592,7 +604,7 @@ constexpr int kUT = 4 * kUM;  // update threads: four per H row of the tile (16 
 //      the shifted-diagonal correction, the new Z2 rows in double-float and
 //      (TCZ) as digit tiles for the next block step.
 template <bool TCZ>
-__global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, int nbe) {
+__global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int k, int nbe) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n = a.n, m = a.m, p = a.p, ldz = p + n;
   const int hrows = k - nbe;              // H rows above the block
@@ -695,7 +707,7 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
     for (int l = tid; l < S; l += kUT) sig[l] = (g * S + l < a.s) ? a.shifts[g * S + l] : mkcd(0.0, 0.0);
     // ---- 1. Z1 P1: stage st in buffer st & 1
     for (int st = 0; st < nst; ++st) {
-      const int buf = st & 1;
+      const int buf = kBufU == 2 ? (st & 1) : 0;
       const bool lok = mbar_wait(lmb0 + 8u * (uint32_t)buf, lphase[buf], kUpdWait);
       if (__syncthreads_or(!lok)) {
         failed = true;
@@ -727,8 +739,8 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
         mma_commit(mb + 8u * (uint32_t)iss);
       }
       // the next stage streams into the other buffer, whose products finished
-      // in the previous round
-      if (st + 1 < nst) {
+      // in the previous round (with one buffer: after these products)
+      if (kBufU == 2 && st + 1 < nst) {
         pend[buf ^ 1] = true;
         if (tid == 0) stage_in(I, g, st + 1, buf ^ 1);
       }
@@ -739,6 +751,10 @@ __global__ void __launch_bounds__(kUT, 1) tcs_update_kernel(TcsArgs a, int k, in
         break;
       }
       mphase ^= 1u;
+      if (kBufU == 1 && st + 1 < nst) {
+        pend[0] = true;
+        if (tid == 0) stage_in(I, g, st + 1, 0);
+      }
     }
     if (failed) break;
     // both stage buffers are free: TCZ fetches the group's Z2 / P2 tiles into them
@@ -1161,7 +1177,7 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
   constexpr size_t kCanary = 0;
 #endif
   unsigned char* buf = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&buf, total + kCanary, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&buf, total + kCanary, st));
   unsigned char* o = buf;
   TcsArgs a;
   a.n = n; a.m = m; a.p = p; a.s = s; a.cs = cs; a.S = S; a.ngroups = G; a.mode = mode;
@@ -1236,7 +1252,8 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
         const int hrows = k - nbe;
         if (hrows > 0) {
           const long long items = (long long)((hrows + kUM - 1) / kUM) * G;
-          const int grid = (int)std::max<long long>(1, std::min<long long>(items, num_sms()));
+          const int grid =
+              (int)std::max<long long>(1, std::min<long long>(items, (long long)num_sms() * kCtasU));
           if (tcz) tcs_update_kernel<true><<<grid, kUT, kUpdSmem, st>>>(a, k, nbe);
           else tcs_update_kernel<false><<<grid, kUT, kUpdSmem, st>>>(a, k, nbe);
           count_launch();

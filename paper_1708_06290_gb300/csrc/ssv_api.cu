@@ -1,6 +1,7 @@
 // C ABI entry points (include/ssv.h): argument checks, handle lifetime and
 // dispatch to the FP64 reduction and the solvers.
 #include <atomic>
+#include <mutex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -13,6 +14,50 @@ static thread_local int g_last_cuda = 0;
 static std::atomic<long long> g_launches{0};
 
 void set_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
+
+// One memory pool per device for the library's stream-ordered scratch.  The
+// device's default pool hands freed memory back at every synchronisation, so
+// a solve after a synchronisation maps its (up to tens of GB of) scratch anew;
+// this pool keeps what it has mapped (release threshold: no limit) until
+// ssv_pool_trim.
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+}  // namespace
+
+static cudaError_t device_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool[dev] == nullptr) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    unsigned long long keep = ~0ull;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = device_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 void count_launch(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 int num_sms() {
@@ -70,7 +115,7 @@ int solve_split(const Handle* h, int s, const double* shifts, int mode, double* 
   if (rc != SSV_OK || resid == nullptr) return rc;
   if (mode == SSV_XHAT) return backward_error_fp64(h, s, shifts, out, ldo, resid, st);
   double* xc = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&xc, sizeof(double) * 2 * (size_t)h->n * h->m * s, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&xc, sizeof(double) * 2 * (size_t)h->n * h->m * s, st));
   rc = solve_tc(h, s, shifts, SSV_XHAT, xc, h->n, nullptr, nullptr, st);
   if (rc == SSV_OK) rc = backward_error_fp64(h, s, shifts, xc, h->n, resid, st);
   cudaError_t e = cudaFreeAsync(xc, st);
@@ -497,6 +542,13 @@ const char* ssv_strerror(int code) {
 }
 
 int ssv_last_cuda_error(void) { return g_last_cuda; }
+
+int ssv_pool_trim(size_t keep_bytes) {
+  cudaMemPool_t pool = nullptr;
+  SSV_CUDA_TRY(device_pool(&pool));
+  SSV_CUDA_TRY(cudaMemPoolTrimTo(pool, keep_bytes));
+  return SSV_OK;
+}
 
 int ssv_refine_counts(long long* corrections, long long* resolves, int reset) {
   long long c[2] = {0, 0};

@@ -79,6 +79,10 @@ struct Handle {
 
 // error plumbing (thread-local last CUDA error)
 void set_cuda_error(cudaError_t e);
+// stream-ordered device allocation from the library's memory pool on the
+// current device (freed with cudaFreeAsync); the pool keeps freed blocks for
+// reuse instead of returning them at every synchronisation (ssv_pool_trim)
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
 #define SSV_CUDA_TRY(expr)                         \
   do {                                             \
     cudaError_t _e = (expr);                       \

@@ -121,7 +121,7 @@ int tf_norm2(const Handle* h, int s, const double* shifts, const ssv_opts* o, do
   ssv_opts og = *o;
   og.mode = SSV_G;
   cd* G = nullptr;
-  SSV_CUDA_TRY(cudaMallocAsync((void**)&G, sizeof(cd) * (size_t)p * m * s, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&G, sizeof(cd) * (size_t)p * m * s, st));
   int rc = og.precision == SSV_MIXED
                ? solve_mixed(h, s, shifts, &og, reinterpret_cast<double*>(G), p, status, nullptr, st)
            : og.precision == SSV_SPLIT

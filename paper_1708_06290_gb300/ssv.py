@@ -62,7 +62,7 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
            "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
            "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2",
-           "ssv_backward_error", "ssv_refine_counts")
+           "ssv_backward_error", "ssv_refine_counts", "ssv_pool_trim")
 
 _lib = None
 
@@ -99,6 +99,8 @@ def load(build_if_missing=True):
     L.ssv_tf_norm2.argtypes = [P, I, P, ctypes.POINTER(Opts), P, P, P]
     L.ssv_backward_error.argtypes = [P, I, P, P, LL, I, P, P]
     L.ssv_refine_counts.argtypes = [ctypes.POINTER(LL), ctypes.POINTER(LL), I]
+    L.ssv_pool_trim.argtypes = [ctypes.c_size_t]
+    L.ssv_pool_trim.restype = I
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.ssv_solve_many.argtypes = [I, PP, ctypes.POINTER(I), PP, ctypes.POINTER(Opts), PP,
                                  ctypes.POINTER(LL), PP, P]
@@ -199,6 +201,11 @@ def opts(precision="fp64", mode="g", nb=0, max_refine=8, tol=1e-13, panel="house
     o.panel = _PANELS[panel] if isinstance(panel, str) else int(panel)
     o.first = _FIRST[first] if isinstance(first, str) else int(first)
     return o
+
+
+def pool_trim(keep_bytes=0):
+    """Return the library's pooled scratch memory on the current device beyond keep_bytes."""
+    _check(load().ssv_pool_trim(int(keep_bytes)), "ssv_pool_trim")
 
 
 def refine_counts(reset=False):
