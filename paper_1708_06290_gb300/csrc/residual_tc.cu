@@ -63,10 +63,14 @@ constexpr int kN = 32;        // real columns per shift (2m, zero-padded)
 #ifndef SSV_TC_BUFFERS
 #define SSV_TC_BUFFERS 1      // 2: the next stage streams in during the products
 #endif
+#ifndef SSV_TC_PAIRS
+#define SSV_TC_PAIRS 1        // 1: two shifts per work item (N = 64, one CTA per SM)
+#endif
 #ifndef SSV_TC_BULK
 #define SSV_TC_BULK 1         // one buffer: stage with 1-D TMA bulk copies (else cp.async)
 #endif
 constexpr int kKS = SSV_TC_KS;  // K per shared-memory stage (16 or 32)
+constexpr bool kPairs = SSV_TC_PAIRS != 0;
 constexpr int kSl = 8;        // digit slices of H and of Xhat
 constexpr int kLev = 8;       // levels t = 2 .. 9
 constexpr int kWin = 128 / kKS;  // stages per exact accumulation window (K = 128)
@@ -485,6 +489,236 @@ __global__ void __launch_bounds__(kM, kCtasPerSm) tc_residual_kernel(
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// ---------------------------------------------------------------------------
+// Two shifts per work item: the same digit products with N = 64 (the two
+// shifts' Xhat slice tiles side by side form one 64-row B tile, since a 32-row
+// tile is exactly four core-matrix row groups), so every H tile staged serves
+// two shifts and each product is twice as large.  One CTA per SM (the eight
+// levels x 64 columns fill TMEM), two stage buffers by TMA bulk copies, 256
+// threads: thread (row, half) reads the 32 columns of one shift.
+// ---------------------------------------------------------------------------
+constexpr int kN2 = 64;
+constexpr int kT2 = 2 * kM;
+constexpr uint32_t kIdesc2 = idesc_bf16(kM, kN2);
+constexpr uint32_t kStage2 = (uint32_t)kSl * (kAT + 2 * kBT) * 2;
+constexpr size_t kSmem2 = 2 * (size_t)kStage2 + 128;
+static_assert(kSmem2 <= 227 * 1024, "shared memory of the two-shift residual");
+static_assert(kLev * kN2 <= 512, "TMEM columns of the two-shift residual");
+constexpr int kPairGroup = 8;  // pairs that resident CTAs take together (L2 sharing of H tiles)
+
+__device__ __forceinline__ void pair_coords(long long t, int RB, int np, int* I, int* w) {
+  const long long full = (long long)(np / kPairGroup) * kPairGroup * RB;
+  if (t < full) {
+    const long long g = t / ((long long)kPairGroup * RB), r = t % ((long long)kPairGroup * RB);
+    *I = (int)(r / kPairGroup);
+    *w = (int)(g * kPairGroup + r % kPairGroup);
+  } else {
+    const int gl = np - (np / kPairGroup) * kPairGroup;
+    const long long r = t - full;
+    *I = (int)(r / gl);
+    *w = (np / kPairGroup) * kPairGroup + (int)(r % gl);
+  }
+}
+
+__global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
+    int n, int m, int npad, const uint4* __restrict__ Hs, const int* __restrict__ hexp,
+    const uint4* __restrict__ Xs, const int* __restrict__ xexp, const double* __restrict__ R,
+    const cd* __restrict__ shifts, const int* __restrict__ list, const int* __restrict__ count,
+    const cd* __restrict__ X, long long ldx, float2* __restrict__ E, double* __restrict__ acc,
+    int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + 2 * (size_t)kStage2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIss + 2);  // mbar[kIss + b]: loads of buffer b
+  __shared__ double red[2][kT2 / 32];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kM - 1), half = tid >> 7;
+  const int KT = npad / kKS, RB = npad / kM;
+  const int cnt = *count;
+  const int npair = (cnt + 1) / 2;
+  const uint32_t mb = smem_addr(mbar);
+  const uint32_t lmb = mb + 8u * kIss;
+  const uint32_t sBase = smem_addr(smem);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tslot)),
+                 "r"(kLev * kN2));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < kIss + 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  uint32_t phase = 0;
+  uint32_t lphase[2] = {0u, 0u};
+  bool pend[2] = {false, false};
+  bool failed = false;
+  float ah[32], al[32];
+  // K stage J of (row block I, shifts s0, s1 (s1 < 0: none)) into buffer b
+  auto stage_in = [&](int I, int s0, int s1, int J, int b) {
+    pend[b] = true;
+    if (tid != 0) return;
+    const uint32_t dst = sBase + (uint32_t)b * kStage2;
+    const uint32_t lb = lmb + 8u * (uint32_t)b;
+    const uint32_t bytes = (uint32_t)kSl * (kAT + (s1 >= 0 ? 2 : 1) * kBT) * 2;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lb), "r"(bytes) : "memory");
+    for (int k = 0; k < kSl; ++k)
+      bulk_copy(dst + (uint32_t)(k * kAT * 2), Hs + ((size_t)(k * RB + I) * KT + J) * (kAT / 8),
+                (uint32_t)(kAT * 2), lb);
+    for (int l = 0; l < kSl; ++l) {
+      const uint32_t xb = dst + (uint32_t)(kSl * kAT * 2 + l * 2 * kBT * 2);
+      bulk_copy(xb, Xs + ((size_t)(s0 * kSl + l) * KT + J) * (kBT / 8), (uint32_t)(kBT * 2), lb);
+      if (s1 >= 0)
+        bulk_copy(xb + (uint32_t)(kBT * 2), Xs + ((size_t)(s1 * kSl + l) * KT + J) * (kBT / 8),
+                  (uint32_t)(kBT * 2), lb);
+    }
+  };
+  // this thread's 32 columns of every level of one window into the double-float sums
+  auto read_window = [&]() {
+    float sc = 0.0078125f * 0.0078125f;  // 2^{-7t}, t = 2
+#pragma unroll 1
+    for (int lv = 0; lv < kLev; ++lv) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(lv * kN2 + half * 32), r);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float p = __uint_as_float(r[c]) * sc;
+        const float s = ah[c] + p;
+        const float bp = s - ah[c];
+        al[c] += (ah[c] - (s - bp)) + (p - bp);
+        ah[c] = s;
+      }
+      sc *= 0.0078125f;
+    }
+  };
+  for (long long t = blockIdx.x; t < (long long)npair * RB && !failed; t += gridDim.x) {
+    int I, w;
+    pair_coords(t, RB, npair, &I, &w);
+    const int s0 = list[2 * w];
+    const int s1 = 2 * w + 1 < cnt ? list[2 * w + 1] : -1;
+    const int i0 = I * kM;
+    const int J0 = max(0, i0 - m) / kKS;
+    const int nst = KT - J0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) { ah[c] = 0.f; al[c] = 0.f; }
+    stage_in(I, s0, s1, J0, 0);
+    for (int st = 0; st < nst; ++st) {
+      const int b = st & 1;
+      const bool lok = mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
+      if (__syncthreads_or(!lok)) {
+        failed = true;
+        break;
+      }
+      lphase[b] ^= 1u;
+      pend[b] = false;
+      const int iss = tid >> 5;
+      if ((tid & 31) == 0 && iss < kIss) {
+        fence_after();
+        const bool fresh = (st % kWin) == 0;
+        const uint32_t aBase = sBase + (uint32_t)b * kStage2;
+        const uint32_t bBase = aBase + (uint32_t)(kSl * kAT * 2);
+        constexpr uint32_t kSbo = (uint32_t)kKG * 128u;
+#pragma unroll 1
+        for (int lv = 2; lv <= kSl + 1; ++lv) {
+          if (level_owner(lv) != iss) continue;
+#pragma unroll 1
+          for (int k = max(1, lv - kSl); k <= min(kSl, lv - 1); ++k) {
+#pragma unroll
+            for (int ks = 0; ks < kKS / 16; ++ks) {
+              const uint64_t ad = mat_desc(aBase + (uint32_t)((k - 1) * kAT * 2 + ks * 256), 128u, kSbo);
+              const uint64_t bd =
+                  mat_desc(bBase + (uint32_t)((lv - k - 1) * 2 * kBT * 2 + ks * 256), 128u, kSbo);
+              const bool first = fresh && k == max(1, lv - kSl) && ks == 0;
+              mma_bf16(tmem + (uint32_t)((lv - 2) * kN2), ad, bd, kIdesc2, first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(mb + 8u * (uint32_t)iss);
+      }
+      // the next stage streams into the other buffer (its products finished
+      // in the previous round)
+      if (st + 1 < nst) stage_in(I, s0, s1, J0 + st + 1, b ^ 1);
+      bool ok = true;
+      for (int q = 0; q < kIss; ++q) ok = mbar_wait(mb + 8u * q, phase) && ok;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      phase ^= 1u;
+      if ((st % kWin) == kWin - 1 || st == nst - 1) {
+        fence_after();
+        read_window();
+        fence_before();
+        __syncthreads();
+      }
+    }
+    if (failed) break;
+    // epilogue of this thread's shift: E(i, q) = R(i, q) - (H Xhat)(i, q) + sigma Xhat(i, q)
+    const int sh = half == 0 ? s0 : s1;
+    const int i = i0 + row;
+    double e2 = 0.0, x2 = 0.0;
+    if (sh >= 0 && i < n) {
+      const cd sigma = shifts[sh];
+      const int Ei = hexp[i];
+      const int* Ec = xexp + (size_t)sh * kN;
+      const cd* Xh = X + (size_t)sh * m * ldx;
+#pragma unroll
+      for (int q = 0; q < kN / 2; ++q) {
+        if (q < m) {
+          const int er_ = Ec[2 * q], ei_ = Ec[2 * q + 1];
+          const bool bad = Ei == kBadExp || er_ == kBadExp || ei_ == kBadExp;
+          const double hxr = ldexp((double)ah[2 * q] + (double)al[2 * q], Ei + er_);
+          const double hxi = ldexp((double)ah[2 * q + 1] + (double)al[2 * q + 1], Ei + ei_);
+          const cd x = Xh[i + (size_t)q * ldx];
+          double vr = -hxr + (sigma.x * x.x - sigma.y * x.y);
+          double vi = -hxi + (sigma.x * x.y + sigma.y * x.x);
+          if (i <= q) vr += R[i + (size_t)q * n];
+          if (bad) vr = __longlong_as_double(0x7ff8000000000000LL);
+          e2 += vr * vr + vi * vi;
+          x2 += x.x * x.x + x.y * x.y;
+          if (E != nullptr) E[(size_t)sh * n * m + i + (size_t)q * n] = make_float2((float)vr, (float)vi);
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+      x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][warp] = e2;
+      red[1][warp] = x2;
+    }
+    __syncthreads();
+    if ((tid & (kM - 1)) == 0 && sh >= 0) {
+      double a = 0.0, bsum = 0.0;
+      for (int k = half * (kM / 32); k < (half + 1) * (kM / 32); ++k) { a += red[0][k]; bsum += red[1][k]; }
+      atomicAdd(acc + 2 * (size_t)sh, a);
+      atomicAdd(acc + 2 * (size_t)sh + 1, bsum);
+    }
+    __syncthreads();
+  }
+  if (failed) {
+    // a completion never arrived: record it (every shift then fails
+    // certification), give the products and copies in flight one more
+    // bounded wait, then release TMEM
+    if (tid == 0) {
+      atomicExch(err, 1);
+      for (int q = 0; q < kIss; ++q) mbar_wait(mb + 8u * q, phase);
+      for (int b = 0; b < 2; ++b)
+        if (pend[b]) mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
+    }
+    __syncthreads();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kLev * kN2));
+}
+
 __global__ void tc_identity_list_kernel(int s, int* __restrict__ list, int* __restrict__ count,
                                         double* __restrict__ acc) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
@@ -559,14 +793,24 @@ int resid_tc_run(const Handle* h, const void* hbuf, void* xbuf, int s, const dou
   const cd* X = reinterpret_cast<const cd*>(Xhat);
   tc_xsplit_kernel<<<s, 256, 0, st>>>(n, m, np, list, count, X, ldx, Xs, xexp);
   count_launch();
-  SSV_CUDA_TRY(cudaFuncSetAttribute(tc_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kSmem));
-  const long long tasks = (long long)s * (np / kM);
-  const int grid =
-      (int)std::max<long long>(1, std::min<long long>(tasks, (long long)num_sms() * kCtasPerSm));
-  tc_residual_kernel<<<grid, kM, kSmem, st>>>(n, m, np, Hs, hexp, Xs, xexp, h->R,
-                                              reinterpret_cast<const cd*>(shifts), list, count, X,
-                                              ldx, static_cast<float2*>(E), acc, err);
+  if (kPairs) {
+    SSV_CUDA_TRY(cudaFuncSetAttribute(tc_residual2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSmem2));
+    const long long tasks = (long long)((s + 1) / 2) * (np / kM);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(tasks, (long long)num_sms()));
+    tc_residual2_kernel<<<grid, kT2, kSmem2, st>>>(n, m, np, Hs, hexp, Xs, xexp, h->R,
+                                                   reinterpret_cast<const cd*>(shifts), list, count, X,
+                                                   ldx, static_cast<float2*>(E), acc, err);
+  } else {
+    SSV_CUDA_TRY(cudaFuncSetAttribute(tc_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSmem));
+    const long long tasks = (long long)s * (np / kM);
+    const int grid =
+        (int)std::max<long long>(1, std::min<long long>(tasks, (long long)num_sms() * kCtasPerSm));
+    tc_residual_kernel<<<grid, kM, kSmem, st>>>(n, m, np, Hs, hexp, Xs, xexp, h->R,
+                                                reinterpret_cast<const cd*>(shifts), list, count, X,
+                                                ldx, static_cast<float2*>(E), acc, err);
+  }
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   return SSV_OK;

@@ -76,3 +76,19 @@ def test_window_bound_and_stage_count():
     # one stage is 8 H tiles of 128 x KS and 8 Xhat tiles of 32 x KS BF16: 80 KB, two CTAs per SM
     stage = SL * (KM * KS + KN * KS) * 2
     assert stage == 81920 and 2 * (stage + 64) <= 227 * 1024
+
+
+def test_two_32_row_tiles_side_by_side_form_one_64_row_tile():
+    """The two-shift residual puts shift A's and shift B's Xhat slice tiles (32
+    rows x 32 K each) next to each other and reads them as one 64-row B tile
+    with the same strides: element (row, k) of the 64-row tile must be element
+    (row mod 32, k) of tile row // 32."""
+    KG = 32 // 8
+
+    def off(row, k):
+        return (((row >> 3) * KG + (k >> 3)) * 8 + (row & 7)) * 8 + (k & 7)
+
+    tile = 32 * 32
+    for row in range(64):
+        for k in range(32):
+            assert off(row, k) == (row // 32) * tile + off(row % 32, k)
