@@ -501,7 +501,7 @@ constexpr int kN2 = 64;
 constexpr int kT2 = 2 * kM;
 constexpr uint32_t kIdesc2 = idesc_bf16(kM, kN2);
 constexpr uint32_t kStage2 = (uint32_t)kSl * (kAT + 2 * kBT) * 2;
-constexpr size_t kSmem2 = 2 * (size_t)kStage2 + 256;
+constexpr size_t kSmem2 = 2 * (size_t)kStage2 + 128;
 static_assert(kSmem2 <= 227 * 1024, "shared memory of the two-shift residual");
 static_assert(kLev * kN2 <= 512, "TMEM columns of the two-shift residual");
 constexpr int kPairGroup = 8;  // pairs that resident CTAs take together (L2 sharing of H tiles)
@@ -527,9 +527,8 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
     const cd* __restrict__ X, long long ldx, float2* __restrict__ E, double* __restrict__ acc,
     int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  // mbarriers: [2 iss + b] products of issuer iss on buffer b, [2 kIss + b] loads of buffer b
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + 2 * (size_t)kStage2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2 * kIss + 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIss + 2);  // mbar[kIss + b]: loads of buffer b
   __shared__ double red[2][kT2 / 32];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & (kM - 1), half = tid >> 7;
@@ -537,7 +536,7 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
   const int cnt = *count;
   const int npair = (cnt + 1) / 2;
   const uint32_t mb = smem_addr(mbar);
-  const uint32_t lmb = mb + 8u * (2 * kIss);
+  const uint32_t lmb = mb + 8u * kIss;
   const uint32_t sBase = smem_addr(smem);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -546,27 +545,18 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int q = 0; q < 2 * kIss + 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
+    for (int q = 0; q < kIss + 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  uint32_t mph[2] = {0u, 0u};       // phase of the product barriers of buffer b
-  bool mpend[2] = {false, false};   // products on buffer b issued, not yet seen complete
+  uint32_t phase = 0;
   uint32_t lphase[2] = {0u, 0u};
   bool pend[2] = {false, false};
   bool failed = false;
   float ah[32], al[32];
-  // wait for the products issued on buffer b (every issuer's commit)
-  auto wait_products = [&](int b) -> bool {
-    bool ok = true;
-    for (int q = 0; q < kIss; ++q) ok = mbar_wait(mb + 8u * (uint32_t)(2 * q + b), mph[b]) && ok;
-    mph[b] ^= 1u;
-    mpend[b] = false;
-    return ok;
-  };
   // K stage J of (row block I, shifts s0, s1 (s1 < 0: none)) into buffer b
   auto stage_in = [&](int I, int s0, int s1, int J, int b) {
     pend[b] = true;
@@ -615,10 +605,6 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
 #pragma unroll
     for (int c = 0; c < 32; ++c) { ah[c] = 0.f; al[c] = 0.f; }
     stage_in(I, s0, s1, J0, 0);
-    // software pipeline: the products of a stage are issued as soon as its
-    // copy lands; a buffer is refilled once its products are done, and a
-    // window's levels are read once its last stage's products are done (the
-    // next window's first products overwrite them)
     for (int st = 0; st < nst; ++st) {
       const int b = st & 1;
       const bool lok = mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
@@ -650,21 +636,19 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
             }
           }
         }
-        mma_commit(mb + 8u * (uint32_t)(2 * iss + b));
+        mma_commit(mb + 8u * (uint32_t)iss);
       }
-      mpend[b] = true;
-      // the other buffer's products (the previous stage) must be done before it
-      // takes the next stage
-      if (mpend[b ^ 1] && __syncthreads_or(!wait_products(b ^ 1))) {
+      // the next stage streams into the other buffer (its products finished
+      // in the previous round)
+      if (st + 1 < nst) stage_in(I, s0, s1, J0 + st + 1, b ^ 1);
+      bool ok = true;
+      for (int q = 0; q < kIss; ++q) ok = mbar_wait(mb + 8u * q, phase) && ok;
+      if (__syncthreads_or(!ok)) {
         failed = true;
         break;
       }
-      if (st + 1 < nst) stage_in(I, s0, s1, J0 + st + 1, b ^ 1);
+      phase ^= 1u;
       if ((st % kWin) == kWin - 1 || st == nst - 1) {
-        if (__syncthreads_or(!wait_products(b))) {
-          failed = true;
-          break;
-        }
         fence_after();
         read_window();
         fence_before();
@@ -722,11 +706,9 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
     // bounded wait, then release TMEM
     if (tid == 0) {
       atomicExch(err, 1);
-      for (int b = 0; b < 2; ++b) {
-        if (mpend[b])
-          for (int q = 0; q < kIss; ++q) mbar_wait(mb + 8u * (uint32_t)(2 * q + b), mph[b]);
+      for (int q = 0; q < kIss; ++q) mbar_wait(mb + 8u * q, phase);
+      for (int b = 0; b < 2; ++b)
         if (pend[b]) mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
-      }
     }
     __syncthreads();
   }
