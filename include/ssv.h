@@ -140,6 +140,31 @@ void ssv_default_opts(ssv_opts* o);
 int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double* B,
                long long ldb, const double* C, long long ldc, void* stream, ssv_handle* out);
 
+/* arithmetic of the reduction's bulk products (ssv_reduce_arith) */
+#define SSV_REDUCE_FP64 0   /* every product on the FP64 pipe (ssv_reduce) */
+#define SSV_REDUCE_TENSOR 1 /* two levels of blocking (Sec. 2.1: blocks of b = floor(128/m) m
+                               columns split into mini-blocks of m), the products A V_s,
+                               V^T A and the block's rank-b updates as error-free BF16 digit
+                               products on the tensor cores (eight 7-bit digits per value,
+                               levels accumulated exactly in FP32, FP64 result, about the
+                               accuracy of an FP64 product); panels, T and the small
+                               products in FP64.  m <= 64, n >= 2 */
+
+/*
+ * ssv_reduce_arith -- ssv_reduce with the arithmetic of its bulk products
+ * chosen by `arith` (SSV_REDUCE_FP64 or SSV_REDUCE_TENSOR).  Same arguments,
+ * ownership, result layout (H with the Householder vectors of Q_A below the
+ * m-th subdiagonal, R with those of Q_B below its diagonal, tau of every
+ * reflector) and errors as ssv_reduce; SSV_ENOTSUP when SSV_REDUCE_TENSOR
+ * is asked for m > 64, n < 2, or an n so large that a panel slice exceeds a
+ * CTA's shared memory (about 77000 rows at m = 16).  The scratch of the
+ * tensor-core form is about (p + n) n x 56 bytes, taken from the library's
+ * memory pool for the duration of the call.
+ */
+int ssv_reduce_arith(int n, int m, int p, const double* A, long long lda, const double* B,
+                     long long ldb, const double* C, long long ldc, int arith, void* stream,
+                     ssv_handle* out);
+
 /*
  * ssv_solve -- the batched shifted m-Hessenberg solve (Sec. 3, Algorithm 8).
  *   s >= 0 shifts, shifts (device) = s interleaved complex doubles.

@@ -121,7 +121,7 @@ __global__ void split_h_kernel(const double* __restrict__ H, int n, int m, float
 }  // namespace
 
 int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long long ldb,
-                const double* C, long long ldc, cudaStream_t st) {
+                const double* C, long long ldc, int arith, cudaStream_t st) {
   const int n = h->n, m = h->m, p = h->p;
   const int ldct = p > 0 ? p : 1;
   SSV_CUDA_TRY(cudaMemcpy2DAsync(h->H, sizeof(double) * n, A, sizeof(double) * lda,
@@ -131,8 +131,9 @@ int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long
   if (p > 0)
     SSV_CUDA_TRY(cudaMemcpy2DAsync(h->Ct, sizeof(double) * ldct, C, sizeof(double) * ldc,
                                    sizeof(double) * p, n, cudaMemcpyDeviceToDevice, st));
-  // Steps 1-4 of Algorithm 1 in one persistent cooperative kernel
-  int rc = reduce_persistent(h, st);
+  // Steps 1-4 of Algorithm 1: one persistent cooperative kernel on the FP64
+  // pipe, or the two-level blocked form with its products on the tensor cores
+  int rc = arith == SSV_REDUCE_TENSOR ? reduce_tc(h, st) : reduce_persistent(h, st);
   if (rc != SSV_OK) return rc;
   h->has_q = 1;
   SSV_CUDA_TRY(cudaMemsetAsync(h->hnorm2, 0, 2 * sizeof(double), st));

@@ -178,17 +178,25 @@ static int make_handle(int n, int m, int p, cudaStream_t st, Handle** out) {
 
 int ssv_reduce(int n, int m, int p, const double* A, long long lda, const double* B,
                long long ldb, const double* C, long long ldc, void* stream, ssv_handle* out) {
+  return ssv_reduce_arith(n, m, p, A, lda, B, ldb, C, ldc, SSV_REDUCE_FP64, stream, out);
+}
+
+int ssv_reduce_arith(int n, int m, int p, const double* A, long long lda, const double* B,
+                     long long ldb, const double* C, long long ldc, int arith, void* stream,
+                     ssv_handle* out) {
   if (!out) return SSV_EINVAL;
+  if (arith != SSV_REDUCE_FP64 && arith != SSV_REDUCE_TENSOR) return SSV_EINVAL;
   *out = nullptr;
   if (n < 1 || m < 1 || m > n || p < 0) return SSV_EINVAL;
   if (!A || !B || (p > 0 && !C)) return SSV_EINVAL;
   if (lda < n || ldb < n || (p > 0 && ldc < p)) return SSV_EINVAL;
+  if (arith == SSV_REDUCE_TENSOR && !reduce_tc_supported(n, m)) return SSV_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   Handle* h = nullptr;
   int rc = make_handle(n, m, p, st, &h);
   if (rc != SSV_OK) return rc;
-  void* tr = trace_begin("reduce", st);
-  rc = reduce_fp64(h, A, lda, B, ldb, C, ldc, st);
+  void* tr = trace_begin(arith == SSV_REDUCE_TENSOR ? "reduce_tc" : "reduce", st);
+  rc = reduce_fp64(h, A, lda, B, ldb, C, ldc, arith, st);
   if (rc == SSV_OK) rc = split_h(h, st);
   trace_end(tr, st);
   if (rc != SSV_OK) {

@@ -97,9 +97,15 @@ cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
 int reduce_persistent(Handle* h, cudaStream_t st);
 // self-test of the bounded grid barrier (expects SSV_ETIMEOUT)
 int barrier_selftest(long long limit, cudaStream_t st);
-// reduction (reduce_fp64.cu)
+// the reduction with two levels of blocking and its O(n^3) products as
+// FP64-accurate BF16 digit products on the tensor cores (reduce_tc.cu); same
+// contract as reduce_persistent.  Synchronises `st`.
+int reduce_tc(Handle* h, cudaStream_t st);
+bool reduce_tc_supported(int n, int m);
+size_t reduce_tc_scratch_bytes(int n, int p);
+// reduction (reduce_fp64.cu): arith SSV_REDUCE_FP64 or SSV_REDUCE_TENSOR
 int reduce_fp64(Handle* h, const double* A, long long lda, const double* B, long long ldb,
-                const double* C, long long ldc, cudaStream_t st);
+                const double* C, long long ldc, int arith, cudaStream_t st);
 // back-transform X = Q Xhat (reduce_fp64.cu)
 int apply_q_fp64(const Handle* h, int ncols, const double* Xhat, long long ldx, double* X,
                  long long ldX, cudaStream_t st);

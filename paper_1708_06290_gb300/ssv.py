@@ -62,7 +62,7 @@ EXPORTS = ("ssv_default_opts", "ssv_reduce", "ssv_solve", "ssv_apply_q", "ssv_ge
            "ssv_batch_create", "ssv_batch_run", "ssv_batch_destroy", "ssv_autotune",
            "ssv_trace_enable", "ssv_trace_reset", "ssv_trace_read", "ssv_selftest_barrier",
            "ssv_solve_rhs", "ssv_solve_trans", "ssv_givens_schedule", "ssv_tf_norm2",
-           "ssv_backward_error", "ssv_refine_counts", "ssv_pool_trim")
+           "ssv_backward_error", "ssv_refine_counts", "ssv_pool_trim", "ssv_reduce_arith")
 
 _lib = None
 
@@ -90,6 +90,7 @@ def load(build_if_missing=True):
     L.ssv_default_opts.argtypes = [ctypes.POINTER(Opts)]
     L.ssv_default_opts.restype = None
     L.ssv_reduce.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
+    L.ssv_reduce_arith.argtypes = [I, I, I, P, LL, P, LL, P, LL, I, P, ctypes.POINTER(P)]
     L.ssv_load_reduced.argtypes = [I, I, I, P, LL, P, LL, P, LL, P, ctypes.POINTER(P)]
     L.ssv_solve.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P, P]
     L.ssv_solve_noalloc.argtypes = [P, I, P, ctypes.POINTER(Opts), P, LL, P, P]
@@ -398,19 +399,30 @@ class Handle:
         return H, R, Ct[:p]
 
 
-def reduce(A, B, C, stream=None):
-    """Controller-Hessenberg reduction of (A, B, C) on the GPU; returns a Handle."""
+REDUCE_FP64, REDUCE_TENSOR = 0, 1
+_ARITH = {"fp64": REDUCE_FP64, "tensor": REDUCE_TENSOR}
+
+
+def reduce(A, B, C, stream=None, arith="fp64"):
+    """Controller-Hessenberg reduction of (A, B, C) on the GPU; returns a Handle.
+
+    arith: "fp64" (every product on the FP64 pipe, ssv_reduce) or "tensor"
+    (two-level blocking with the bulk products as FP64-accurate BF16 digit
+    products on the tensor cores, ssv_reduce_arith)."""
     L = load()
     for t, nm in ((A, "A"), (B, "B"), (C, "C")):
         _need_cuda(t, torch.float64, nm)
+    if arith not in _ARITH:
+        raise ValueError("arith must be one of %s" % sorted(_ARITH))
     n = A.shape[0]
     m = B.shape[1]
     p = C.shape[0]
     h = ctypes.c_void_p()
-    rc = L.ssv_reduce(n, m, p, ctypes.c_void_p(A.data_ptr()), _ld(A, n),
-                      ctypes.c_void_p(B.data_ptr()), _ld(B, n), ctypes.c_void_p(C.data_ptr()),
-                      _ld(C, p) if p > 0 else 1, _stream_ptr(stream), ctypes.byref(h))
-    _check(rc, "ssv_reduce")
+    rc = L.ssv_reduce_arith(n, m, p, ctypes.c_void_p(A.data_ptr()), _ld(A, n),
+                            ctypes.c_void_p(B.data_ptr()), _ld(B, n), ctypes.c_void_p(C.data_ptr()),
+                            _ld(C, p) if p > 0 else 1, _ARITH[arith], _stream_ptr(stream),
+                            ctypes.byref(h))
+    _check(rc, "ssv_reduce_arith")
     return Handle(h, n, m, p, stream)
 
 
