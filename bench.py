@@ -47,6 +47,9 @@ def parse():
                          "(--profile-solve: the precision of the profiled solve)")
     ap.add_argument("--first", choices=["tensor", "dfloat", "c64"], default="tensor",
                     help="first solve of the mixed path")
+    ap.add_argument("--reduce", choices=["auto", "fp64", "tensor"], default="auto",
+                    help="arithmetic of the reduction's bulk products; auto: FP64 for the fp64 "
+                         "step, the tensor-core form for the others")
     ap.add_argument("--side-steps", type=int, default=5,
                     help="timed steps of the comparison precisions")
     ap.add_argument("--nb", type=int, default=0)
@@ -71,14 +74,22 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(sysr, sig, nb, precision):
+def reduce_arith(args, precision):
+    if args.reduce != "auto":
+        return args.reduce
+    return "fp64" if precision == "fp64" else "tensor"
+
+
+def workload_config(sysr, sig, nb, precision, arith="fp64"):
+    red = ("FP64 reduction" if arith == "fp64" else
+           "reduction with tensor-core digit products (FP64 accuracy)")
     return {
         "workload": "precision grid: n=%d, m=p=%d, %d shifts on the 50x40 grid over [-4,0]x[-2,2], "
                     "A=-2I+G/sqrt(n)" % (sysr.n, sysr.m, len(sig)),
         "n": sysr.n, "m": sysr.m, "p": sysr.p, "shifts": int(len(sig)),
         "output": "G(sigma)=C X, complex128, p x (s*m)",
-        "step": "FP64 reduction + %s solve of all shifts (certified: backward error <= 1e-12)"
-                % precision,
+        "step": "%s + %s solve of all shifts (certified: backward error <= 1e-12)"
+                % (red, precision), "reduce": arith,
         "precision": precision, "nb": nb or (128 if sysr.n >= 1024 else 64),
         "l2": "inputs larger than L2 (A and H are 200 MB each; every step re-reads A)",
     }
@@ -245,7 +256,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(sysr, sig, 0, args.precision),
+        "config": workload_config(sysr, sig, 0, args.precision, reduce_arith(args, args.precision)),
         "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
                          "sample": "per step: oracle tier-2 reduced GEPP on %d grid shifts in one "
                                    "call (parallel over shifts, %.3f s) + those shifts' share of "
@@ -438,9 +449,11 @@ def profile_reduce(args):
     A, B, C = dev(sysr.A), dev(sysr.B), dev(sysr.C)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = ssv.reduce(A, B, C)
+    arith = "fp64" if args.reduce == "auto" else args.reduce
+    h = ssv.reduce(A, B, C, arith=arith)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": "reduce", "n": n, "m": args.profile_m, "s": time.perf_counter() - t0}))
+    print(json.dumps({"profile": "reduce", "arith": arith, "n": n, "m": args.profile_m,
+                      "s": time.perf_counter() - t0}))
     h.close()
     return 0
 
@@ -499,7 +512,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step(precision):
-        h = ssv.reduce(A_d, B_d, C_d)
+        h = ssv.reduce(A_d, B_d, C_d, arith=reduce_arith(args, precision))
         h.solve(sig_d, mode="g", precision=precision, nb=args.nb, out=out, status=status)
         return h
 
@@ -576,7 +589,7 @@ def main():
         B_e.copy_(B_h, non_blocking=True)
         C_e.copy_(C_h, non_blocking=True)
         sig_e.copy_(sig_h, non_blocking=True)
-        hh = ssv.reduce(A_e.t(), B_e.t(), C_e.t())
+        hh = ssv.reduce(A_e.t(), B_e.t(), C_e.t(), arith=reduce_arith(args, headp))
         o, st2, _ = hh.solve(sig_e, mode="g", precision=headp, nb=args.nb)
         G_h.copy_(o.t(), non_blocking=True)
         st_h.copy_(st2, non_blocking=True)
@@ -632,7 +645,8 @@ def main():
         "traffic": None,
     }
     # the largest single kernel of the mixed step: the FP64 reduction
-    red_ms = res["mixed"]["phase_ms_per_step"].get("reduce", float("nan"))
+    red_phases = res["mixed"]["phase_ms_per_step"]
+    red_ms = red_phases.get("reduce", red_phases.get("reduce_tc", float("nan")))
     red_flops = 10.0 / 3.0 * n ** 3 - 4.5 * n * n * m
     red_ach = red_flops / (red_ms * 1e-3) / 1e12
     roof_reduce = {
@@ -655,7 +669,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"mixed": "f32-pair+bf16-tc+f64", "fp64": "f64", "dfloat": "f32-pair"}[headp],
         "data": "synthetic",
-        "config": workload_config(sysr, sig, args.nb, headp),
+        "config": workload_config(sysr, sig, args.nb, headp, reduce_arith(args, headp)),
         "mixed_value": mx["value"], "fp64_value": res["fp64"]["value"],
         "dfloat_value": res["dfloat"]["value"],
         "mixed_speedup_vs_fp64": mx["value"] / res["fp64"]["value"],

@@ -15,9 +15,9 @@
 // below that scale, and with eight levels their error grew to about ten
 // times an FP64 product's.  A level's sums are integers below 2^24 for
 // K <= 128 (8 pairs x 128 x 127^2 < 2^24), hence exact in FP32;
-// after each window of 128 the levels are combined exactly in two 64-bit
-// fixed-point integers (levels 0-3 and 4-7, each below 2^46) and added into
-// FP64, two roundings per window.
+// after each window of 128 the levels are added exactly into 64-bit
+// fixed-point words (levels 0-3, 4-7 and 8; a window adds below 2^46 to a
+// word), kept across the whole K range and turned into FP64 once per output.
 //
 // A column of the V factor of a block's reflectors has entries of magnitude
 // <= 1 with a unit pivot (|v_r| <= 1 because |alpha - beta| >= |beta| >=
@@ -167,19 +167,17 @@ __global__ void __launch_bounds__(256) split_dig_kernel(const double* __restrict
 
 
 // ---------------------------------------------------------------------------
-// The digit product C (+)= op: output (r + roff, c + coff) for A rows r in
-// [M0, M1) and B rows c in [N0, N1) (column-major C, leading dimension ldc)
-// receives sum over the segments of sum_k A(r, k) B(c, k), k over the
-// segment's K tiles.  sub: C -= x, else C = x; with ksplit > 1 (one segment)
-// chunk s of the K range writes C + s * kstride.
+// The digit product: output (r + roff, c + coff) for A rows r in [M0, M1)
+// and B rows c in [N0, N1) (column-major C, leading dimension ldc) receives
+// x = sum_k A(r, k) B(c, k), k over the K tiles [J0, J1).  sub: C -= x, else
+// C = x; with ksplit > 1 chunk s of the K range writes C + s * kstride.
 // ---------------------------------------------------------------------------
 struct GSeg {
   DigitMat A, B;
   int J0, J1;
 };
 struct GArgs {
-  GSeg seg[2];
-  int nseg;
+  GSeg seg;
   int M0, M1, N0, N1;
   int roff, coff;
   double* C;
@@ -195,7 +193,9 @@ struct GCfg {
   static constexpr uint32_t kABytes = 2u * kTileEl * 2u;        // 128 rows x 32 K of one digit
   static constexpr uint32_t kBBytes = (uint32_t)NT * kTK * 2u;  // NT rows x 32 K of one digit
   static constexpr uint32_t kStage = (uint32_t)kD * (kABytes + kBBytes);
-  static constexpr size_t kSmem = 2 * (size_t)kStage + 256;
+  // stage buffers: three when they fit (N = 16: two loads in flight), else two
+  static constexpr int kNS = 3 * (size_t)kStage + 256 <= 227 * 1024 ? 3 : 2;
+  static constexpr size_t kSmem = kNS * (size_t)kStage + 256;
   static constexpr uint32_t kUsed = (uint32_t)LV * NT;
   static constexpr uint32_t kCols = kUsed <= 32 ? 32 : kUsed <= 64 ? 64 : kUsed <= 128 ? 128 : kUsed <= 256 ? 256 : 512;
   static constexpr uint32_t kIdesc = idesc_bf16(128, NT);
@@ -236,8 +236,9 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
   using Cfg = GCfg<NT, LV>;
   constexpr int CPT = NT / 2;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + 2 * (size_t)Cfg::kStage);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIssuers + 2);
+  constexpr int NS = Cfg::kNS;
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + NS * (size_t)Cfg::kStage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kIssuers + NS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3, half = warp >> 2;
   const uint32_t mb = smem_addr(mbar);
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int q = 0; q < kIssuers + 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
+    for (int q = 0; q < kIssuers + NS; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
@@ -257,41 +258,41 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
   fence_after();
   const uint32_t tmem = *tslot;
   uint32_t phase = 0;
-  uint32_t lphase[2] = {0u, 0u};
-  bool pend[2] = {false, false};
+  uint32_t lphase[3] = {0u, 0u, 0u};
+  bool pend[3] = {false, false, false};
   bool failed = false;
   const int iI0 = g.M0 / 128, iI1 = (g.M1 + 127) / 128;
   const int iN0 = g.N0 / NT, iN1 = (g.N1 + NT - 1) / NT;
   const int nI = max(0, iI1 - iI0), nN = max(0, iN1 - iN0);
   const long long ntile = (long long)nI * nN * g.ksplit;
+  const DigitMat& A = g.seg.A;
+  const DigitMat& B = g.seg.B;
+  constexpr int NW = (LV + 3) / 4;  // 64-bit words of the level sums
   for (long long tt = blockIdx.x; tt < ntile && !failed; tt += gridDim.x) {
     const int iN = iN0 + (int)(tt % nN);
     const int iI = iI0 + (int)((tt / nN) % nI);
     const int ks = (int)(tt / ((long long)nN * nI));
     const int i0 = iI * 128, n0 = iN * NT;
-    int jlo[2] = {0, 0}, len[2] = {0, 0};
-    for (int s = 0; s < g.nseg; ++s) {
-      int a = g.seg[s].J0, b = g.seg[s].J1;
-      if (g.ksplit > 1) {
-        int chunk = (b - a + g.ksplit - 1) / g.ksplit;
-        chunk = (chunk + kWinTiles - 1) / kWinTiles * kWinTiles;
-        a = a + ks * chunk;
-        b = min(b, a + chunk);
-      }
-      jlo[s] = a;
-      len[s] = max(0, b - a);
+    int jlo = g.seg.J0, jhi = g.seg.J1;
+    if (g.ksplit > 1) {
+      int chunk = (jhi - jlo + g.ksplit - 1) / g.ksplit;
+      chunk = (chunk + kWinTiles - 1) / kWinTiles * kWinTiles;
+      jlo = jlo + ks * chunk;
+      jhi = min(jhi, jlo + chunk);
     }
-    const int nst = len[0] + len[1];
-    double acc[CPT];
+    const int nst = max(0, jhi - jlo);
+    // exact level sums of every window, in 64-bit words: word w holds levels
+    // 4w .. 4w + 3, level L at bit 21 - 7 (L - 4 w); a window adds less than
+    // 2^46 to a word, so 2^17 windows (K up to 16 M) cannot overflow it
+    long long wacc[NW][CPT];
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) acc[c] = 0.0;
+    for (int w = 0; w < NW; ++w)
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) wacc[w][c] = 0;
     auto stage_in = [&](int st, int b) {
       pend[b] = true;
       if (tid != 0) return;
-      const int s = st < len[0] ? 0 : 1;
-      const int J = jlo[s] + (s == 0 ? st : st - len[0]);
-      const DigitMat& A = g.seg[s].A;
-      const DigitMat& B = g.seg[s].B;
+      const int J = jlo + st;
       const uint32_t dst = sBase + (uint32_t)b * Cfg::kStage;
       const uint32_t lb = lmb + 8u * (uint32_t)b;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lb), "r"(Cfg::kStage) : "memory");
@@ -301,11 +302,9 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
         bulk_copy(dst + kD * Cfg::kABytes + (uint32_t)d * Cfg::kBBytes,
                   B.d + tile_index(B, d, J, n0 / kTR) + (size_t)(n0 % kTR) * kTK, Cfg::kBBytes, lb);
     };
-    if (nst > 0) stage_in(0, 0);
+    for (int q = 0; q < NS - 1 && q < nst; ++q) stage_in(q, q);
     for (int st = 0; st < nst; ++st) {
-      const int b = st & 1;
-      const int s = st < len[0] ? 0 : 1;
-      const int jr = s == 0 ? st : st - len[0];  // stage within the segment
+      const int b = st % NS;
       const bool lok = mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
       if (__syncthreads_or(!lok)) {
         failed = true;
@@ -315,7 +314,7 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
       pend[b] = false;
       if (lane == 0 && warp < kIssuers) {
         fence_after();
-        const bool fresh = (jr % kWinTiles) == 0;
+        const bool fresh = (st % kWinTiles) == 0;
         const uint32_t aBase = sBase + (uint32_t)b * Cfg::kStage;
         const uint32_t bBase = aBase + kD * Cfg::kABytes;
 #pragma unroll 1
@@ -335,7 +334,8 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
         }
         mma_commit(mb + 8u * (uint32_t)warp);
       }
-      if (st + 1 < nst) stage_in(st + 1, b ^ 1);
+      // the buffer of stage st - 1 (its products finished last round) takes stage st + NS - 1
+      if (st + NS - 1 < nst) stage_in(st + NS - 1, (st + NS - 1) % NS);
       bool ok = true;
       for (int q = 0; q < kIssuers; ++q) ok = mbar_wait(mb + 8u * q, phase) && ok;
       if (__syncthreads_or(!ok)) {
@@ -343,36 +343,17 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
         break;
       }
       phase ^= 1u;
-      const bool seg_end = jr == len[s] - 1;
-      if ((jr % kWinTiles) == kWinTiles - 1 || seg_end) {
-        // the window's exact levels, combined exactly in 64-bit integers
-        // (levels 0-3 in units of 2^-35 of the product's scale, 4-7 in units
-        // of 2^-63, level 8 in units of 2^-91; each word stays below 2^46, so
-        // it converts to FP64 exactly), then added into FP64: one rounding per word
+      if ((st % kWinTiles) == kWinTiles - 1 || st == nst - 1) {
         fence_after();
-        const int r = i0 + quarter * 32 + lane;
-        const int Ea = exp_of(g.seg[s].A.ex, r);
-#pragma unroll 1
-        for (int word = 0; word < (LV + 3) / 4; ++word) {
-          long long wacc[CPT];
 #pragma unroll
-          for (int c = 0; c < CPT; ++c) wacc[c] = 0;
+        for (int w = 0; w < NW; ++w) {
 #pragma unroll 1
-          for (int L = 4 * word; L < min(LV, 4 * word + 4); ++L) {
+          for (int L = 4 * w; L < min(LV, 4 * w + 4); ++L) {
             uint32_t rv[CPT];
             tmem_ld_cols<CPT>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L * NT + half * CPT), rv);
-            const int sh = 21 - 7 * (L - 4 * word);
+            const int sh = 21 - 7 * (L - 4 * w);
 #pragma unroll
-            for (int c = 0; c < CPT; ++c)
-              wacc[c] += (long long)__float2int_rn(__uint_as_float(rv[c])) << sh;
-          }
-          const int unit = -35 - 28 * word;  // level L of word w sits at bit 21 - 7 (L - 4 w)
-#pragma unroll
-          for (int c = 0; c < CPT; ++c) {
-            const int col = n0 + half * CPT + c;
-            const int Eb = exp_of(g.seg[s].B.ex, col);
-            if (Ea == kBadExp || Eb == kBadExp) acc[c] = __longlong_as_double(0x7ff8000000000000LL);
-            else if (Ea > -4000 && Eb > -4000) acc[c] = fma((double)wacc[c], pow2(Ea + Eb + unit), acc[c]);
+            for (int c = 0; c < CPT; ++c) wacc[w][c] += (long long)__float2int_rn(__uint_as_float(rv[c])) << sh;
           }
         }
         fence_before();
@@ -380,16 +361,42 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
       }
     }
     if (failed) break;
+    // epilogue: word w weighs 2^{Ea + Eb - 35 - 28 w}; all loads of C first
     const int r = i0 + quarter * 32 + lane;
     if (r >= g.M0 && r < g.M1) {
+      const int Ea = exp_of(A.ex, r);
       double* Cr = g.C + (size_t)ks * g.kstride + (long long)(r + g.roff);
+      double x[CPT];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         const int col = n0 + half * CPT + c;
-        if (col >= g.N0 && col < g.N1) {
-          double* pc = Cr + (long long)(col + g.coff) * g.ldc;
-          if (g.sub) *pc -= acc[c];
-          else *pc = acc[c];
+        const int Eb = (col >= g.N0 && col < g.N1) ? exp_of(B.ex, col) : 0;
+        double v = 0.0;
+        if (Ea == kBadExp || Eb == kBadExp) {
+          v = __longlong_as_double(0x7ff8000000000000LL);
+        } else if (Ea > -4000 && Eb > -4000) {
+#pragma unroll
+          for (int w = NW - 1; w >= 0; --w) v = fma((double)wacc[w][c], pow2(Ea + Eb - 35 - 28 * w), v);
+        }
+        x[c] = v;
+      }
+      if (g.sub) {
+        double old[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const int col = n0 + half * CPT + c;
+          old[c] = (col >= g.N0 && col < g.N1) ? Cr[(long long)(col + g.coff) * g.ldc] : 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const int col = n0 + half * CPT + c;
+          if (col >= g.N0 && col < g.N1) Cr[(long long)(col + g.coff) * g.ldc] = old[c] - x[c];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const int col = n0 + half * CPT + c;
+          if (col >= g.N0 && col < g.N1) Cr[(long long)(col + g.coff) * g.ldc] = x[c];
         }
       }
     }
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
     if (tid == 0) {
       atomicExch(g.err, 1);
       for (int q = 0; q < kIssuers; ++q) mbar_wait(mb + 8u * q, phase);
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < NS; ++b)
         if (pend[b]) mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
     }
     __syncthreads();
@@ -424,7 +431,7 @@ constexpr int kRedZ = 4096;              // Z = T^T W
 constexpr int kRedPiv = 8192;            // pivot rows of the QR (two slots of 64)
 constexpr int kRedS = 8192 + 128;        // S = V^T V_s ((j + wp) x wp)
 constexpr int kRedTotal = kRedS + 8192;
-constexpr size_t kPanFixed = 4096 + 4096 + 256 + 64 * 3 + 8 + 8 * 64;  // doubles besides the panel
+constexpr size_t kPanFixed = 4096 + 4096 + 256 + 64 * 3 + 8 + 8 * kBmax;  // doubles besides the panel
 
 struct PanArgs {
   double* P;          // panel column t, matrix row r: P[r + t * ldp]
@@ -480,6 +487,38 @@ __device__ bool grid_sync(unsigned* bar, int* err) {
   return s_ok != 0;
 }
 
+// Sums with every thread of the CTA: out(e) = sum_k term(e, k) for e in
+// [e0, e1), k < count(e); tpe threads (a power of two <= 32, the largest with
+// tpe (e1 - e0) <= kPT) share an output, each taking every tpe-th k four at a
+// time, then a shuffle tree.  The order is fixed, so every CTA that forms the
+// same sums gets the same bits.
+template <typename Count, typename Term, typename Store>
+__device__ __forceinline__ void block_sums(int e0, int e1, Count count, Term term, Store store) {
+  const int nE = e1 - e0;
+  if (nE <= 0) return;
+  int tpe = 32;
+  while (tpe > 1 && tpe * nE > kPT) tpe >>= 1;
+  const int per = kPT / tpe;
+  const int t = threadIdx.x, sub = t % tpe;
+  for (int c0 = 0; c0 < nE; c0 += per) {
+    const int el = c0 + t / tpe;
+    const bool act = el < nE;
+    const int e = e0 + el;
+    double acc = 0.0;
+    if (act) {
+      const int K = count(e);
+      int k = sub;
+      for (; k + 3 * tpe < K; k += 4 * tpe) {
+        const double a0 = term(e, k), a1 = term(e, k + tpe), a2 = term(e, k + 2 * tpe), a3 = term(e, k + 3 * tpe);
+        acc += (a0 + a1) + (a2 + a3);
+      }
+      for (; k < K; k += tpe) acc += term(e, k);
+    }
+    for (int o = tpe >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (act && sub == 0) store(e, acc);
+  }
+}
+
 __device__ __forceinline__ void put_digits_v(const DigitMat& M, int row, int k, double v) {
   unsigned short d[kD];
   digits_of(v, 1, d);
@@ -505,7 +544,7 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
   double* piv = dots + 64;
   double* taus = piv + 64;
   double* misc = taus + 64;
-  double* tw = misc + 8;                 // 8 warps x 64: new entries of a row of T
+  double* tw = misc + 8;                 // 8 warps x kBmax: a row of T
   auto slot = [&](int q, int gg) { return a.part + ((size_t)q * G + gg) * kPartW; };
 
   for (int e = tid; e < nr * w; e += kPT) {
@@ -538,18 +577,16 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
     }
     if (!grid_sync(a.bar, a.err)) return;
     const int ch = (j * w + G - 1) / G;
-    for (int e = g * ch + tid; e < min(j * w, (g + 1) * ch); e += kPT) {
-      double acc = 0.0;
-      for (int gg = 0; gg < G; ++gg) acc += __ldcg(slot(0, gg) + e);
-      a.red[kRedW + e] = acc;
-    }
+    const int e0 = min(j * w, g * ch), e1 = min(j * w, (g + 1) * ch);
+    const double* s0 = slot(0, 0);
+    block_sums(
+        e0, e1, [&](int) { return G; }, [&](int e, int gg) { return __ldcg(s0 + (size_t)gg * kPartW + e); },
+        [&](int e, double v) { a.red[kRedW + e] = v; });
     if (!grid_sync(a.bar, a.err)) return;
-    for (int e = g * ch + tid; e < min(j * w, (g + 1) * ch); e += kPT) {
-      const int i = e / w, t = e % w;
-      double acc = 0.0;
-      for (int k = 0; k <= i; ++k) acc = fma(a.T[k + (size_t)i * kBmax], __ldcg(a.red + kRedW + k * w + t), acc);
-      a.red[kRedZ + e] = acc;
-    }
+    block_sums(
+        e0, e1, [&](int e) { return e / w + 1; },
+        [&](int e, int k) { return a.T[k + (size_t)(e / w) * kBmax] * __ldcg(a.red + kRedW + k * w + e % w); },
+        [&](int e, double v) { a.red[kRedZ + e] = v; });
     if (!grid_sync(a.bar, a.err)) return;
     for (int e = tid; e < j * w; e += kPT) Zs[e] = __ldcg(a.red + kRedZ + e);
     __syncthreads();
@@ -581,11 +618,12 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
       if (pr >= ra && pr < ra + nr && tid < nk) a.red[kRedPiv + (t & 1) * 64 + tid] = Ps[(size_t)(t + tid) * rpc + (pr - ra)];
     }
     if (!grid_sync(a.bar, a.err)) return;
-    if (tid < nk) {
-      double acc = 0.0;
-      for (int gg = 0; gg < G; ++gg) acc += __ldcg(slot(t & 1, gg) + tid);
-      dots[tid] = acc;
-      piv[tid] = __ldcg(a.red + kRedPiv + (t & 1) * 64 + tid);
+    {
+      const double* sq = slot(t & 1, 0);
+      block_sums(
+          0, nk, [&](int) { return G; }, [&](int e, int gg) { return __ldcg(sq + (size_t)gg * kPartW + e); },
+          [&](int e, double v) { dots[e] = v; });
+      if (tid < nk) piv[tid] = __ldcg(a.red + kRedPiv + (t & 1) * 64 + tid);
     }
     __syncthreads();
     if (tid == 0) {
@@ -656,17 +694,21 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
   if (!grid_sync(a.bar, a.err)) return;
   {
     const int ch = (ns + G - 1) / G;
-    for (int e = g * ch + tid; e < min(ns, (g + 1) * ch); e += kPT) {
-      double acc = 0.0;
-      for (int gg = 0; gg < G; ++gg) acc += __ldcg(slot(2, gg) + e);
-      a.red[kRedS + e] = acc;
-    }
+    const double* s2 = slot(2, 0);
+    block_sums(
+        min(ns, g * ch), min(ns, (g + 1) * ch), [&](int) { return G; },
+        [&](int e, int gg) { return __ldcg(s2 + (size_t)gg * kPartW + e); }, [&](int e, double v) { a.red[kRedS + e] = v; });
   }
   if (!grid_sync(a.bar, a.err)) return;
   // T's new columns (Eq. for T, one reflector at a time): row i of CTA i mod G,
-  // a warp per row, lanes along k
-  double* my_tw = tw + warp * 64;
+  // a warp per row, lanes along k; S and the row staged in shared memory
+  double* Ss = Vc;  // ns <= 8192 doubles over Vc and Zs
+  for (int e = tid; e < ns; e += kPT) Ss[e] = __ldcg(a.red + kRedS + e);
+  __syncthreads();
+  double* trow = tw + warp * kBmax;
   for (int i = g + warp * G; i < j + wp; i += 8 * G) {
+    for (int k = lane; k < j; k += 32) trow[k] = a.T[i + (size_t)k * kBmax];
+    __syncwarp();
     for (int t = 0; t < wp; ++t) {
       const int col = j + t;
       double val;
@@ -676,18 +718,15 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
         val = taus[t];
       } else {
         double acc = 0.0;
-        for (int k = i + lane; k < col; k += 32) {
-          const double tik = k < j ? a.T[i + (size_t)k * kBmax] : my_tw[k - j];
-          acc = fma(tik, __ldcg(a.red + kRedS + k * wp + t), acc);
-        }
+        for (int k = i + lane; k < col; k += 32) acc = fma(trow[k], Ss[k * wp + t], acc);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         val = -taus[t] * acc;
       }
       __syncwarp();
-      if (lane == 0) my_tw[t] = val;
+      if (lane == 0) trow[col] = val;
       __syncwarp();
     }
-    for (int t = lane; t < wp; t += 32) a.T[i + (size_t)(j + t) * kBmax] = my_tw[t];
+    for (int t = lane; t < wp; t += 32) a.T[i + (size_t)(j + t) * kBmax] = trow[j + t];
     __syncwarp();
   }
 }
@@ -900,12 +939,10 @@ int gemm_long(int width, const GArgs& g, cudaStream_t st) {
 GArgs gemm_args(const DigitMat& A, const DigitMat& B, int J0, int J1, int M0, int M1, int N0, int N1, double* C,
                 long long ldc, int sub, const RtcScratch& S) {
   GArgs g;
-  g.seg[0].A = A;
-  g.seg[0].B = B;
-  g.seg[0].J0 = J0;
-  g.seg[0].J1 = J1;
-  g.seg[1] = g.seg[0];
-  g.nseg = 1;
+  g.seg.A = A;
+  g.seg.B = B;
+  g.seg.J0 = J0;
+  g.seg.J1 = J1;
   g.M0 = M0;
   g.M1 = M1;
   g.N0 = N0;
