@@ -33,6 +33,10 @@ import workloads as W  # noqa: E402
 METRIC = "shift-solves/s at n=5000,m=16 (mixed vs FP64, resid<=1e-12); p50/p99 latency"
 # DRAM bytes of one reduce_blocked_kernel launch at n = 5000, m = p = 16 (ncu), or None
 REDUCE_TRAFFIC_N5000_M16 = 130381078528 + 90573036032
+# dram__bytes_read.sum + dram__bytes_write.sum of all tcs_update_kernel launches of one
+# 304-shift sweep of this workload, per shift (profiles/tcs_sweep_n5000_m16_304shifts.md);
+# the window state it streams is per shift, so traffic scales with the shifts
+TCS_UPDATE_TRAFFIC_PER_SHIFT = (17579877120 + 18607825408) / 304.0
 UNIT = "shift-solves/s"
 
 
@@ -359,6 +363,16 @@ def batching_measurement(ssv, dev, args):
     return res
 
 
+def bf16_peak_sustained():
+    """The sustained BF16 figure of MEASURED_PEAKS.json (the kernels below are timed inside
+    a long step), else the recipe's fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+    except (OSError, ValueError, KeyError):
+        return 1700.0, "fallback sustained BF16 1.7 PFLOP/s (of fallback)"
+
+
 def tensor_residual_roofline(n, m, s, mixed):
     """BF16 tensor work of one certification pass of the mixed path: per shift and
     128-row block I, 36 digit-slice products of 128 x 32 x (K from column I*128-m)."""
@@ -366,19 +380,39 @@ def tensor_residual_roofline(n, m, s, mixed):
     k_total = sum(npad - (max(0, i0 - m) // 32) * 32 for i0 in range(0, npad, 128))
     flops = 2.0 * 36 * 128 * 32 * k_total * s
     ms = mixed["phase_ms_per_step"].get("mixed_residual", float("nan"))
-    peak = None
-    try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
-            peak = float(json.load(f)["bf16_tflops"])
-    except (OSError, ValueError, KeyError):
-        peak = 1900.0
+    peak, src = bf16_peak_sustained()
     ach = flops / (ms * 1e-3) / 1e12
-    return {"kernel": "tc_residual_kernel (+ digit split of Xhat)", "bound": "tensor",
+    return {"kernel": "tc_residual2_kernel (two shifts per item, + digit split of Xhat)", "bound": "tensor",
             "unit": "TFLOP/s", "achieved": ach, "peak": peak, "frac": ach / peak,
-            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; of measured)",
+            "peak_source": src,
             "flops_per_pass": flops, "pass_ms": ms,
             "flops_definition": "executed BF16 products: 36 slice pairs x 2 x 128 x 32 x K per "
                                 "(shift, 128-row block); K = npad - 32 floor((128 I - m) / 32)"}
+
+
+def tcs_update_flops(n, m, s):
+    """Executed BF16 flops of all tcs_update_kernel launches of one tensor-core sweep (the
+    loop of solve_tc): per item (128 rows above the block x one group of S = 64 / 2m shifts)
+    ceil(nbe / 32) stages of 35 digit pairs x 2 K-halves of 128 x 64 x 16, then per shift 28
+    pairs x 2 K-halves of 128 x 2m x 16 (Z2 P2).  Valid for 2m dividing 64."""
+    cs = 2 * m
+    if 64 % cs:
+        return None, 0
+    S = 64 // cs
+    G = -(-s // S)
+    nbe_first = (n - m) % 128 or 128
+    k, step, flops, launches = n, 0, 0.0, 0
+    while k > m:
+        nbe = nbe_first if step == 0 else 128
+        step += 1
+        hrows = k - nbe
+        if hrows > 0:
+            items = -(-hrows // 128) * G
+            per_item = -(-nbe // 32) * 70 * 2.0 * 128 * 64 * 16 + S * 56 * 2.0 * 128 * cs * 16
+            flops += items * per_item
+            launches += 1
+        k -= nbe
+    return flops, launches
 
 
 def profile_resid(args):
@@ -551,8 +585,9 @@ def main():
         corr, resol = ssv.refine_counts(reset=True)
         value, total_ms = combine_ranks(world, s, steps, e0.elapsed_time(e1), max_over_ranks)
         phase_ms = {k: round(v[0] / steps, 3) for k, v in phases.items()}
+        phase_calls = {k: int(v[1]) for k, v in phases.items()}
         return {"value": value, "ms_per_step": total_ms / steps, "steps": steps,
-                "phase_ms_per_step": phase_ms, "gpu_launches": int(launches),
+                "phase_ms_per_step": phase_ms, "phase_calls": phase_calls, "gpu_launches": int(launches),
                 "corrections_per_step": corr / steps, "fp64_resolves_per_step": resol / steps,
                 **gate}
 
@@ -644,24 +679,50 @@ def main():
                       "tensor cores instead, so this is the rate a double-float sweep would need",
         "traffic": None,
     }
-    # the largest single kernel of the mixed step: the FP64 reduction
+    # the reduction of the mixed step (tensor-core form unless --reduce fp64): FP64-equivalent
+    # rate against the DFMA peak, so a fraction above 1 is a reduction faster than the FP64
+    # pipe could run it
     red_phases = res["mixed"]["phase_ms_per_step"]
-    red_ms = red_phases.get("reduce", red_phases.get("reduce_tc", float("nan")))
+    red_tc = "reduce_tc" in red_phases
+    red_ms = red_phases.get("reduce_tc", red_phases.get("reduce", float("nan")))
     red_flops = 10.0 / 3.0 * n ** 3 - 4.5 * n * n * m
     red_ach = red_flops / (red_ms * 1e-3) / 1e12
     roof_reduce = {
-        "kernel": "reduce_blocked_kernel (FP64 controller-Hessenberg reduction, one launch)",
-        "bound": "alu", "unit": "TFLOP/s", "achieved": red_ach, "peak": fp64_peak,
+        "kernel": ("tensor-core reduction (panel_kernel, tc_gemm_kernel<16,9> / <32,9> / <64,8>, "
+                   "digit splits; about 1400 launches)" if red_tc else
+                   "reduce_blocked_kernel (FP64 controller-Hessenberg reduction, one launch)"),
+        "bound": "alu", "unit": "TFLOP/s (FP64-equivalent)", "achieved": red_ach, "peak": fp64_peak,
         "frac": red_ach / fp64_peak,
         "peak_source": "FP64 DFMA probe measured in this run (nominal GB300 FP64 1.25 TFLOP/s)",
         "launch_ms": red_ms,
         "flops_definition": "10/3 n^3 - 9/2 n^2 m (the blocking-independent terms of the "
                             "paper's reduction count)",
-        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one reduction launch at
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of the FP64 reduction launch at
         # n = 5000, m = p = 16 (profiles/reduce_blocked_kernel_n5000_m16.md)
-        "traffic": REDUCE_TRAFFIC_N5000_M16 if (n, m, p) == (5000, 16, 16) else None,
+        "traffic": (REDUCE_TRAFFIC_N5000_M16 if (n, m, p) == (5000, 16, 16) and not red_tc else None),
     }
-    roofline = roof_reduce if headp == "mixed" else roof_fp64
+    # the largest kernel of the mixed step by time: the tensor-core sweep's update, timed
+    # per launch by the library's tracer spans (CUDA events on the solve's stream)
+    upd_tot = res["mixed"]["phase_ms_per_step"].get("tcs_update", float("nan")) * res["mixed"]["steps"]
+    upd_calls = res["mixed"]["phase_calls"].get("tcs_update", 0)
+    upd_flops, upd_launches = tcs_update_flops(n, m, s)
+    bf16_peak, bf16_src = bf16_peak_sustained()
+    roof_update = None
+    if upd_flops and upd_calls:
+        upd_ms = upd_tot / upd_calls
+        ach_u = upd_flops / upd_launches / (upd_ms * 1e-3) / 1e12
+        roof_update = {
+            "kernel": "tcs_update_kernel<true> (tensor-core sweep trailing update, %d launches "
+                      "per solve)" % upd_launches,
+            "bound": "tensor", "unit": "TFLOP/s", "achieved": ach_u, "peak": bf16_peak,
+            "frac": ach_u / bf16_peak, "peak_source": bf16_src, "launch_ms": upd_ms,
+            "flops_definition": "executed BF16 digit products per launch, averaged over the "
+                                "solve's launches (bench.py tcs_update_flops)",
+            "traffic": (TCS_UPDATE_TRAFFIC_PER_SHIFT * s / upd_launches
+                        if TCS_UPDATE_TRAFFIC_PER_SHIFT and (n, m) == (5000, 16) else None),
+        }
+    roofline = (roof_update if headp in ("mixed", "split") and roof_update else
+                (roof_reduce if headp != "fp64" else roof_fp64))
     mx = res["mixed"]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -679,6 +740,7 @@ def main():
         "mixed_fp64_resolves_per_step": mx["fp64_resolves_per_step"],
         "fp64_max_backward_error": res["fp64"]["max_backward_error"],
         "roofline": roofline,
+        "roofline_reduction": roof_reduce,
         "roofline_first_solve": roof_first,
         "roofline_fp64_sweep": roof_fp64,
         "phase_ms": {k: res[k]["phase_ms_per_step"] for k in ("mixed", "fp64", "dfloat")},

@@ -1254,9 +1254,11 @@ int solve_tc(const Handle* h, int s, const double* shifts, int mode, double* out
           const long long items = (long long)((hrows + kUM - 1) / kUM) * G;
           const int grid =
               (int)std::max<long long>(1, std::min<long long>(items, (long long)num_sms() * kCtasU));
+          void* tru = trace_begin("tcs_update", st);  // per-launch span when tracing is on
           if (tcz) tcs_update_kernel<true><<<grid, kUT, kUpdSmem, st>>>(a, k, nbe);
           else tcs_update_kernel<false><<<grid, kUT, kUpdSmem, st>>>(a, k, nbe);
           count_launch();
+          trace_end(tru, st);
         }
         k -= nbe;
       }
