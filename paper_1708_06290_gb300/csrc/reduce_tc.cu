@@ -59,12 +59,11 @@ constexpr int kTR = 64;                  // rows of a digit tile
 constexpr int kTK = 32;                  // K of a digit tile
 constexpr int kTileEl = kTR * kTK;       // 2048 BF16 values (4 KB) in the core-matrix layout
 constexpr int kD = kDigits;              // digits per operand value
-constexpr int kLvMax = 9;                // levels kept at most (level 8: the long-K products)
 constexpr int kBmax = 128;               // reflectors per block at most
 constexpr int kMaxW = 64;                // mini-block width (m) at most
 constexpr int kWinTiles = 4;             // K tiles per exact window (4 x 32 = 128)
 constexpr int kGT = 256;                 // threads of the product kernel
-constexpr int kIssuers = 4;              // warps issuing the digit products
+constexpr int kIssuers = 1;              // MMA completion barriers (one issuing thread)
 constexpr unsigned long long kSpin = 1ull << 26;  // grid barrier naps before giving up
 
 // Digit tiles of an R x K operand (R rows, each scaled by 2^ex[r]): tile
@@ -192,7 +191,9 @@ template <int NT, int LV>
 struct GCfg {
   static constexpr uint32_t kABytes = 2u * kTileEl * 2u;        // 128 rows x 32 K of one digit
   static constexpr uint32_t kBBytes = (uint32_t)NT * kTK * 2u;  // NT rows x 32 K of one digit
-  static constexpr uint32_t kStage = (uint32_t)kD * (kABytes + kBBytes);
+  // A digit planes, B digit planes, then one B plane of zeros (written once)
+  // so that the first fused product of a window covers every level
+  static constexpr uint32_t kStage = (uint32_t)kD * (kABytes + kBBytes) + kBBytes;
   // stage buffers: three when they fit (N = 16: two loads in flight), else two
   static constexpr int kNS = 3 * (size_t)kStage + 256 <= 227 * 1024 ? 3 : 2;
   static constexpr size_t kSmem = kNS * (size_t)kStage + 256;
@@ -203,20 +204,6 @@ struct GCfg {
   static_assert(kUsed <= 512, "TMEM columns");
   static_assert(LV == 8 || LV == 9, "levels");
 };
-
-// Levels issued by warp w (0..3), balanced by pair count (level t has
-// min(t, 14 - t) + 1 pairs): eight levels {7,0} {6,1} {5,2} {4,3} (9 pairs
-// each); nine levels {8,2,0} {7,3} {6,4} {5,1} (11, 12, 12, 8).
-template <int LV>
-__device__ __forceinline__ int owned_level(int w, int q) {
-  if constexpr (LV == 8) {
-    return q == 0 ? 7 - w : (q == 1 ? w : -1);
-  } else {
-    if (q == 0) return 8 - w;
-    if (q == 1) return w == 0 ? 2 : (w == 3 ? 1 : w + 2);
-    return w == 0 ? 0 : -1;
-  }
-}
 
 template <int CPT>
 __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[CPT]) {
@@ -253,6 +240,11 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
     for (int q = 0; q < kIssuers + NS; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int bq = 0; bq < NS; ++bq) {
+    uint4* zp = reinterpret_cast<uint4*>(smem + (size_t)bq * Cfg::kStage + kD * (Cfg::kABytes + Cfg::kBBytes));
+    for (int e = tid; e < (int)(Cfg::kBBytes / 16); e += kGT) zp[e] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeros, seen by the tensor cores
   fence_before();
   __syncthreads();
   fence_after();
@@ -268,19 +260,46 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
   const DigitMat& A = g.seg.A;
   const DigitMat& B = g.seg.B;
   constexpr int NW = (LV + 3) / 4;  // 64-bit words of the level sums
-  for (long long tt = blockIdx.x; tt < ntile && !failed; tt += gridDim.x) {
-    const int iN = iN0 + (int)(tt % nN);
-    const int iI = iI0 + (int)((tt / nN) % nI);
-    const int ks = (int)(tt / ((long long)nN * nI));
-    const int i0 = iI * 128, n0 = iN * NT;
+  struct Tile {
+    int iI, n0, ks, jlo, nst;
+  };
+  auto tile_of = [&](long long tt) {
+    Tile t;
+    t.n0 = (iN0 + (int)(tt % nN)) * NT;
+    t.iI = iI0 + (int)((tt / nN) % nI);
+    t.ks = (int)(tt / ((long long)nN * nI));
     int jlo = g.seg.J0, jhi = g.seg.J1;
     if (g.ksplit > 1) {
       int chunk = (jhi - jlo + g.ksplit - 1) / g.ksplit;
       chunk = (chunk + kWinTiles - 1) / kWinTiles * kWinTiles;
-      jlo = jlo + ks * chunk;
+      jlo = jlo + t.ks * chunk;
       jhi = min(jhi, jlo + chunk);
     }
-    const int nst = max(0, jhi - jlo);
+    t.jlo = jlo;
+    t.nst = max(0, jhi - jlo);
+    return t;
+  };
+  // stage st of tile t into buffer b
+  auto stage_in = [&](const Tile& t, int st, int b) {
+    pend[b] = true;
+    if (tid != 0) return;
+    const int J = t.jlo + st;
+    const uint32_t dst = sBase + (uint32_t)b * Cfg::kStage;
+    const uint32_t lb = lmb + 8u * (uint32_t)b;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lb),
+                 "r"(Cfg::kStage - Cfg::kBBytes)
+                 : "memory");
+    for (int d = 0; d < kD; ++d)
+      bulk_copy(dst + (uint32_t)d * Cfg::kABytes, A.d + tile_index(A, d, J, 2 * t.iI), Cfg::kABytes, lb);
+    for (int d = 0; d < kD; ++d)
+      bulk_copy(dst + kD * Cfg::kABytes + (uint32_t)d * Cfg::kBBytes,
+                B.d + tile_index(B, d, J, t.n0 / kTR) + (size_t)(t.n0 % kTR) * kTK, Cfg::kBBytes, lb);
+  };
+  bool prefetched = false;  // the first stages of this CTA's next tile are already in flight
+  for (long long tt = blockIdx.x; tt < ntile && !failed; tt += gridDim.x) {
+    const Tile cur = tile_of(tt);
+    const int i0 = cur.iI * 128, n0 = cur.n0, ks = cur.ks;
+    const int nst = cur.nst;
     // exact level sums of every window, in 64-bit words: word w holds levels
     // 4w .. 4w + 3, level L at bit 21 - 7 (L - 4 w); a window adds less than
     // 2^46 to a word, so 2^17 windows (K up to 16 M) cannot overflow it
@@ -289,20 +308,9 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
     for (int w = 0; w < NW; ++w)
 #pragma unroll
       for (int c = 0; c < CPT; ++c) wacc[w][c] = 0;
-    auto stage_in = [&](int st, int b) {
-      pend[b] = true;
-      if (tid != 0) return;
-      const int J = jlo + st;
-      const uint32_t dst = sBase + (uint32_t)b * Cfg::kStage;
-      const uint32_t lb = lmb + 8u * (uint32_t)b;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lb), "r"(Cfg::kStage) : "memory");
-      for (int d = 0; d < kD; ++d)
-        bulk_copy(dst + (uint32_t)d * Cfg::kABytes, A.d + tile_index(A, d, J, 2 * iI), Cfg::kABytes, lb);
-      for (int d = 0; d < kD; ++d)
-        bulk_copy(dst + kD * Cfg::kABytes + (uint32_t)d * Cfg::kBBytes,
-                  B.d + tile_index(B, d, J, n0 / kTR) + (size_t)(n0 % kTR) * kTK, Cfg::kBBytes, lb);
-    };
-    for (int q = 0; q < NS - 1 && q < nst; ++q) stage_in(q, q);
+    if (!prefetched)
+      for (int q = 0; q < NS - 1 && q < nst; ++q) stage_in(cur, q, q);
+    prefetched = false;
     for (int st = 0; st < nst; ++st) {
       const int b = st % NS;
       const bool lok = mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
@@ -312,37 +320,49 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
       }
       lphase[b] ^= 1u;
       pend[b] = false;
-      if (lane == 0 && warp < kIssuers) {
+      if (tid == 0) {
+        // fused levels: the B digit planes of a stage sit side by side (NT rows
+        // each, then the zero plane), so one product of A digit a against B
+        // digits b0 .. b0 + c - 1 (N = NT c <= 256) lands digit b in TMEM level
+        // a + b; the products of a = 0 reach every level (the zero plane stands
+        // for B digit 8) and open the window, so one thread issues them all
         fence_after();
         const bool fresh = (st % kWinTiles) == 0;
         const uint32_t aBase = sBase + (uint32_t)b * Cfg::kStage;
         const uint32_t bBase = aBase + kD * Cfg::kABytes;
-#pragma unroll 1
-        for (int q = 0; q < 3; ++q) {
-          const int L = owned_level<LV>(warp, q);
-          if (L < 0) continue;
-#pragma unroll 1
-          for (int a = L > 7 ? L - 7 : 0; a <= (L < 7 ? L : 7); ++a) {
+        constexpr int kMaxC = 256 / NT;
 #pragma unroll
-            for (int kk = 0; kk < kTK / 16; ++kk) {
+        for (int kk = 0; kk < kTK / 16; ++kk) {
+#pragma unroll
+          for (int a = 0; a < kD; ++a) {
+            const int nb = a == 0 ? LV : LV - a;  // B digits 0 .. nb - 1 (digit 8: the zero plane)
+#pragma unroll
+            for (int b0 = 0; b0 < nb; b0 += kMaxC) {
+              const int c = min(kMaxC, nb - b0);
               const uint64_t ad = mat_desc(aBase + (uint32_t)a * Cfg::kABytes + (uint32_t)kk * 256u, 128u, 512u);
-              const uint64_t bd = mat_desc(bBase + (uint32_t)(L - a) * Cfg::kBBytes + (uint32_t)kk * 256u, 128u, 512u);
-              const bool first = fresh && a == (L > 7 ? L - 7 : 0) && kk == 0;
-              mma_bf16(tmem + (uint32_t)(L * NT), ad, bd, Cfg::kIdesc, first ? 0u : 1u);
+              const uint64_t bd = mat_desc(bBase + (uint32_t)b0 * Cfg::kBBytes + (uint32_t)kk * 256u, 128u, 512u);
+              mma_bf16(tmem + (uint32_t)((a + b0) * NT), ad, bd, idesc_bf16(128, NT * c),
+                       (fresh && kk == 0 && a == 0) ? 0u : 1u);
             }
           }
         }
-        mma_commit(mb + 8u * (uint32_t)warp);
+        mma_commit(mb);
       }
       // the buffer of stage st - 1 (its products finished last round) takes stage st + NS - 1
-      if (st + NS - 1 < nst) stage_in(st + NS - 1, (st + NS - 1) % NS);
-      bool ok = true;
-      for (int q = 0; q < kIssuers; ++q) ok = mbar_wait(mb + 8u * q, phase) && ok;
+      if (st + NS - 1 < nst) stage_in(cur, st + NS - 1, (st + NS - 1) % NS);
+      const bool ok = mbar_wait(mb, phase);
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
       }
       phase ^= 1u;
+      if (st == nst - 1 && tt + gridDim.x < ntile) {
+        // every buffer is free: the next tile's first stages stream in during
+        // the drain and the epilogue of this one
+        const Tile nx = tile_of(tt + gridDim.x);
+        for (int q = 0; q < NS - 1 && q < nx.nst; ++q) stage_in(nx, q, q);
+        prefetched = true;
+      }
       if ((st % kWinTiles) == kWinTiles - 1 || st == nst - 1) {
         fence_after();
 #pragma unroll
@@ -404,7 +424,7 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
   if (failed) {
     if (tid == 0) {
       atomicExch(g.err, 1);
-      for (int q = 0; q < kIssuers; ++q) mbar_wait(mb + 8u * q, phase);
+      mbar_wait(mb, phase);
       for (int b = 0; b < NS; ++b)
         if (pend[b]) mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
     }
@@ -452,33 +472,33 @@ struct PanArgs {
                       // every reflector's largest entry)
   double* part;       // [3][G][kPartW]
   double* red;        // kRedTotal
-  unsigned* bar;      // [0] arrivals, [1] generation
+  unsigned* bar;      // this launch's arrival counter (zero at its start)
   int* err;
 };
 
 // Grid-wide barrier with a bounded wait: false once any CTA has given up.
+// *bar counts this launch's arrivals (every panel launch has a counter of its
+// own, zeroed at the start of the reduction); the k-th barrier completes when
+// it reaches k * gridDim.x, so a CTA waits for the multiple of gridDim.x at or
+// above its own arrival.
 __device__ bool grid_sync(unsigned* bar, int* err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g0 = *gen;
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*gen == g0) {
-        if (*(volatile int*)err != 0) break;
-        if (++spins > kSpin) {
-          atomicExch(err, 1);
-          break;
-        }
-        __nanosleep(64);
+    const unsigned target = (arrived + gridDim.x - 1) / gridDim.x * gridDim.x;
+    unsigned long long spins = 0;
+    for (;;) {
+      unsigned now;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(bar) : "memory");
+      if ((int)(now - target) >= 0) break;
+      if (*(volatile int*)err != 0) break;
+      if (++spins > kSpin) {
+        atomicExch(err, 1);
+        break;
       }
+      if (spins > 64) __nanosleep(32);
     }
     __threadfence();
     s_ok = (*(volatile int*)err == 0);
@@ -489,8 +509,8 @@ __device__ bool grid_sync(unsigned* bar, int* err) {
 
 // Sums with every thread of the CTA: out(e) = sum_k term(e, k) for e in
 // [e0, e1), k < count(e); tpe threads (a power of two <= 32, the largest with
-// tpe (e1 - e0) <= kPT) share an output, each taking every tpe-th k four at a
-// time, then a shuffle tree.  The order is fixed, so every CTA that forms the
+// tpe (e1 - e0) <= kPT) share an output, each taking every tpe-th k eight at
+// a time, then a shuffle tree.  The order is fixed, so every CTA that forms the
 // same sums gets the same bits.
 template <typename Count, typename Term, typename Store>
 __device__ __forceinline__ void block_sums(int e0, int e1, Count count, Term term, Store store) {
@@ -508,9 +528,11 @@ __device__ __forceinline__ void block_sums(int e0, int e1, Count count, Term ter
     if (act) {
       const int K = count(e);
       int k = sub;
-      for (; k + 3 * tpe < K; k += 4 * tpe) {
-        const double a0 = term(e, k), a1 = term(e, k + tpe), a2 = term(e, k + 2 * tpe), a3 = term(e, k + 3 * tpe);
-        acc += (a0 + a1) + (a2 + a3);
+      for (; k + 7 * tpe < K; k += 8 * tpe) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = term(e, k + q * tpe);
+        acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
       }
       for (; k < K; k += tpe) acc += term(e, k);
     }
@@ -839,7 +861,9 @@ struct RtcScratch {
   double* AV;       // ksY x (ldE x kMaxW)
   double* part;     // 3 x G x kPartW
   double* red;      // kRedTotal
-  unsigned* bar;    // [0..1] barrier, [2] error flag
+  unsigned* bar;    // [0..3]: [2] the error flag; then one arrival counter per panel launch
+  int nbar;         // panel-launch counters available
+  int panels;       // panel launches so far
   DigitMat erow, ecol, yrow, vrow, vcol, zcol;
   int G;
 };
@@ -874,7 +898,9 @@ size_t rtc_layout(int n, int p, unsigned char* base, RtcScratch* S) {
   s.AV = (double*)take(sizeof(double) * ksY * ldE * kMaxW);
   s.part = (double*)take(sizeof(double) * 3 * (size_t)G * kPartW);
   s.red = (double*)take(sizeof(double) * kRedTotal);
-  s.bar = (unsigned*)take(16);
+  s.nbar = n + 16;
+  s.panels = 0;
+  s.bar = (unsigned*)take(16 + sizeof(unsigned) * (size_t)s.nbar);
   auto dm = [&](int RT, int KT, bool ex) {
     DigitMat M;
     M.RT = RT;
@@ -959,8 +985,9 @@ GArgs gemm_args(const DigitMat& A, const DigitMat& B, int J0, int J1, int M0, in
 }
 
 // One mini-block: panel (cooperative), A V_s on the tensor cores, Y's new columns.
-int run_panel(const RtcScratch& S, int n, int p, double* P, long long ldp, int r0, int w, int wp, int pv0, int j,
+int run_panel(RtcScratch& S, int n, int p, double* P, long long ldp, int r0, int w, int wp, int pv0, int j,
               int c0, double* tau, cudaStream_t st) {
+  if (S.panels >= S.nbar) return SSV_EINVAL;
   const int L = n - r0;
   int G = std::min(S.G, std::max(1, (L + 15) / 16));
   const int rpc = (L + G - 1) / G;
@@ -985,7 +1012,7 @@ int run_panel(const RtcScratch& S, int n, int p, double* P, long long ldp, int r
   a.vcol = S.vcol;
   a.part = S.part;
   a.red = S.red;
-  a.bar = S.bar;
+  a.bar = S.bar + 4 + S.panels++;
   a.err = reinterpret_cast<int*>(S.bar + 2);
   const size_t smem = sizeof(double) * ((size_t)rpc * w + kPanFixed);
   SSV_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1088,7 +1115,7 @@ int reduce_tc(Handle* h, cudaStream_t st) {
       rc = e == cudaErrorMemoryAllocation ? SSV_ENOMEM : SSV_ECUDA;
     }
   };
-  cu(cudaMemsetAsync(S.bar, 0, 16, st));
+  cu(cudaMemsetAsync(S.bar, 0, 16 + sizeof(unsigned) * (size_t)S.nbar, st));
   if (p > 0)
     cu(cudaMemcpy2DAsync(S.E, sizeof(double) * S.ldE, h->Ct, sizeof(double) * ldct, sizeof(double) * p, n,
                          cudaMemcpyDeviceToDevice, st));

@@ -63,6 +63,9 @@ constexpr int kN = 32;        // real columns per shift (2m, zero-padded)
 #ifndef SSV_TC_BUFFERS
 #define SSV_TC_BUFFERS 1      // 2: the next stage streams in during the products
 #endif
+#ifndef SSV_TC_FUSED
+#define SSV_TC_FUSED 1        // 1: fused-level products in the two-shift kernel (24 per stage)
+#endif
 #ifndef SSV_TC_PAIRS
 #define SSV_TC_PAIRS 1        // 1: two shifts per work item (N = 64, one CTA per SM)
 #endif
@@ -504,6 +507,7 @@ constexpr uint32_t kStage2 = (uint32_t)kSl * (kAT + 2 * kBT) * 2;
 constexpr size_t kSmem2 = 2 * (size_t)kStage2 + 128;
 static_assert(kSmem2 <= 227 * 1024, "shared memory of the two-shift residual");
 static_assert(kLev * kN2 <= 512, "TMEM columns of the two-shift residual");
+constexpr int kWaitIss = SSV_TC_FUSED ? 1 : kIss;  // MMA barriers the two-shift kernel commits
 constexpr int kPairGroup = 8;  // pairs that resident CTAs take together (L2 sharing of H tiles)
 
 __device__ __forceinline__ void pair_coords(long long t, int RB, int np, int* I, int* w) {
@@ -615,6 +619,35 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
       lphase[b] ^= 1u;
       pend[b] = false;
       const int iss = tid >> 5;
+#if SSV_TC_FUSED
+      // fused levels: the B digit tiles of a stage sit side by side (64 rows
+      // each), so one product of H digit a against B digits b0 .. b0 + c - 1
+      // (N = 64 c <= 256) lands digit b in TMEM level a + b; 24 products per
+      // stage instead of 72.  The two products of a = 0 cover all eight
+      // levels and open the window, so one thread issues everything in order.
+      if (tid == 0) {
+        fence_after();
+        const bool fresh = (st % kWin) == 0;
+        const uint32_t aBase = sBase + (uint32_t)b * kStage2;
+        const uint32_t bBase = aBase + (uint32_t)(kSl * kAT * 2);
+        constexpr uint32_t kSbo = (uint32_t)kKG * 128u;
+#pragma unroll
+        for (int ks = 0; ks < kKS / 16; ++ks) {
+#pragma unroll
+          for (int da = 0; da < kSl; ++da) {
+#pragma unroll
+            for (int b0 = 0; b0 < kSl - da; b0 += 4) {
+              const int c = min(4, kSl - da - b0);
+              const uint64_t ad = mat_desc(aBase + (uint32_t)(da * kAT * 2 + ks * 256), 128u, kSbo);
+              const uint64_t bd = mat_desc(bBase + (uint32_t)(b0 * 2 * kBT * 2 + ks * 256), 128u, kSbo);
+              const bool first = fresh && ks == 0 && da == 0;
+              mma_bf16(tmem + (uint32_t)((da + b0) * kN2), ad, bd, idesc_bf16(kM, kN2 * c), first ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(mb);
+      }
+#else
       if ((tid & 31) == 0 && iss < kIss) {
         fence_after();
         const bool fresh = (st % kWin) == 0;
@@ -638,11 +671,13 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
         }
         mma_commit(mb + 8u * (uint32_t)iss);
       }
+#endif
+      (void)iss;
       // the next stage streams into the other buffer (its products finished
       // in the previous round)
       if (st + 1 < nst) stage_in(I, s0, s1, J0 + st + 1, b ^ 1);
       bool ok = true;
-      for (int q = 0; q < kIss; ++q) ok = mbar_wait(mb + 8u * q, phase) && ok;
+      for (int q = 0; q < kWaitIss; ++q) ok = mbar_wait(mb + 8u * q, phase) && ok;
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
@@ -706,7 +741,7 @@ __global__ void __launch_bounds__(kT2, 1) tc_residual2_kernel(
     // bounded wait, then release TMEM
     if (tid == 0) {
       atomicExch(err, 1);
-      for (int q = 0; q < kIss; ++q) mbar_wait(mb + 8u * q, phase);
+      for (int q = 0; q < kWaitIss; ++q) mbar_wait(mb + 8u * q, phase);
       for (int b = 0; b < 2; ++b)
         if (pend[b]) mbar_wait(lmb + 8u * (uint32_t)b, lphase[b]);
     }

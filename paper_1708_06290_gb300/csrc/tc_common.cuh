@@ -97,7 +97,7 @@ static __device__ __forceinline__ uint64_t mat_desc(uint32_t addr, uint32_t lbo,
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 // instruction descriptor of kind::f16: D F32, A and B BF16, both K-major, N, M
-constexpr uint32_t idesc_bf16(int M, int N) {
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
