@@ -95,7 +95,15 @@ constexpr int kLev = 8;              // levels k + l = 0 .. 7
 constexpr int kStages = kNBT / kKS;  // stages per block step
 constexpr int kAT = kUM * kKS;       // BF16 elements of one H digit tile
 constexpr int kBT = kUN * kKS;       // BF16 elements of one P1 digit tile
-constexpr uint32_t kStageBytes = (uint32_t)(kSDH * kAT + kSD * kBT) * 2;
+#ifndef SSV_TCS_FUSED
+#define SSV_TCS_FUSED 1  // 1: Z1 P1 as fused-level products (one per H digit and <= 256 columns)
+#endif
+// a stage: eight H digit tiles, seven P1 digit tiles and (fused form) one tile of
+// zeros standing for P1 digit 7, so that the H digit 0 products reach all levels
+constexpr int kBPlanes = SSV_TCS_FUSED ? kSD + 1 : kSD;
+constexpr uint32_t kStageBytes = (uint32_t)(kSDH * kAT + kBPlanes * kBT) * 2;
+constexpr uint32_t kLoadBytes = (uint32_t)(kSDH * kAT + kSD * kBT) * 2;  // copied per stage
+constexpr uint32_t kZeroOff = kLoadBytes;                                 // the zero tile in a stage
 constexpr int kIss = 4;              // threads issuing products (lane 0 of warps 0..3)
 constexpr uint32_t kIdescU = idesc_bf16(kUM, kUN);
 constexpr int kTmemCols = 8 * kUN;   // 8 levels x kUN columns
@@ -640,6 +648,14 @@ __global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int 
     for (int q = 0; q < kIss + 3; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb + 8u * q));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // the zero tiles of the stage buffers (fused form; the copies never write them)
+  auto zero_tile = [&](int b) {
+    if (!SSV_TCS_FUSED) return;
+    uint4* zp = reinterpret_cast<uint4*>(smem + (size_t)b * kStageBytes + kZeroOff);
+    for (int e = tid; e < kBT * 2 / 16; e += kUT) zp[e] = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  };
+  for (int b = 0; b < kBufU; ++b) zero_tile(b);
   fence_before();
   __syncthreads();
   fence_after();
@@ -658,7 +674,7 @@ __global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int 
   auto stage_in = [&](int I, int g, int st, int b) {
     const uint32_t dst = sBase + (uint32_t)b * kStageBytes;
     const uint32_t lmb = lmb0 + 8u * (uint32_t)b;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lmb), "r"(kStageBytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lmb), "r"(kLoadBytes)
                  : "memory");
     for (int l = 0; l < kSDH; ++l)
       bulk_copy(dst + (uint32_t)(l * kAT * 2),
@@ -716,6 +732,38 @@ __global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int 
       lphase[buf] ^= 1u;
       pend[buf] = false;
       const int iss = tid >> 5;
+#if SSV_TCS_FUSED
+      // fused levels: the P1 digit tiles sit side by side (kUN rows each, then
+      // the zero tile), so one product of H digit kd against P1 digits
+      // b0 .. b0 + c - 1 (N = kUN c <= 256) lands digit b in TMEM level kd + b;
+      // the kd = 0 products cover every level and open the item, so one thread
+      // issues all of them, and commits to every issuer barrier (their phases
+      // stay in step with the Z2 P2 round)
+      (void)iss;
+      if (tid == 0) {
+        fence_after();
+        const uint32_t aBase = sBase + (uint32_t)buf * kStageBytes;
+        const uint32_t bBase = aBase + (uint32_t)(kSDH * kAT * 2);
+        constexpr uint32_t kSbo = (uint32_t)kKG * 128u;
+        constexpr int kMaxC = 256 / kUN;
+#pragma unroll
+        for (int ks = 0; ks < kKS / 16; ++ks) {
+#pragma unroll
+          for (int kd = 0; kd < kSDH; ++kd) {
+            const int nb = kd == 0 ? kLev : min(kSD, kLev - kd);  // P1 digits (7: the zero tile)
+#pragma unroll
+            for (int b0 = 0; b0 < nb; b0 += kMaxC) {
+              const int c = min(kMaxC, nb - b0);
+              const uint64_t ad = mat_desc(aBase + (uint32_t)(kd * kAT * 2 + ks * 256), 128u, kSbo);
+              const uint64_t bd = mat_desc(bBase + (uint32_t)(b0 * kBT * 2 + ks * 256), 128u, kSbo);
+              const bool first = st == 0 && ks == 0 && kd == 0;
+              mma_bf16(tmem + (uint32_t)((kd + b0) * kUN), ad, bd, idesc_bf16(kUM, kUN * c), first ? 0u : 1u);
+            }
+          }
+        }
+        for (int q = 0; q < kIss; ++q) mma_commit(mb + 8u * (uint32_t)q);
+      }
+#else
       if ((tid & 31) == 0 && iss < kIss) {
         fence_after();
         const uint32_t aBase = sBase + (uint32_t)buf * kStageBytes;
@@ -738,6 +786,7 @@ __global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int 
         }
         mma_commit(mb + 8u * (uint32_t)iss);
       }
+#endif
       // the next stage streams into the other buffer, whose products finished
       // in the previous round (with one buffer: after these products)
       if (kBufU == 2 && st + 1 < nst) {
@@ -840,6 +889,11 @@ __global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int 
         break;
       }
       mphase ^= 1u;
+      // the Z2 / P2 tiles covered buffer 0's zero tile: write it again before
+      // the next item's first products read it (ordered by the load wait and
+      // barrier that precede them)
+      for (int b = 0; b < kBufU; ++b)
+        if ((size_t)b * kStageBytes + kZeroOff < (size_t)S * (zbytes + pbytes)) zero_tile(b);
     }
     // ---- 3. the stage buffers are free again: the next item's first stage
     //      streams in during the rest of the epilogue
