@@ -577,14 +577,14 @@ __global__ void __launch_bounds__(kPT, 3) tcs_panel_kernel(TcsArgs a, int k, int
 // the level sums of one thread's 16 TMEM columns (lane = its row), each level t
 // scaled by 2^{-7 (t + 2)} and added into double-float sums
 static __device__ __forceinline__ void drain_levels(uint32_t tl, int nlev, float (&ah)[16],
-                                                    float (&al)[16]) {
+                                                    float (&al)[16], int lstride = kUN) {
 #pragma unroll
   for (int c = 0; c < 16; ++c) { ah[c] = 0.f; al[c] = 0.f; }
   float sc = 0.0078125f * 0.0078125f;  // 2^{-7 (t + 2)}, t = 0
 #pragma unroll 1
   for (int lv = 0; lv < nlev; ++lv) {
     uint32_t rr[16];
-    tmem_ld16(tl + (uint32_t)(lv * kUN), rr);
+    tmem_ld16(tl + (uint32_t)(lv * lstride), rr);
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const float pv = __uint_as_float(rr[c]) * sc;
@@ -857,6 +857,32 @@ __global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int 
       l2phase ^= 1u;
       pend2 = false;
       const int iss = tid >> 5;
+#if SSV_TCS_FUSED
+      // fused levels: shift l's seven levels sit side by side in TMEM (columns
+      // 7 cs l + cs lv) and its P2 digit tiles (cs rows each) are stacked, so one
+      // product of Z2 digit kd against P2 digits 0 .. 6 - kd (N = cs (7 - kd))
+      // lands digit ld in level kd + ld; kd = 0 opens all seven
+      (void)iss;
+      if (tid == 0) {
+        fence_after();
+        const uint32_t sboz = (uint32_t)kgz * 128u;
+        for (int l = 0; l < nsh; ++l) {
+          const uint32_t zb = sBase + (uint32_t)l * zbytes;
+          const uint32_t pb = sBase + (uint32_t)S * zbytes + (uint32_t)l * pbytes;
+#pragma unroll 1
+          for (int ks = 0; ks < cs / 16; ++ks) {
+#pragma unroll
+            for (int kd = 0; kd < 7; ++kd) {
+              const uint64_t ad = mat_desc(zb + (uint32_t)(kd * 128 * cs * 2 + ks * 256), 128u, sboz);
+              const uint64_t bd = mat_desc(pb + (uint32_t)(ks * 256), 128u, sboz);
+              mma_bf16(tmem + (uint32_t)(7 * cs * l + kd * cs), ad, bd, idesc_bf16(kUM, cs * (7 - kd)),
+                       (kd == 0 && ks == 0) ? 0u : 1u);
+            }
+          }
+        }
+        for (int q = 0; q < kIss; ++q) mma_commit(mb + 8u * (uint32_t)q);
+      }
+#else
       if ((tid & 31) == 0 && iss < kIss) {
         fence_after();
         const uint32_t idz = idesc_bf16(kUM, cs);
@@ -882,6 +908,7 @@ __global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int 
         }
         mma_commit(mb + 8u * (uint32_t)iss);
       }
+#endif
       bool ok = true;
       for (int q = 0; q < kIss; ++q) ok = mbar_wait(mb + 8u * q, mphase, kUpdWait) && ok;
       if (__syncthreads_or(!ok)) {
@@ -905,7 +932,14 @@ __global__ void __launch_bounds__(kUT, kCtasU) tcs_update_kernel(TcsArgs a, int 
     if (TCZ) {
       fence_after();
       float ah[16], al[16];
+#if SSV_TCS_FUSED
+      // shift l = (16 qt) / cs: its levels start at column 7 cs l, this
+      // quarter's columns at (16 qt) mod cs within them
+      drain_levels(tl - (uint32_t)(qt * 16) + (uint32_t)(7 * cs * ((qt * 16) / cs) + (qt * 16) % cs), 7, ah, al,
+                   cs);
+#else
       drain_levels(tl, 7, ah, al);
+#endif
       const int l = (qt * 16) / cs;  // one shift per quarter (cs >= 16)
       const int sh = g * S + l;
       const int Ez = (live && sh < a.s) ? a.zexp[BCK((size_t)sh * a.npad + ih, (size_t)a.s * a.npad)] : 0;
