@@ -6,16 +6,18 @@
 //
 // Arithmetic of the products.  An operand row (or column) is scaled by the
 // power of two 2^E above its largest magnitude and cut into eight 7-bit
-// digits (56 bits, more than FP64's 53).  A digit pair (a, b) of one K = 16
-// slice is one tcgen05.mma of kind::f16 into FP32 TMEM; pairs with a + b = t
-// accumulate in level t.  The rank-b updates keep t = 0..7 (36 pairs; the
+// digits (56 bits, more than FP64's 53).  The product of digit pair (a, b)
+// over one K = 16 slice is a tcgen05.mma of kind::f16 into FP32 TMEM; pairs
+// with a + b = t accumulate in level t.  The rank-b updates keep t = 0..7 (36 pairs; the
 // dropped pairs weigh below 2^-53 of the product's scale, the row maximum
 // times the column maximum); the long-K products A V_s and V^T A keep
 // t = 0..8 (43 pairs, dropped part below 2^-60): their terms mostly sit far
 // below that scale, and with eight levels their error grew to about ten
-// times an FP64 product's.  A level's sums are integers below 2^24 for
-// K <= 128 (8 pairs x 128 x 127^2 < 2^24), hence exact in FP32;
-// after each window of 128 the levels are added exactly into 64-bit
+// times an FP64 product's.  One instruction serves several pairs: the B digit
+// tiles of a stage sit side by side, so A digit a against B digits b0 .. b0+c-1
+// (N c <= 256 columns) lands digit b in level a + b (fused levels).  A level's
+// sums are integers below 2^24 for K <= 128 (8 pairs x 128 x 127^2 < 2^24),
+// hence exact in FP32; after each window of 128 the levels are added exactly into 64-bit
 // fixed-point words (levels 0-3, 4-7 and 8; a window adds below 2^46 to a
 // word), kept across the whole K range and turned into FP64 once per output.
 //
@@ -199,7 +201,6 @@ struct GCfg {
   static constexpr size_t kSmem = kNS * (size_t)kStage + 256;
   static constexpr uint32_t kUsed = (uint32_t)LV * NT;
   static constexpr uint32_t kCols = kUsed <= 32 ? 32 : kUsed <= 64 ? 64 : kUsed <= 128 ? 128 : kUsed <= 256 ? 256 : 512;
-  static constexpr uint32_t kIdesc = idesc_bf16(128, NT);
   static_assert(kSmem <= 227 * 1024, "shared memory of the digit product");
   static_assert(kUsed <= 512, "TMEM columns");
   static_assert(LV == 8 || LV == 9, "levels");
