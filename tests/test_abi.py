@@ -70,6 +70,14 @@ def test_argument_validation_needs_no_gpu(lib):
     assert lib.ssv_reduce(4, 2, -1, fake, 4, fake, 4, fake, 1, None, ctypes.byref(h)) == ssv.SSV_EINVAL
     assert lib.ssv_reduce(4, 2, 1, fake, 3, fake, 4, fake, 1, None, ctypes.byref(h)) == ssv.SSV_EINVAL
     assert lib.ssv_reduce(4, 2, 1, fake, 4, fake, 4, fake, 1, None, None) == ssv.SSV_EINVAL
+    # the arithmetic of the reduction's products: FP64 pipe or tensor cores, nothing else
+    for arith in (-1, 2, 7):
+        assert lib.ssv_reduce_arith(4, 2, 1, fake, 4, fake, 4, fake, 1, arith, None,
+                                    ctypes.byref(h)) == ssv.SSV_EINVAL
+    assert lib.ssv_reduce_arith(0, 1, 1, fake, 1, fake, 1, fake, 1, ssv.REDUCE_TENSOR, None,
+                                ctypes.byref(h)) == ssv.SSV_EINVAL
+    assert lib.ssv_reduce_arith(4, 2, 1, fake, 3, fake, 4, fake, 1, ssv.REDUCE_TENSOR, None,
+                                ctypes.byref(h)) == ssv.SSV_EINVAL
     assert lib.ssv_solve(None, 1, fake, None, fake, 4, None, None, None) == ssv.SSV_EINVAL
     assert lib.ssv_apply_q(None, 1, fake, 4, fake, 4, None) == ssv.SSV_EINVAL
     bad = ssv.Opts()
