@@ -325,7 +325,8 @@ def batching_measurement(ssv, dev, args):
     """The batching workload: 64 systems, n ~ U{200..3000}, m in {1,2,4,8},
     16..512 shifts each; n_b autotuned per system, then one batch plan per
     precision (FP64, double-float) captured in a CUDA graph and replayed
-    (median of 3 replays); reductions and tuning untimed."""
+    (median of 3 replays); the mixed path through ssv_solve_many; reductions
+    and tuning untimed."""
     import torch
 
     work = W.workload_batching()
@@ -358,6 +359,27 @@ def batching_measurement(ssv, dev, args):
                      "nb_tuned": sorted(set(tuned)), "nonzero_status": bad}
         plan.close()
         del g
+    # the mixed path (certified per shift): ssv_solve_many runs the systems' mixed solves
+    # back to back; the mixed path takes its scratch per call, so it is timed directly
+    # (median of 3), not replayed from a graph.  An extra measurement: a failure is
+    # reported on the line, not raised.
+    try:
+        ssv.solve_many(handles, shifts, mode="g", precision="mixed", stream=stream)
+        torch.cuda.synchronize()
+        ts, bad = [], 0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, sts = ssv.solve_many(handles, shifts, mode="g", precision="mixed", stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            bad = int(sum(int((x != 0).sum()) for x in sts))
+        ms = float(np.median(ts))
+        res["mixed"] = {"ms": round(ms, 3), "shift_solves_per_s": round(total / (ms * 1e-3), 1),
+                        "graph_replay": False, "nonzero_status": bad}
+    except Exception as exc:  # noqa: BLE001
+        res["mixed"] = {"error": str(exc)[:200]}
     for h in handles:
         h.close()
     return res
