@@ -68,22 +68,49 @@ constexpr int kGT = 256;                 // threads of the product kernel
 constexpr int kIssuers = 1;              // MMA completion barriers (one issuing thread)
 constexpr unsigned long long kSpin = 1ull << 26;  // grid barrier naps before giving up
 
+// Debug builds (-DSSV_BOUNDS_CHECK): every global index of these kernels is
+// checked against its buffer's extent; one out of range is clamped to 0 (a
+// bulk copy then stays inside its buffer) and sets bit 2 of the error word,
+// so the reduction fails.  The scratch is filled with NaN before use and a
+// canary after it is verified at the end.  In normal builds RBCK(i, n, e) is i.
+#ifdef SSV_BOUNDS_CHECK
+__device__ __forceinline__ size_t rbck(long long i, size_t n, int* err) {
+  if (i < 0 || (size_t)i >= n) {
+    if (err) atomicOr(err, 2);
+    return 0;
+  }
+  return (size_t)i;
+}
+// [i, i + len) inside [0, n)
+__device__ __forceinline__ size_t rbcr(long long i, long long len, size_t n, int* err) {
+  if (i < 0 || (size_t)(i + len) > n) {
+    if (err) atomicOr(err, 2);
+    return 0;
+  }
+  return (size_t)i;
+}
+#define RBCK(i, n, e) rbck((long long)(i), (size_t)(n), (e))
+#define RBCR(i, len, n, e) rbcr((long long)(i), (long long)(len), (size_t)(n), (e))
+#else
+#define RBCK(i, n, e) ((size_t)(i))
+#define RBCR(i, len, n, e) ((size_t)(i))
+#endif
+
 // Digit tiles of an R x K operand (R rows, each scaled by 2^ex[r]): tile
 // (digit, J, I) holds rows 64 I .. 64 I + 63 and K 32 J .. 32 J + 31, the
 // tiles of one (digit, J) consecutive in I, so that two neighbours are the
 // 128-row A operand of one product.
 struct DigitMat {
   unsigned short* d;
-  int* ex;  // per row; null: the fixed exponent 1
-  int RT;   // 64-row tiles (even)
-  int KT;   // 32-wide K tiles
+  int* ex;    // per row; null: the fixed exponent 1
+  int RT;     // 64-row tiles (even)
+  int KT;     // 32-wide K tiles
+  size_t nd;  // BF16 values in d (the extent the debug build checks)
 };
 
 __host__ __device__ __forceinline__ size_t tile_index(const DigitMat& M, int dig, int J, int I) {
   return (((size_t)dig * M.KT + J) * M.RT + I) * kTileEl;
 }
-
-__device__ __forceinline__ int exp_of(const int* ex, int r) { return ex ? ex[r] : 1; }
 
 // bit pattern of the BF16 digit `l` of x at exponent E
 __device__ __forceinline__ void digits_of(double x, int E, unsigned short (&d)[kD]) { digits8(x, E, d); }
@@ -96,7 +123,8 @@ __device__ __forceinline__ void digits_of(double x, int E, unsigned short (&d)[k
 // exponent pass: ex[r] = max over the K range of scale_exp(|x|) (ex preset to INT_MIN)
 __global__ void __launch_bounds__(256) split_exp_kernel(const double* __restrict__ src, long long sr,
                                                         long long sk, int r_lo, int r_hi, int k_lo,
-                                                        int k_hi, int kchunk, int* __restrict__ ex) {
+                                                        int k_hi, int kchunk, int* __restrict__ ex,
+                                                        size_t nsrc, size_t nex, int* err) {
   const int tid = threadIdx.x;
   const int rb = r_lo + blockIdx.x * 64;
   const int kb = k_lo + blockIdx.y * kchunk;
@@ -108,9 +136,9 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const double* __restrict
       const int r = rb + rr;
       if (r >= r_hi) break;
       double mx = 0.0;
-      for (int k = kb + lane; k < ke; k += 32) mx = fmax(mx, fabs(src[(size_t)r * sr + k]));
+      for (int k = kb + lane; k < ke; k += 32) mx = fmax(mx, fabs(src[RBCK((size_t)r * sr + k, nsrc, err)]));
       for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) atomicMax(ex + r, scale_exp(mx));
+      if (lane == 0) atomicMax(ex + RBCK(r, nex, err), scale_exp(mx));
     }
   } else {
     // rows contiguous (sr == 1 in every use): threads along rows, four K groups
@@ -119,12 +147,13 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const double* __restrict
     const int r = rb + rr;
     double mx = 0.0;
     if (r < r_hi)
-      for (int k = kb + g; k < ke; k += 4) mx = fmax(mx, fabs(src[(size_t)r * sr + (size_t)k * sk]));
+      for (int k = kb + g; k < ke; k += 4)
+        mx = fmax(mx, fabs(src[RBCK((size_t)r * sr + (size_t)k * sk, nsrc, err)]));
     part[g][rr] = mx;
     __syncthreads();
     if (g == 0 && r < r_hi) {
       mx = fmax(fmax(part[0][rr], part[1][rr]), fmax(part[2][rr], part[3][rr]));
-      atomicMax(ex + r, scale_exp(mx));
+      atomicMax(ex + RBCK(r, nex, err), scale_exp(mx));
     }
   }
 }
@@ -132,7 +161,8 @@ __global__ void __launch_bounds__(256) split_exp_kernel(const double* __restrict
 // digit pass: one CTA per tile (I, J) of [I0, I0 + gridDim.x) x [J0, J0 + gridDim.y)
 __global__ void __launch_bounds__(256) split_dig_kernel(const double* __restrict__ src, long long sr,
                                                         long long sk, int r_lo, int r_hi, int k_lo,
-                                                        int k_hi, DigitMat M, int I0, int J0) {
+                                                        int k_hi, DigitMat M, int I0, int J0, size_t nsrc,
+                                                        size_t nex, int* err) {
   __shared__ double t[kTR][kTK + 1];
   const int tid = threadIdx.x;
   const int I = I0 + blockIdx.x, J = J0 + blockIdx.y;
@@ -143,13 +173,13 @@ __global__ void __launch_bounds__(256) split_dig_kernel(const double* __restrict
     else { rr = e % kTR; kk = e / kTR; }
     const int r = rb + rr, k = kb + kk;
     double v = 0.0;
-    if (r >= r_lo && r < r_hi && k >= k_lo && k < k_hi) v = src[(size_t)r * sr + (size_t)k * sk];
+    if (r >= r_lo && r < r_hi && k >= k_lo && k < k_hi) v = src[RBCK((size_t)r * sr + (size_t)k * sk, nsrc, err)];
     t[rr][kk] = v;
   }
   __syncthreads();
   const int rr = tid >> 2, kq = (tid & 3) * 8;
   const int r = rb + rr;
-  int E = (r >= r_lo && r < r_hi) ? exp_of(M.ex, r) : 0;
+  int E = (r >= r_lo && r < r_hi) ? (M.ex ? M.ex[RBCK(r, nex, err)] : 1) : 0;
   if (E < -4000) E = 0;  // a row with an empty K range (all of its values are 0)
   unsigned short dg[8][kD];
 #pragma unroll
@@ -162,7 +192,7 @@ __global__ void __launch_bounds__(256) split_dig_kernel(const double* __restrict
     v.y = (unsigned)dg[2][l] | ((unsigned)dg[3][l] << 16);
     v.z = (unsigned)dg[4][l] | ((unsigned)dg[5][l] << 16);
     v.w = (unsigned)dg[6][l] | ((unsigned)dg[7][l] << 16);
-    *reinterpret_cast<uint4*>(M.d + tile_index(M, l, J, I) + off) = v;
+    *reinterpret_cast<uint4*>(M.d + RBCR(tile_index(M, l, J, I) + off, 8, M.nd, err)) = v;
   }
 }
 
@@ -182,6 +212,7 @@ struct GArgs {
   int M0, M1, N0, N1;
   int roff, coff;
   double* C;
+  size_t nc;  // doubles from C on (the extent the debug build checks)
   long long ldc;
   int sub;
   int ksplit;
@@ -291,10 +322,12 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
                  "r"(Cfg::kStage - Cfg::kBBytes)
                  : "memory");
     for (int d = 0; d < kD; ++d)
-      bulk_copy(dst + (uint32_t)d * Cfg::kABytes, A.d + tile_index(A, d, J, 2 * t.iI), Cfg::kABytes, lb);
+      bulk_copy(dst + (uint32_t)d * Cfg::kABytes,
+                A.d + RBCR(tile_index(A, d, J, 2 * t.iI), 2 * kTileEl, A.nd, g.err), Cfg::kABytes, lb);
     for (int d = 0; d < kD; ++d)
       bulk_copy(dst + kD * Cfg::kABytes + (uint32_t)d * Cfg::kBBytes,
-                B.d + tile_index(B, d, J, t.n0 / kTR) + (size_t)(t.n0 % kTR) * kTK, Cfg::kBBytes, lb);
+                B.d + RBCR(tile_index(B, d, J, t.n0 / kTR) + (size_t)(t.n0 % kTR) * kTK, NT * kTK, B.nd, g.err),
+                Cfg::kBBytes, lb);
   };
   bool prefetched = false;  // the first stages of this CTA's next tile are already in flight
   for (long long tt = blockIdx.x; tt < ntile && !failed; tt += gridDim.x) {
@@ -385,13 +418,13 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
     // epilogue: word w weighs 2^{Ea + Eb - 35 - 28 w}; all loads of C first
     const int r = i0 + quarter * 32 + lane;
     if (r >= g.M0 && r < g.M1) {
-      const int Ea = exp_of(A.ex, r);
-      double* Cr = g.C + (size_t)ks * g.kstride + (long long)(r + g.roff);
+      const int Ea = A.ex ? A.ex[RBCK(r, (size_t)A.RT * kTR, g.err)] : 1;
+      const size_t c0 = (size_t)ks * g.kstride + (size_t)(r + g.roff);  // C offset of column 0
       double x[CPT];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         const int col = n0 + half * CPT + c;
-        const int Eb = (col >= g.N0 && col < g.N1) ? exp_of(B.ex, col) : 0;
+        const int Eb = (col >= g.N0 && col < g.N1) ? (B.ex ? B.ex[RBCK(col, (size_t)B.RT * kTR, g.err)] : 1) : 0;
         double v = 0.0;
         if (Ea == kBadExp || Eb == kBadExp) {
           v = __longlong_as_double(0x7ff8000000000000LL);
@@ -401,23 +434,24 @@ __global__ void __launch_bounds__(kGT, 1) tc_gemm_kernel(GArgs g) {
         }
         x[c] = v;
       }
+      auto cidx = [&](int col) { return RBCK(c0 + (long long)(col + g.coff) * g.ldc, g.nc, g.err); };
       if (g.sub) {
         double old[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
           const int col = n0 + half * CPT + c;
-          old[c] = (col >= g.N0 && col < g.N1) ? Cr[(long long)(col + g.coff) * g.ldc] : 0.0;
+          old[c] = (col >= g.N0 && col < g.N1) ? g.C[cidx(col)] : 0.0;
         }
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
           const int col = n0 + half * CPT + c;
-          if (col >= g.N0 && col < g.N1) Cr[(long long)(col + g.coff) * g.ldc] = old[c] - x[c];
+          if (col >= g.N0 && col < g.N1) g.C[cidx(col)] = old[c] - x[c];
         }
       } else {
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
           const int col = n0 + half * CPT + c;
-          if (col >= g.N0 && col < g.N1) Cr[(long long)(col + g.coff) * g.ldc] = x[c];
+          if (col >= g.N0 && col < g.N1) g.C[cidx(col)] = x[c];
         }
       }
     }
@@ -475,6 +509,8 @@ struct PanArgs {
   double* red;        // kRedTotal
   unsigned* bar;      // this launch's arrival counter (zero at its start)
   int* err;
+  // extents (doubles from each pointer on) the debug build checks
+  size_t np, nv, ny, ntau, npart;
 };
 
 // Grid-wide barrier with a bounded wait: false once any CTA has given up.
@@ -542,12 +578,13 @@ __device__ __forceinline__ void block_sums(int e0, int e1, Count count, Term ter
   }
 }
 
-__device__ __forceinline__ void put_digits_v(const DigitMat& M, int row, int k, double v) {
+__device__ __forceinline__ void put_digits_v(const DigitMat& M, int row, int k, double v, int* err) {
   unsigned short d[kD];
   digits_of(v, 1, d);
   const size_t off = (size_t)tile_off_kg(row % kTR, k % kTK, kTK / 8);
 #pragma unroll
-  for (int l = 0; l < kD; ++l) M.d[tile_index(M, l, k / kTK, row / kTR) + off] = d[l];
+  for (int l = 0; l < kD; ++l) M.d[RBCK(tile_index(M, l, k / kTK, row / kTR) + off, M.nd, err)] = d[l];
+  (void)err;
 }
 
 __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
@@ -568,24 +605,31 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
   double* taus = piv + 64;
   double* misc = taus + 64;
   double* tw = misc + 8;                 // 8 warps x kBmax: a row of T
-  auto slot = [&](int q, int gg) { return a.part + ((size_t)q * G + gg) * kPartW; };
+  auto slot = [&](int q, int gg) { return a.part + RBCR(((size_t)q * G + gg) * kPartW, kPartW, a.npart, a.err); };
+  // checked element accesses (plain indexing in normal builds)
+  auto Pi = [&](long long i) -> double& { return a.P[RBCK(i, a.np, a.err)]; };
+  auto Vi = [&](long long i) -> double& { return a.V[RBCK(i, a.nv, a.err)]; };
+  auto Ti = [&](long long i) -> double& { return a.T[RBCK(i, (size_t)kBmax * kBmax, a.err)]; };
+  auto Ri = [&](long long i) { return a.red + RBCK(i, (size_t)kRedTotal, a.err); };
+  // partial e of CTA gg in slot q
+  auto Pt = [&](int q, int gg, int e) { return a.part + RBCK(((size_t)q * G + gg) * kPartW + e, a.npart, a.err); };
 
   for (int e = tid; e < nr * w; e += kPT) {
     const int rl = e % nr, t = e / nr;
-    Ps[t * rpc + rl] = a.P[(size_t)(ra + rl) + (size_t)t * a.ldp];
+    Ps[t * rpc + rl] = Pi((size_t)(ra + rl) + (size_t)t * a.ldp);
   }
   if (j > 0) {
     // from the right: P -= Y(rows, 0:j) V(c0:c0+w, 0:j)^T
     for (int e = tid; e < w * j; e += kPT) {
       const int t = e % w, i = e / w;
-      Vc[t * j + i] = a.V[(size_t)(a.c0 + t) + (size_t)i * a.ldv];
+      Vc[t * j + i] = Vi((size_t)(a.c0 + t) + (size_t)i * a.ldv);
     }
     __syncthreads();
     for (int e = tid; e < nr * w; e += kPT) {
       const int rl = e % nr, t = e / nr;
-      const double* yr = a.Y + a.yoff + ra + rl;
+      const size_t y0 = (size_t)a.yoff + ra + rl;
       double acc = Ps[t * rpc + rl];
-      for (int i = 0; i < j; ++i) acc = fma(-yr[(size_t)i * a.ldy], Vc[t * j + i], acc);
+      for (int i = 0; i < j; ++i) acc = fma(-a.Y[RBCK(y0 + (size_t)i * a.ldy, a.ny, a.err)], Vc[t * j + i], acc);
       Ps[t * rpc + rl] = acc;
     }
     __syncthreads();
@@ -593,31 +637,30 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
     double* my = slot(0, g);
     for (int e = tid; e < j * w; e += kPT) {
       const int i = e / w, t = e % w;
-      const double* vr = a.V + ra + (size_t)i * a.ldv;
+      const size_t v0 = (size_t)ra + (size_t)i * a.ldv;
       double acc = 0.0;
-      for (int rl = 0; rl < nr; ++rl) acc = fma(vr[rl], Ps[t * rpc + rl], acc);
-      my[e] = acc;
+      for (int rl = 0; rl < nr; ++rl) acc = fma(Vi(v0 + rl), Ps[t * rpc + rl], acc);
+      my[RBCK(e, kPartW, a.err)] = acc;
     }
     if (!grid_sync(a.bar, a.err)) return;
     const int ch = (j * w + G - 1) / G;
     const int e0 = min(j * w, g * ch), e1 = min(j * w, (g + 1) * ch);
-    const double* s0 = slot(0, 0);
     block_sums(
-        e0, e1, [&](int) { return G; }, [&](int e, int gg) { return __ldcg(s0 + (size_t)gg * kPartW + e); },
-        [&](int e, double v) { a.red[kRedW + e] = v; });
+        e0, e1, [&](int) { return G; }, [&](int e, int gg) { return __ldcg(Pt(0, gg, e)); },
+        [&](int e, double v) { *Ri(kRedW + e) = v; });
     if (!grid_sync(a.bar, a.err)) return;
     block_sums(
         e0, e1, [&](int e) { return e / w + 1; },
-        [&](int e, int k) { return a.T[k + (size_t)(e / w) * kBmax] * __ldcg(a.red + kRedW + k * w + e % w); },
-        [&](int e, double v) { a.red[kRedZ + e] = v; });
+        [&](int e, int k) { return Ti(k + (size_t)(e / w) * kBmax) * __ldcg(Ri(kRedW + k * w + e % w)); },
+        [&](int e, double v) { *Ri(kRedZ + e) = v; });
     if (!grid_sync(a.bar, a.err)) return;
-    for (int e = tid; e < j * w; e += kPT) Zs[e] = __ldcg(a.red + kRedZ + e);
+    for (int e = tid; e < j * w; e += kPT) Zs[e] = __ldcg(Ri(kRedZ + e));
     __syncthreads();
     for (int e = tid; e < nr * w; e += kPT) {
       const int rl = e % nr, t = e / nr;
-      const double* vr = a.V + ra + rl;
+      const size_t v0 = (size_t)ra + rl;
       double acc = Ps[t * rpc + rl];
-      for (int i = 0; i < j; ++i) acc = fma(-vr[(size_t)i * a.ldv], Zs[i * w + t], acc);
+      for (int i = 0; i < j; ++i) acc = fma(-Vi(v0 + (size_t)i * a.ldv), Zs[i * w + t], acc);
       Ps[t * rpc + rl] = acc;
     }
   }
@@ -638,15 +681,15 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
       rs[grp * 64 + kk] = acc;
       __syncthreads();
       if (tid < nk) slot(t & 1, g)[tid] = rs[tid] + rs[64 + tid] + rs[128 + tid] + rs[192 + tid];
-      if (pr >= ra && pr < ra + nr && tid < nk) a.red[kRedPiv + (t & 1) * 64 + tid] = Ps[(size_t)(t + tid) * rpc + (pr - ra)];
+      if (pr >= ra && pr < ra + nr && tid < nk) *Ri(kRedPiv + (t & 1) * 64 + tid) = Ps[(size_t)(t + tid) * rpc + (pr - ra)];
     }
     if (!grid_sync(a.bar, a.err)) return;
     {
-      const double* sq = slot(t & 1, 0);
+      const int q = t & 1;
       block_sums(
-          0, nk, [&](int) { return G; }, [&](int e, int gg) { return __ldcg(sq + (size_t)gg * kPartW + e); },
+          0, nk, [&](int) { return G; }, [&](int e, int gg) { return __ldcg(Pt(q, gg, e)); },
           [&](int e, double v) { dots[e] = v; });
-      if (tid < nk) piv[tid] = __ldcg(a.red + kRedPiv + (t & 1) * 64 + tid);
+      if (tid < nk) piv[tid] = __ldcg(Ri(kRedPiv + (t & 1) * 64 + tid));
     }
     __syncthreads();
     if (tid == 0) {
@@ -662,7 +705,7 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
       misc[1] = scal;
       misc[2] = beta;
       taus[t] = tk;
-      if (g == 0) a.tau[t] = tk;
+      if (g == 0) a.tau[RBCK(t, a.ntau, a.err)] = tk;
     }
     __syncthreads();
     const double tk = misc[0], scal = misc[1], beta = misc[2];
@@ -689,7 +732,7 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
   // the panel back, the new columns of V (values and digits)
   for (int e = tid; e < nr * w; e += kPT) {
     const int rl = e % nr, t = e / nr;
-    a.P[(size_t)(ra + rl) + (size_t)t * a.ldp] = Ps[t * rpc + rl];
+    Pi((size_t)(ra + rl) + (size_t)t * a.ldp) = Ps[t * rpc + rl];
   }
   auto vt = [&](int rl, int t) -> double {
     const int r = ra + rl, pr = a.pv0 + t;
@@ -698,8 +741,8 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
   for (int e = tid; e < nr * wp; e += kPT) {
     const int rl = e % nr, t = e / nr;
     const double v = vt(rl, t);
-    a.V[(size_t)(ra + rl) + (size_t)(j + t) * a.ldv] = v;
-    if (v != 0.0) put_digits_v(a.vcol, j + t, ra + rl, v);
+    Vi((size_t)(ra + rl) + (size_t)(j + t) * a.ldv) = v;
+    if (v != 0.0) put_digits_v(a.vcol, j + t, ra + rl, v, a.err);
   }
   // S = V(:, 0:j+wp)^T V_s over the panel rows
   const int ns = (j + wp) * wp;
@@ -707,30 +750,30 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
     const int i = e / wp, t = e % wp;
     double acc = 0.0;
     if (i < j) {
-      const double* vr = a.V + ra + (size_t)i * a.ldv;
-      for (int rl = 0; rl < nr; ++rl) acc = fma(vr[rl], vt(rl, t), acc);
+      const size_t v0 = (size_t)ra + (size_t)i * a.ldv;
+      for (int rl = 0; rl < nr; ++rl) acc = fma(Vi(v0 + rl), vt(rl, t), acc);
     } else {
       for (int rl = 0; rl < nr; ++rl) acc = fma(vt(rl, i - j), vt(rl, t), acc);
     }
-    slot(2, g)[e] = acc;
+    slot(2, g)[RBCK(e, kPartW, a.err)] = acc;
   }
   if (!grid_sync(a.bar, a.err)) return;
   {
     const int ch = (ns + G - 1) / G;
-    const double* s2 = slot(2, 0);
     block_sums(
         min(ns, g * ch), min(ns, (g + 1) * ch), [&](int) { return G; },
-        [&](int e, int gg) { return __ldcg(s2 + (size_t)gg * kPartW + e); }, [&](int e, double v) { a.red[kRedS + e] = v; });
+        [&](int e, int gg) { return __ldcg(Pt(2, gg, e)); },
+        [&](int e, double v) { *Ri(kRedS + e) = v; });
   }
   if (!grid_sync(a.bar, a.err)) return;
   // T's new columns (Eq. for T, one reflector at a time): row i of CTA i mod G,
   // a warp per row, lanes along k; S and the row staged in shared memory
   double* Ss = Vc;  // ns <= 8192 doubles over Vc and Zs
-  for (int e = tid; e < ns; e += kPT) Ss[e] = __ldcg(a.red + kRedS + e);
+  for (int e = tid; e < ns; e += kPT) Ss[e] = __ldcg(Ri(kRedS + e));
   __syncthreads();
   double* trow = tw + warp * kBmax;
   for (int i = g + warp * G; i < j + wp; i += 8 * G) {
-    for (int k = lane; k < j; k += 32) trow[k] = a.T[i + (size_t)k * kBmax];
+    for (int k = lane; k < j; k += 32) trow[k] = Ti(i + (size_t)k * kBmax);
     __syncwarp();
     for (int t = 0; t < wp; ++t) {
       const int col = j + t;
@@ -749,7 +792,7 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
       if (lane == 0) trow[col] = val;
       __syncwarp();
     }
-    for (int t = lane; t < wp; t += 32) a.T[i + (size_t)(j + t) * kBmax] = trow[j + t];
+    for (int t = lane; t < wp; t += 32) Ti(i + (size_t)(j + t) * kBmax) = trow[j + t];
     __syncwarp();
   }
 }
@@ -759,30 +802,32 @@ __global__ void __launch_bounds__(kPT, 1) panel_kernel(PanArgs a) {
 __global__ void __launch_bounds__(256) yfix_kernel(const double* __restrict__ AV, int ks, long long kstride,
                                                    long long ldav, int rows, double* __restrict__ Y,
                                                    long long ldy, int j, int wp, const double* __restrict__ S,
-                                                   const double* __restrict__ T) {
+                                                   const double* __restrict__ T, size_t nav, size_t ny,
+                                                   int* err) {
   extern __shared__ double ysm[];
   double* Ss = ysm;              // S(i, t) for i < j
   double* Tt = Ss + j * wp;      // Tt[t' + t * wp] = T(j + t', j + t)
   const int R = 256 / wp;        // rows per CTA
   double* us = Tt + wp * wp;     // us[t' * R + rl]
   const int tid = threadIdx.x;
-  for (int e = tid; e < j * wp; e += 256) Ss[e] = S[e];
-  for (int e = tid; e < wp * wp; e += 256) Tt[e] = T[(size_t)(j + e % wp) + (size_t)(j + e / wp) * kBmax];
+  for (int e = tid; e < j * wp; e += 256) Ss[e] = S[RBCK(e, 8192, err)];
+  for (int e = tid; e < wp * wp; e += 256)
+    Tt[e] = T[RBCK((size_t)(j + e % wp) + (size_t)(j + e / wp) * kBmax, (size_t)kBmax * kBmax, err)];
   __syncthreads();
   const int rl = tid % R, tp = tid / R;
   const int e = blockIdx.x * R + rl;
   const bool act = tp < wp && e < rows;
   if (act) {
     double u = 0.0;
-    for (int q = 0; q < ks; ++q) u += AV[(size_t)q * kstride + e + (size_t)tp * ldav];
-    for (int i = 0; i < j; ++i) u = fma(-Y[e + (size_t)i * ldy], Ss[i * wp + tp], u);
+    for (int q = 0; q < ks; ++q) u += AV[RBCK((size_t)q * kstride + e + (size_t)tp * ldav, nav, err)];
+    for (int i = 0; i < j; ++i) u = fma(-Y[RBCK(e + (size_t)i * ldy, ny, err)], Ss[i * wp + tp], u);
     us[tp * R + rl] = u;
   }
   __syncthreads();
   if (act) {
     double y = 0.0;
     for (int q = 0; q <= tp; ++q) y = fma(us[q * R + rl], Tt[q + tp * wp], y);
-    Y[e + (size_t)(j + tp) * ldy] = y;
+    Y[RBCK(e + (size_t)(j + tp) * ldy, ny, err)] = y;
   }
 }
 
@@ -791,7 +836,7 @@ __global__ void __launch_bounds__(256) yfix_kernel(const double* __restrict__ AV
 // the exponent of column c.
 __global__ void __launch_bounds__(256) zmake_kernel(const double* __restrict__ Wp, int ks, long long kstride,
                                                     int jb, int cs, int n, const double* __restrict__ T,
-                                                    DigitMat Z) {
+                                                    DigitMat Z, size_t nw, int* err) {
   __shared__ double Ws[kBmax][33];
   __shared__ int Es[32];
   const int tid = threadIdx.x;
@@ -801,7 +846,7 @@ __global__ void __launch_bounds__(256) zmake_kernel(const double* __restrict__ W
     const int c = cb + cl;
     double v = 0.0;
     if (i < jb && c < n)
-      for (int q = 0; q < ks; ++q) v += Wp[(size_t)q * kstride + i + (size_t)c * kBmax];
+      for (int q = 0; q < ks; ++q) v += Wp[RBCK((size_t)q * kstride + i + (size_t)c * kBmax, nw, err)];
     Ws[i][cl] = v;
   }
   __syncthreads();
@@ -812,7 +857,7 @@ __global__ void __launch_bounds__(256) zmake_kernel(const double* __restrict__ W
     const int i = ig + 8 * q;
     double acc = 0.0;
     if (i < jb)
-      for (int k = 0; k <= i; ++k) acc = fma(T[k + (size_t)i * kBmax], Ws[k][cl], acc);
+      for (int k = 0; k <= i; ++k) acc = fma(T[RBCK(k + (size_t)i * kBmax, (size_t)kBmax * kBmax, err)], Ws[k][cl], acc);
     zv[q] = acc;
   }
   __syncthreads();
@@ -824,7 +869,7 @@ __global__ void __launch_bounds__(256) zmake_kernel(const double* __restrict__ W
     for (int i = 0; i < jb; ++i) mx = fmax(mx, fabs(Ws[i][tid]));
     const int E = scale_exp(mx);
     Es[tid] = E;
-    if (cb + tid < n) Z.ex[cb + tid] = E;
+    if (cb + tid < n) Z.ex[RBCK(cb + tid, (size_t)Z.RT * kTR, err)] = E;
   }
   __syncthreads();
   const int kmax = ((jb + kTK - 1) / kTK) * kTK;
@@ -843,7 +888,7 @@ __global__ void __launch_bounds__(256) zmake_kernel(const double* __restrict__ W
       v.y = (unsigned)dg[2][l] | ((unsigned)dg[3][l] << 16);
       v.z = (unsigned)dg[4][l] | ((unsigned)dg[5][l] << 16);
       v.w = (unsigned)dg[6][l] | ((unsigned)dg[7][l] << 16);
-      *reinterpret_cast<uint4*>(Z.d + tile_index(Z, l, i0 / kTK, c / kTR) + off) = v;
+      *reinterpret_cast<uint4*>(Z.d + RBCR(tile_index(Z, l, i0 / kTK, c / kTR) + off, 8, Z.nd, err)) = v;
     }
   }
 }
@@ -867,6 +912,7 @@ struct RtcScratch {
   int panels;       // panel launches so far
   DigitMat erow, ecol, yrow, vrow, vcol, zcol;
   int G;
+  size_t nE, nV, nY, nW, nAV, npart;  // extents in doubles
 };
 
 inline long long rup(long long x, long long a) { return (x + a - 1) / a * a; }
@@ -891,13 +937,19 @@ size_t rtc_layout(int n, int p, unsigned char* base, RtcScratch* S) {
   s.ldE = ldE;
   s.ldv = ldv;
   s.G = G;
-  s.E = (double*)take(sizeof(double) * ldE * n);
-  s.V = (double*)take(sizeof(double) * ldv * kBmax);
+  s.nE = (size_t)ldE * n;
+  s.nV = (size_t)ldv * kBmax;
+  s.nY = (size_t)ldE * kBmax;
+  s.nW = (size_t)ksW * kBmax * (size_t)n;
+  s.nAV = (size_t)ksY * ldE * kMaxW;
+  s.npart = 3 * (size_t)G * kPartW;
+  s.E = (double*)take(sizeof(double) * s.nE);
+  s.V = (double*)take(sizeof(double) * s.nV);
   s.T = (double*)take(sizeof(double) * kBmax * kBmax);
-  s.Y = (double*)take(sizeof(double) * ldE * kBmax);
-  s.W = (double*)take(sizeof(double) * ksW * kBmax * (size_t)n);
-  s.AV = (double*)take(sizeof(double) * ksY * ldE * kMaxW);
-  s.part = (double*)take(sizeof(double) * 3 * (size_t)G * kPartW);
+  s.Y = (double*)take(sizeof(double) * s.nY);
+  s.W = (double*)take(sizeof(double) * s.nW);
+  s.AV = (double*)take(sizeof(double) * s.nAV);
+  s.part = (double*)take(sizeof(double) * s.npart);
   s.red = (double*)take(sizeof(double) * kRedTotal);
   s.nbar = n + 16;
   s.panels = 0;
@@ -907,6 +959,7 @@ size_t rtc_layout(int n, int p, unsigned char* base, RtcScratch* S) {
     M.RT = RT;
     M.KT = KT;
     M.d = (unsigned short*)take(digit_bytes(RT, KT));
+    M.nd = digit_bytes(RT, KT) / sizeof(unsigned short);
     M.ex = ex ? (int*)take(sizeof(int) * (size_t)RT * kTR) : nullptr;
     return M;
   };
@@ -922,20 +975,21 @@ size_t rtc_layout(int n, int p, unsigned char* base, RtcScratch* S) {
 
 // rows [r_lo, r_hi) x K [k_lo, k_hi) of src into M (tiles of whole 128-row pairs)
 int split_into(const double* src, long long sr, long long sk, int r_lo, int r_hi, int k_lo, int k_hi,
-               const DigitMat& M, cudaStream_t st) {
+               const DigitMat& M, size_t nsrc, int* err, cudaStream_t st) {
+  const size_t nex = (size_t)M.RT * kTR;
   if (r_hi <= r_lo || k_hi <= k_lo) return SSV_OK;
   if (M.ex) {
     SSV_CUDA_TRY(cudaMemsetAsync(M.ex, 0x80, sizeof(int) * (size_t)M.RT * kTR, st));
     const int kchunk = 512;
     dim3 grid((unsigned)((r_hi - r_lo + 63) / 64), (unsigned)((k_hi - k_lo + kchunk - 1) / kchunk));
-    split_exp_kernel<<<grid, 256, 0, st>>>(src, sr, sk, r_lo, r_hi, k_lo, k_hi, kchunk, M.ex);
+    split_exp_kernel<<<grid, 256, 0, st>>>(src, sr, sk, r_lo, r_hi, k_lo, k_hi, kchunk, M.ex, nsrc, nex, err);
     count_launch();
     SSV_CUDA_TRY(cudaGetLastError());
   }
   const int I0 = 2 * (r_lo / 128), I1 = 2 * ((r_hi + 127) / 128);
   const int J0 = k_lo / kTK, J1 = (k_hi + kTK - 1) / kTK;
   split_dig_kernel<<<dim3((unsigned)(I1 - I0), (unsigned)(J1 - J0)), 256, 0, st>>>(src, sr, sk, r_lo, r_hi, k_lo,
-                                                                                 k_hi, M, I0, J0);
+                                                                                 k_hi, M, I0, J0, nsrc, nex, err);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   return SSV_OK;
@@ -964,7 +1018,7 @@ int gemm_long(int width, const GArgs& g, cudaStream_t st) {
 }
 
 GArgs gemm_args(const DigitMat& A, const DigitMat& B, int J0, int J1, int M0, int M1, int N0, int N1, double* C,
-                long long ldc, int sub, const RtcScratch& S) {
+                size_t nc, long long ldc, int sub, const RtcScratch& S) {
   GArgs g;
   g.seg.A = A;
   g.seg.B = B;
@@ -977,6 +1031,7 @@ GArgs gemm_args(const DigitMat& A, const DigitMat& B, int J0, int J1, int M0, in
   g.roff = 0;
   g.coff = 0;
   g.C = C;
+  g.nc = nc;
   g.ldc = ldc;
   g.sub = sub;
   g.ksplit = 1;
@@ -986,8 +1041,8 @@ GArgs gemm_args(const DigitMat& A, const DigitMat& B, int J0, int J1, int M0, in
 }
 
 // One mini-block: panel (cooperative), A V_s on the tensor cores, Y's new columns.
-int run_panel(RtcScratch& S, int n, int p, double* P, long long ldp, int r0, int w, int wp, int pv0, int j,
-              int c0, double* tau, cudaStream_t st) {
+int run_panel(RtcScratch& S, int n, int p, double* P, size_t np, long long ldp, int r0, int w, int wp, int pv0,
+              int j, int c0, double* tau, size_t ntau, cudaStream_t st) {
   if (S.panels >= S.nbar) return SSV_EINVAL;
   const int L = n - r0;
   int G = std::min(S.G, std::max(1, (L + 15) / 16));
@@ -1015,6 +1070,11 @@ int run_panel(RtcScratch& S, int n, int p, double* P, long long ldp, int r0, int
   a.red = S.red;
   a.bar = S.bar + 4 + S.panels++;
   a.err = reinterpret_cast<int*>(S.bar + 2);
+  a.np = np;
+  a.nv = S.nV;
+  a.ny = S.nY;
+  a.ntau = ntau;
+  a.npart = S.npart;
   const size_t smem = sizeof(double) * ((size_t)rpc * w + kPanFixed);
   SSV_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   void* args[] = {&a};
@@ -1023,7 +1083,7 @@ int run_panel(RtcScratch& S, int n, int p, double* P, long long ldp, int r0, int
   // A V_s: every row of E against the new reflectors (rows pv0.. of V_s are nonzero)
   const int KTn = (n + kTK - 1) / kTK;
   const int rowsE = p + n;
-  GArgs g = gemm_args(S.erow, S.vcol, pv0 / kTK, KTn, 0, rowsE, j, j + wp, S.AV, S.ldE, 0, S);
+  GArgs g = gemm_args(S.erow, S.vcol, pv0 / kTK, KTn, 0, rowsE, j, j + wp, S.AV, S.nAV, S.ldE, 0, S);
   g.coff = -j;
   const int NT = wp <= 16 ? 16 : 32;
   const int nI = (rowsE + 127) / 128, nN = (j + wp + NT - 1) / NT - j / NT;
@@ -1035,7 +1095,7 @@ int run_panel(RtcScratch& S, int n, int p, double* P, long long ldp, int r0, int
   const size_t ysm = sizeof(double) * ((size_t)j * wp + (size_t)wp * wp + 256);
   SSV_CUDA_TRY(cudaFuncSetAttribute(yfix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm));
   yfix_kernel<<<(rowsE + R - 1) / R, 256, ysm, st>>>(S.AV, g.ksplit, g.kstride, S.ldE, rowsE, S.Y, S.ldE, j, wp,
-                                                     S.red + kRedS, S.T);
+                                                     S.red + kRedS, S.T, S.nAV, S.nY, a.err);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
   return SSV_OK;
@@ -1047,34 +1107,43 @@ int run_panel(RtcScratch& S, int n, int p, double* P, long long ldp, int r0, int
 int run_block_end(const RtcScratch& S, int n, int p, int r0, int tc0, int cs, int jb, cudaStream_t st) {
   const int rowsE = p + n;
   const int KTn = (n + kTK - 1) / kTK, KTj = (jb + kTK - 1) / kTK;
-  int rc = split_into(S.Y, 1, S.ldE, 0, rowsE, 0, jb, S.yrow, st);
+  int* err = reinterpret_cast<int*>(S.bar + 2);
+  int rc = split_into(S.Y, 1, S.ldE, 0, rowsE, 0, jb, S.yrow, S.nY, err, st);
   // V by rows, each with its own exponent (a row of V across the block's
   // reflectors is mostly far below the unit pivots)
-  if (rc == SSV_OK) rc = split_into(S.V, 1, S.ldv, 0, n, 0, jb, S.vrow, st);
+  if (rc == SSV_OK) rc = split_into(S.V, 1, S.ldv, 0, n, 0, jb, S.vrow, S.nV, err, st);
   if (rc != SSV_OK) return rc;
   if (tc0 == cs) {
-    rc = gemm_launch<64, 8>(gemm_args(S.yrow, S.vrow, 0, KTj, 0, rowsE, cs, n, S.E, S.ldE, 1, S), st);
+    rc = gemm_launch<64, 8>(gemm_args(S.yrow, S.vrow, 0, KTj, 0, rowsE, cs, n, S.E, S.nE, S.ldE, 1, S), st);
   } else {
-    rc = gemm_launch<64, 8>(gemm_args(S.yrow, S.vrow, 0, KTj, 0, p + r0, tc0, n, S.E, S.ldE, 1, S), st);
+    rc = gemm_launch<64, 8>(gemm_args(S.yrow, S.vrow, 0, KTj, 0, p + r0, tc0, n, S.E, S.nE, S.ldE, 1, S), st);
     if (rc == SSV_OK)
-      rc = gemm_launch<64, 8>(gemm_args(S.yrow, S.vrow, 0, KTj, p + r0, rowsE, cs, n, S.E, S.ldE, 1, S), st);
+      rc = gemm_launch<64, 8>(gemm_args(S.yrow, S.vrow, 0, KTj, p + r0, rowsE, cs, n, S.E, S.nE, S.ldE, 1, S), st);
   }
   if (rc != SSV_OK || cs >= n) return rc;
-  rc = split_into(S.E + p, S.ldE, 1, cs, n, r0, n, S.ecol, st);
+  rc = split_into(S.E + p, S.ldE, 1, cs, n, r0, n, S.ecol, S.nE - p, err, st);
   if (rc != SSV_OK) return rc;
-  GArgs g = gemm_args(S.vcol, S.ecol, r0 / kTK, KTn, 0, jb, cs, n, S.W, kBmax, 0, S);
+  GArgs g = gemm_args(S.vcol, S.ecol, r0 / kTK, KTn, 0, jb, cs, n, S.W, S.nW, kBmax, 0, S);
   const int nN = (n + 31) / 32 - cs / 32;
   g.ksplit = std::max(1, std::min(8, S.G / std::max(1, nN)));
   g.kstride = (long long)kBmax * n;
   rc = gemm_launch<32, 9>(g, st);
   if (rc != SSV_OK) return rc;
-  zmake_kernel<<<(n - cs + 31) / 32, 256, 0, st>>>(S.W, g.ksplit, g.kstride, jb, cs, n, S.T, S.zcol);
+  zmake_kernel<<<(n - cs + 31) / 32, 256, 0, st>>>(S.W, g.ksplit, g.kstride, jb, cs, n, S.T, S.zcol, S.nW, err);
   count_launch();
   SSV_CUDA_TRY(cudaGetLastError());
-  GArgs gl = gemm_args(S.vrow, S.zcol, 0, KTj, r0, n, cs, n, S.E, S.ldE, 1, S);
+  GArgs gl = gemm_args(S.vrow, S.zcol, 0, KTj, r0, n, cs, n, S.E, S.nE, S.ldE, 1, S);
   gl.roff = p;
   return gemm_launch<64, 8>(gl, st);
 }
+
+#ifdef SSV_BOUNDS_CHECK
+// bit 4 of the error word when a byte of the canary after the scratch changed
+__global__ void rtc_canary_kernel(const unsigned char* c, size_t nbytes, int* err) {
+  for (size_t i = threadIdx.x; i < nbytes; i += blockDim.x)
+    if (c[i] != 0xA5) atomicOr(err, 4);
+}
+#endif
 
 int clear_block(const RtcScratch& S, int n, cudaStream_t st) {
   SSV_CUDA_TRY(cudaMemsetAsync(S.V, 0, sizeof(double) * S.ldv * kBmax, st));
@@ -1102,10 +1171,16 @@ int reduce_tc(Handle* h, cudaStream_t st) {
   if (!reduce_tc_supported(n, m)) return SSV_ENOTSUP;
   const int ldct = p > 0 ? p : 1;
   const size_t bytes = rtc_layout(n, p, nullptr, nullptr);
+#ifdef SSV_BOUNDS_CHECK
+  constexpr size_t kCanary = 256;  // checked at the end
+#else
+  constexpr size_t kCanary = 0;
+#endif
   unsigned char* base = nullptr;
-  SSV_CUDA_TRY(pool_alloc((void**)&base, bytes, st));
+  SSV_CUDA_TRY(pool_alloc((void**)&base, bytes + kCanary, st));
   RtcScratch S;
   rtc_layout(n, p, base, &S);
+  int* err = reinterpret_cast<int*>(S.bar + 2);
   int rc = SSV_OK;
   auto step = [&](int r) {
     if (rc == SSV_OK) rc = r;
@@ -1116,6 +1191,12 @@ int reduce_tc(Handle* h, cudaStream_t st) {
       rc = e == cudaErrorMemoryAllocation ? SSV_ENOMEM : SSV_ECUDA;
     }
   };
+#ifdef SSV_BOUNDS_CHECK
+  // scratch read before it is written shows up as NaN (0xFF bytes), the canary
+  // after the scratch as a changed byte
+  cu(cudaMemsetAsync(base, 0xFF, bytes, st));
+  cu(cudaMemsetAsync(base + bytes, 0xA5, kCanary, st));
+#endif
   cu(cudaMemsetAsync(S.bar, 0, 16 + sizeof(unsigned) * (size_t)S.nbar, st));
   if (p > 0)
     cu(cudaMemcpy2DAsync(S.E, sizeof(double) * S.ldE, h->Ct, sizeof(double) * ldct, sizeof(double) * p, n,
@@ -1125,8 +1206,9 @@ int reduce_tc(Handle* h, cudaStream_t st) {
   // Step 1: the QR of B, applied to A from both sides and to C from the right
   if (h->kb > 0) {
     step(clear_block(S, n, st));
-    step(split_into(S.E, 1, S.ldE, 0, p + n, 0, n, S.erow, st));
-    if (rc == SSV_OK) step(run_panel(S, n, p, h->R, n, 0, m, h->kb, 0, 0, 0, h->tauB, st));
+    step(split_into(S.E, 1, S.ldE, 0, p + n, 0, n, S.erow, S.nE, err, st));
+    if (rc == SSV_OK)
+      step(run_panel(S, n, p, h->R, (size_t)n * m, n, 0, m, h->kb, 0, 0, 0, h->tauB, (size_t)h->kb, st));
     if (rc == SSV_OK) step(run_block_end(S, n, p, 0, 0, 0, h->kb, st));
   }
   // Steps 2-3: the m-Hessenberg reduction of A, blocks of b = floor(128 / m) m columns
@@ -1135,11 +1217,13 @@ int reduce_tc(Handle* h, cudaStream_t st) {
     const int jb = std::min(b, h->ka - z);
     const int r0 = z + m;
     step(clear_block(S, n, st));
-    step(split_into(S.E, 1, S.ldE, 0, p + n, r0, n, S.erow, st));
+    step(split_into(S.E, 1, S.ldE, 0, p + n, r0, n, S.erow, S.nE, err, st));
     for (int j = 0; j < jb && rc == SSV_OK; j += m) {
       const int w = std::min(m, jb - j);
       const int c0 = z + j;
-      step(run_panel(S, n, p, S.E + p + (size_t)c0 * S.ldE, S.ldE, r0, w, w, c0 + m, j, c0, h->tauA + c0, st));
+      const size_t off = (size_t)p + (size_t)c0 * S.ldE;
+      step(run_panel(S, n, p, S.E + off, S.nE - off, S.ldE, r0, w, w, c0 + m, j, c0, h->tauA + c0,
+                     (size_t)(h->ka - c0), st));
     }
     if (rc == SSV_OK) step(run_block_end(S, n, p, r0, r0, z + jb, jb, st));
   }
@@ -1148,10 +1232,20 @@ int reduce_tc(Handle* h, cudaStream_t st) {
   if (p > 0)
     cu(cudaMemcpy2DAsync(h->Ct, sizeof(double) * ldct, S.E, sizeof(double) * S.ldE, sizeof(double) * p, n,
                          cudaMemcpyDeviceToDevice, st));
+#ifdef SSV_BOUNDS_CHECK
+  if (rc == SSV_OK) {
+    rtc_canary_kernel<<<1, 256, 0, st>>>(base + bytes, kCanary, err);
+    count_launch();
+    cu(cudaGetLastError());
+  }
+#endif
   int herr = 0;
   cu(cudaMemcpyAsync(&herr, S.bar + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
   cu(cudaStreamSynchronize(st));
-  if (rc == SSV_OK && herr != 0) rc = SSV_ETIMEOUT;
+  // bit 1: a wait gave up; bits 2 and 4 (debug builds): an index out of range,
+  // a changed canary
+  if (rc == SSV_OK && (herr & 1)) rc = SSV_ETIMEOUT;
+  else if (rc == SSV_OK && herr != 0) rc = SSV_ECUDA;
   cudaError_t e2 = cudaFreeAsync(base, st);
   if (e2 != cudaSuccess && rc == SSV_OK) {
     set_cuda_error(e2);
